@@ -1,0 +1,54 @@
+"""Plants plausible mistakes in a copy of the oracle (CPU only) and checks that
+the pins of test_oracle_pins.py catch every one of them."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "amg_oracle.c")
+
+# (name, original text, mutated text, pins expected to fail)
+MUTANTS = [
+    ("prolongation_sign", "x[i] = x[i] + xc[l->agg[i]];", "x[i] = x[i] - xc[l->agg[i]];",
+     "test_vcycle_closed_form_on_2x2_blocks"),
+    ("restriction_drops_term", "else fc[I] = fc[I] + t[i];", "else fc[I] = t[i];",
+     "test_vcycle_closed_form_on_2x2_blocks"),
+    ("jacobi_without_omega", "x[i] = x[i] + omega * (f[i] - t[i]) / l->diag[i];",
+     "x[i] = x[i] + (f[i] - t[i]) / l->diag[i];", "test_vcycle_closed_form_on_2x2_blocks"),
+    ("galerkin_drops_term", "val_c[slot[J]] = val_c[slot[J]] + val[e];", "val_c[slot[J]] = val_c[slot[J]];",
+     "test_worked_example_matches_paper"),
+    ("tie_break_larger_index", "if (a->u != b->u) return a->u < b->u ? -1 : 1;",
+     "if (a->u != b->u) return a->u > b->u ? -1 : 1;", "test_greedy_matching_bruteforce"),
+    ("rounds_tie_break", "(g.w[k] == best && j < pick[i])", "(g.w[k] == best && j > pick[i])",
+     "test_handshake_rounds_reach_greedy_matching"),
+    ("numbering_by_largest", "if (mate[i] < 0 || i < mate[i]) agg[i] = C++;",
+     "if (mate[i] < 0 || i > mate[i]) agg[i] = C++;", "test_aggregates_partition_and_numbering"),
+    ("pcg_residual_sign", "r[i] = r[i] - alpha * q[i];", "r[i] = r[i] + alpha * q[i];",
+     "test_pcg_matches_dense_solve_to_1e10"),
+    ("bicgstab_p_update", "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
+     "test_krylov_finite_termination_two_eigenvalues"),
+    ("coarse_cg_steepest_descent", "double beta = rz_new / rz;\n      rz = rz_new;\n      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];",
+     "double beta = 0.0 * rz_new / rz;\n      rz = rz_new;\n      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];",
+     "test_coarse_cg_solver_agrees_with_dense"),
+    ("lu_no_pivoting", "if (fabs(a[(size_t)i * n + k]) > best)", "if (0 && fabs(a[(size_t)i * n + k]) > best)",
+     "test_dense_lu_matches_numpy"),
+]
+
+
+@pytest.mark.parametrize("name,orig,mut,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, mut, pins):
+    src = open(SRC).read()
+    assert src.count(orig) == 1, f"mutation anchor for {name} not unique"
+    bad = tmp_path / "amg_oracle_mutant.c"
+    bad.write_text(src.replace(orig, mut))
+    so = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(so), str(bad), "-lm"])
+    env = dict(os.environ, AMG_ORACLE_SO=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"), "-k", pins],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 1, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"

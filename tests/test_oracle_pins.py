@@ -1,0 +1,430 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these tests compares the oracle with itself: each checks it against a
+value printed in the paper, a closed form, an invariant, a textbook routine
+(numpy dense algebra) or brute force on tiny inputs.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_00056_gb300 import workloads as W
+from tests.conftest import read_golden
+
+
+def _P(agg, nc):
+    P = np.zeros((len(agg), nc))
+    P[np.arange(len(agg)), agg] = 1.0
+    return P
+
+
+def _dense(rp, ci, val, n):
+    a = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    a[rows, ci] = val
+    return a
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1.1 worked example (printed A, P, A_c)
+# --------------------------------------------------------------------------
+
+def test_worked_example_matches_paper():
+    g = read_golden("worked_example.txt")
+    s = W.from_dense(g["A"])
+    mate = O.match_greedy(s.rp, s.ci, s.val)
+    agg, nc = O.aggregates(mate)
+    assert nc == 3
+    np.testing.assert_array_equal(_P(agg, nc), g["P"])
+    rpc, cic, vc = O.galerkin(s.rp, s.ci, s.val, agg, nc)
+    np.testing.assert_array_equal(_dense(rpc, cic, vc, nc), g["Ac"])
+    # the handshake rounds reach the same pairs (one productive round + one empty round)
+    mate_r, rounds = O.match_rounds(s.rp, s.ci, s.val)
+    np.testing.assert_array_equal(mate_r, mate)
+    assert rounds == 2
+    # the paper's own Algorithm 2 (node-based) produces the printed P too
+    agg_n, nc_n = O.nhem(s.rp, s.ci, s.val)
+    np.testing.assert_array_equal(_P(agg_n, nc_n), g["P"])
+
+
+def test_galerkin_diagonal_formula():
+    """(A_c)_kk = a_ij + a_ji + a_ii + a_jj for a pair k = {i, j} (Sec. 2.1.1)."""
+    for seed in range(5):
+        s = W.random_spd(40, 0.15, seed)
+        a = s.dense()
+        a = a + np.triu(np.random.default_rng(seed).uniform(-0.1, 0.1, a.shape), 1) * (a != 0)
+        s2 = W.from_dense(a)
+        mate = O.match_greedy(s2.rp, s2.ci, s2.val)
+        agg, nc = O.aggregates(mate)
+        rpc, cic, vc = O.galerkin(s2.rp, s2.ci, s2.val, agg, nc)
+        ac = _dense(rpc, cic, vc, nc)
+        for i in range(s2.n):
+            j = mate[i]
+            if j > i:
+                k = agg[i]
+                assert ac[k, k] == pytest.approx(a[i, j] + a[j, i] + a[i, i] + a[j, j], rel=1e-15, abs=1e-15)
+            elif j < 0:
+                assert ac[agg[i], agg[i]] == a[i, i]
+
+
+# --------------------------------------------------------------------------
+# Galerkin product against dense P^T A P
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(6))
+def test_galerkin_equals_dense_triple_product(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(5, 60))
+    mask = rng.random((n, n)) < 0.2
+    np.fill_diagonal(mask, True)
+    a = np.where(mask, rng.standard_normal((n, n)), 0.0)
+    # plant explicit zeros that must survive as structural entries
+    zeros = mask & (rng.random((n, n)) < 0.1)
+    a[zeros] = 0.0
+    s = W.from_dense(a, keep_zeros=mask)
+    nc = int(rng.integers(1, n + 1))
+    agg = np.concatenate([np.arange(nc), rng.integers(0, nc, n - nc)]).astype(np.int32)
+    rng.shuffle(agg)
+    # renumber so that aggregate ids follow the smallest member (any map works for P^T A P)
+    rpc, cic, vc = O.galerkin(s.rp, s.ci, s.val, agg, nc)
+    P = _P(agg, nc)
+    np.testing.assert_allclose(_dense(rpc, cic, vc, nc), P.T @ a @ P, rtol=1e-13, atol=1e-13)
+    # structural pattern: (I,J) stored iff some stored (i,j) maps to it
+    pat = (P.T @ mask.astype(float) @ P) > 0
+    got = np.zeros((nc, nc), dtype=bool)
+    rows = np.repeat(np.arange(nc), np.diff(rpc))
+    got[rows, cic] = True
+    np.testing.assert_array_equal(got, pat)
+    # columns strictly ascending per row
+    for I in range(nc):
+        assert np.all(np.diff(cic[rpc[I]:rpc[I + 1]]) > 0)
+
+
+def test_galerkin_symmetric_stays_exactly_symmetric():
+    for seed in range(4):
+        s = W.random_spd(80, 0.08, seed)
+        mate = O.match_greedy(s.rp, s.ci, s.val)
+        agg, nc = O.aggregates(mate)
+        rpc, cic, vc = O.galerkin(s.rp, s.ci, s.val, agg, nc)
+        ac = _dense(rpc, cic, vc, nc)
+        np.testing.assert_array_equal(ac, ac.T)
+
+
+# --------------------------------------------------------------------------
+# Matching: brute force, invariants, handshake rounds
+# --------------------------------------------------------------------------
+
+def _edges(a):
+    n = a.shape[0]
+    E = {}
+    for i in range(n):
+        for j in range(n):
+            if i != j and a[i, j] != 0:
+                u, v = min(i, j), max(i, j)
+                E[(u, v)] = max(E.get((u, v), 0.0), abs(a[i, j]))
+    return E
+
+
+def _bruteforce_greedy(a):
+    """Lexicographically first maximal matching in the edge order (w desc,
+    min asc, max asc), found by enumerating every matching."""
+    E = _edges(a)
+    order = sorted(E, key=lambda e: (-E[e], e[0], e[1]))
+    rank = {e: r for r, e in enumerate(order)}
+    n = a.shape[0]
+    best = None
+    edges = list(E)
+    for k in range(0, n // 2 + 1):
+        for combo in itertools.combinations(edges, k):
+            used = set()
+            ok = True
+            for u, v in combo:
+                if u in used or v in used:
+                    ok = False
+                    break
+                used.add(u); used.add(v)
+            if not ok:
+                continue
+            if any(u not in used and v not in used for u, v in edges):
+                continue  # not maximal
+            key = sorted(rank[e] for e in combo)
+            if best is None or key < best[0]:
+                best = (key, combo)
+    mate = -np.ones(n, dtype=np.int32)
+    for u, v in best[1]:
+        mate[u], mate[v] = v, u
+    return mate
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_greedy_matching_bruteforce(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(2, 9))
+    mask = np.triu(rng.random((n, n)) < 0.5, 1)
+    w = -rng.integers(1, 3, (n, n)).astype(float)  # ties on purpose
+    a = np.where(mask, w, 0.0)
+    if seed % 2:  # nonsymmetric values on a symmetric pattern
+        a = a + np.where(mask, -rng.integers(1, 3, (n, n)), 0.0).T
+    else:
+        a = a + a.T
+    a[np.diag_indices(n)] = 10.0
+    s = W.from_dense(a)
+    np.testing.assert_array_equal(O.match_greedy(s.rp, s.ci, s.val), _bruteforce_greedy(a))
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_handshake_rounds_reach_greedy_matching(seed):
+    """Synchronous mutual-heaviest handshakes, run to the fixed point, give the
+    greedy edge-order matching (locally dominant edges are greedy edges)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 80))
+    s = W.random_spd(n, float(rng.uniform(0.05, 0.4)), seed, int_weights=bool(seed % 3))
+    mate_g = O.match_greedy(s.rp, s.ci, s.val)
+    mate_r, rounds = O.match_rounds(s.rp, s.ci, s.val)
+    np.testing.assert_array_equal(mate_r, mate_g)
+    assert rounds >= 1
+
+
+def test_matching_is_maximal_and_consistent():
+    for seed in range(10):
+        s = W.random_spd(100, 0.05, seed, int_weights=True)
+        mate = O.match_greedy(s.rp, s.ci, s.val)
+        a = s.dense()
+        for i in range(s.n):
+            if mate[i] >= 0:
+                assert mate[mate[i]] == i and a[i, mate[i]] != 0
+        for (u, v) in _edges(a):
+            assert mate[u] >= 0 or mate[v] >= 0, "an edge with both ends free remains"
+
+
+def test_numbering_invariance_distinct_weights():
+    """EHEM is invariant to the numbering when the weights are distinct (Sec. 2.1.2)."""
+    for seed in range(5):
+        s = W.random_spd(60, 0.1, seed)
+        a = s.dense()
+        perm = np.random.default_rng(seed).permutation(s.n)
+        ap = a[np.ix_(perm, perm)]  # new index k is old node perm[k]
+        sp = W.from_dense(ap)
+        m0 = O.match_greedy(s.rp, s.ci, s.val)
+        m1 = O.match_greedy(sp.rp, sp.ci, sp.val)
+        inv = np.argsort(perm)
+        for k in range(s.n):
+            old = perm[k]
+            if m0[old] < 0:
+                assert m1[k] < 0
+            else:
+                assert m1[k] == inv[m0[old]]
+
+
+def test_aggregates_partition_and_numbering():
+    s = W.random_spd(200, 0.03, 7, int_weights=True)
+    mate = O.match_greedy(s.rp, s.ci, s.val)
+    agg, nc = O.aggregates(mate)
+    assert agg.min() == 0 and agg.max() == nc - 1
+    counts = np.bincount(agg, minlength=nc)
+    assert np.all((counts >= 1) & (counts <= 2))  # pairs or singletons
+    assert nc >= s.n / 2  # coarsening ratio slightly below two per pass
+    # aggregate id = rank of the smallest member
+    first = np.array([np.min(np.nonzero(agg == I)[0]) for I in range(nc)])
+    assert np.all(np.diff(first) > 0)
+
+
+# --------------------------------------------------------------------------
+# Hierarchy shapes
+# --------------------------------------------------------------------------
+
+def test_uniform_grid_hierarchy_quarters_each_level():
+    s = W.poisson2d(64)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=64)
+    assert h.sizes() == [4096, 1024, 256, 64]
+    s = W.anisotropic3d(16)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=64)
+    assert h.sizes() == [4096, 1024, 256, 64]
+
+
+def test_hierarchy_levels_are_galerkin_products():
+    s = W.lognormal3d(10, seed=3)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=50)
+    assert h.num_levels >= 3
+    for k in range(h.num_levels - 1):
+        rp, ci, val, agg = h.level(k)
+        rpc, cic, vc, _ = h.level(k + 1)
+        n, nc = len(rp) - 1, len(rpc) - 1
+        counts = np.bincount(agg, minlength=nc)
+        assert counts.min() >= 1 and counts.max() <= 4  # two pairwise passes
+        P = _P(agg, nc)
+        np.testing.assert_allclose(_dense(rpc, cic, vc, nc), P.T @ _dense(rp, ci, val, n) @ P,
+                                   rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Coarse solve, V-cycle, Krylov
+# --------------------------------------------------------------------------
+
+def test_dense_lu_matches_numpy():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 5, 17, 40):
+        a = rng.standard_normal((n, n)) + n * np.eye(n)
+        b = rng.standard_normal(n)
+        np.testing.assert_allclose(O.dense_solve(a, b), np.linalg.solve(a, b), rtol=1e-12, atol=1e-12)
+    # pivoting is needed: zero leading entry
+    a = np.array([[0.0, 1.0], [2.0, 3.0]])
+    np.testing.assert_allclose(O.dense_solve(a, np.array([1.0, 5.0])), [1.0, 1.0])
+
+
+def _block2x2(nblocks, a_, b_):
+    blk = np.array([[a_, -b_], [-b_, a_]])
+    return np.kron(np.eye(nblocks), blk)
+
+
+def test_vcycle_closed_form_on_2x2_blocks():
+    """Two-grid cycle on blockdiag([[a,-b],[-b,a]]): each block is one aggregate.
+    Smooth rhs (1,1) is solved exactly: the presmoothed guess w f/a plus the
+    coarse correction (1 - w(a-b)/a)/(a-b) gives 1/(a-b).  Oscillatory rhs
+    (1,-1) restricts to zero, so the result is two Jacobi steps:
+    w/a + (w/a)(1 - w(a+b)/a); for a=4, b=1, w=2/3 that is 7/36."""
+    a_, b_ = 4.0, 1.0
+    s = W.from_dense(_block2x2(8, a_, b_))
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=8)
+    assert h.sizes() == [16, 8]
+    smooth = np.ones(16)
+    np.testing.assert_allclose(h.vcycle(smooth), smooth / (a_ - b_), rtol=1e-15)
+    osc = np.tile([1.0, -1.0], 8)
+    np.testing.assert_allclose(h.vcycle(osc), osc * 7.0 / 36.0, rtol=1e-15)
+
+
+def test_single_level_vcycle_is_exact_solve():
+    s = W.random_spd(30, 0.2, 1)
+    h = O.Hierarchy(s.rp, s.ci, s.val)  # N <= coarse_max: coarsest level only
+    assert h.num_levels == 1 and h.dense_coarse
+    np.testing.assert_allclose(h.vcycle(s.b), np.linalg.solve(s.dense(), s.b), rtol=1e-12)
+
+
+def _vcycle_matrix(h, n):
+    return np.column_stack([h.vcycle(e) for e in np.eye(n)])
+
+
+def test_vcycle_operator_symmetric_and_contracting():
+    """With identical pre/post Jacobi sweeps and an exact coarse solve, M^{-1}
+    is symmetric for symmetric A and the error propagator I - M^{-1} A has
+    spectral radius below one (two-grid and multi-level)."""
+    s = W.poisson2d(16)
+    for coarse_max, levels in ((64, 2), (16, 3)):
+        h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=coarse_max)
+        assert h.num_levels == levels
+        M = _vcycle_matrix(h, s.n)
+        np.testing.assert_allclose(M, M.T, atol=1e-13)
+        E = np.eye(s.n) - M @ s.dense()
+        rho = np.max(np.abs(np.linalg.eigvals(E)))
+        assert rho < 1.0
+    s = W.lognormal3d(6, seed=5)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=20)
+    E = np.eye(s.n) - _vcycle_matrix(h, s.n) @ s.dense()
+    assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
+
+
+def test_coarse_cg_solver_agrees_with_dense():
+    s = W.lognormal3d(8, seed=2)
+    hd = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=60, coarse_solver=1)
+    hc = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=60, coarse_solver=2)
+    assert hd.dense_coarse and not hc.dense_coarse
+    np.testing.assert_allclose(hc.vcycle(s.b), hd.vcycle(s.b), rtol=1e-9, atol=1e-12)
+    # conjugate gradients end within n_L steps (finite termination), far below the cap
+    n_coarse = hc.sizes()[-1]
+    assert 1 <= hc.last_coarse_cg_iters <= n_coarse
+    s = W.lognormal3d(12, seed=2)
+    hc = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=400, coarse_solver=2)
+    hd = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=400, coarse_solver=1)
+    np.testing.assert_allclose(hc.vcycle(s.b), hd.vcycle(s.b), rtol=1e-9, atol=1e-12)
+    assert 1 <= hc.last_coarse_cg_iters <= hc.sizes()[-1] // 4
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pcg_tiny_spd_converges_within_n_steps(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(6, 30))
+    s = W.random_spd(n, 0.3, seed)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=3)
+    x, info = h.pcg(s.b, rtol=1e-12, max_iter=n)
+    assert info.status == O.OK and info.iterations <= n
+    np.testing.assert_allclose(x, np.linalg.solve(s.dense(), s.b), rtol=1e-9, atol=1e-11)
+
+
+def test_pcg_matches_dense_solve_to_1e10():
+    s = W.lognormal3d(9, seed=4)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=40)
+    x_ref = np.linalg.solve(s.dense(), s.b)
+    for flexible in (False, True):
+        x, info = h.pcg(s.b, rtol=1e-14, max_iter=200, flexible=flexible)
+        assert info.status == O.OK
+        assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10
+        assert info.rel_res_true < 1e-13
+
+
+def test_pcg_rtol_and_recurrence_residual():
+    s = W.poisson2d(32)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=16)
+    x, info = h.pcg(s.b, rtol=1e-8)
+    assert info.status == O.OK and info.rel_res_recurrence <= 1e-8
+    r = s.b - s.dense() @ x
+    assert np.linalg.norm(r) / np.linalg.norm(s.b) == pytest.approx(info.rel_res_true, rel=1e-6)
+    # one iteration fewer does not meet the tolerance
+    _, info2 = h.pcg(s.b, rtol=0.0, max_iter=info.iterations - 1)
+    assert info2.rel_res_recurrence > 1e-8
+
+
+def test_pcg_edge_cases():
+    s = W.poisson2d(8)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=4)
+    x, info = h.pcg(np.zeros(s.n))
+    assert info.iterations == 0 and np.all(x == 0)
+    x_ref = np.linalg.solve(s.dense(), s.b)
+    x, info = h.pcg(s.b, x0=x_ref)  # already converged start
+    assert info.iterations == 0
+    x, info = h.pcg(s.b, rtol=1e-30, max_iter=3)
+    assert info.status == O.ERR_NOT_CONVERGED and info.iterations == 3
+
+
+def test_bicgstab_nonsymmetric_matches_dense():
+    s = W.convdiff2d(14, peclet=200.0)
+    assert not np.allclose(s.dense(), s.dense().T)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=20)
+    x, info = h.bicgstab(s.b, rtol=1e-13, max_iter=200)
+    assert info.status == O.OK
+    x_ref = np.linalg.solve(s.dense(), s.b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-10
+    assert info.rel_res_true < 1e-12
+
+
+def test_bicgstab_spd_and_exact_preconditioner():
+    s = W.random_spd(20, 0.3, 3)
+    h = O.Hierarchy(s.rp, s.ci, s.val)  # single level: M^{-1} = A^{-1}
+    x, info = h.bicgstab(s.b, rtol=1e-12)
+    # with an exact preconditioner the first half step already solves the system
+    assert info.iterations == 1 and info.status == O.OK
+    np.testing.assert_allclose(x, np.linalg.solve(s.dense(), s.b), rtol=1e-11)
+
+
+def test_check_csr_rejects_bad_input():
+    s = W.poisson2d(4)
+    assert O.check_csr(s.rp, s.ci) == O.OK
+    ci = s.ci.copy(); ci[3] = 99
+    assert O.check_csr(s.rp, ci) == O.ERR_INVALID_CSR
+    ci = s.ci.copy(); ci[1], ci[2] = ci[2], ci[1]
+    assert O.check_csr(s.rp, ci) == O.ERR_INVALID_CSR
+
+
+def test_krylov_finite_termination_two_eigenvalues():
+    """On blockdiag([[4,-1],[-1,4]]) the two-grid preconditioned operator has
+    exactly two eigenvalues (1 on the pair-constant vectors, 35/36 on the
+    pair-alternating ones, from the closed form above), so PCG and BiCGStab
+    reach rounding level within two iterations for any right-hand side."""
+    s = W.from_dense(_block2x2(10, 4.0, 1.0))
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=10)
+    b = np.random.default_rng(0).uniform(-1, 1, s.n)
+    _, info = h.pcg(b, rtol=1e-13, max_iter=50)
+    assert info.status == O.OK and info.iterations <= 2
+    _, info = h.bicgstab(b, rtol=1e-13, max_iter=50)
+    assert info.status == O.OK and info.iterations <= 2
