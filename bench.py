@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 aggregation-AMG PCG solver.
+
+Workload (one step): the 3D 7-point lognormal-coefficient diffusion system on
+128^3 cells (2,097,152 unknowns, 14,581,760 nonzeros, FP64 CSR, coefficients
+exp(N(0,1)) seed 1): device AMG setup (pairwise heavy-edge matching, two
+passes per level, Galerkin products, coarsest solver) followed by FP64
+AMG-preconditioned CG from x = 0 to a relative residual of 1e-8.  Inputs are
+resident in HBM when the timed region starts; the level-0 matrix (183 MB) is
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Printed: one JSON line (rank 0).  value = solves per second over all ranks
+(replicas: every rank solves its own copy; no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "AMG-PCG time to 1e-8 rel. residual; V-cycle HBM GB/s; batched solves/s + p99"
+UNIT = "solves/s"
+WORKLOAD = "lognormal3d_128: 3D 7-pt FV diffusion, 128^3 cells, lognormal(0,1) coefficients seed 1, FP64 CSR"
+RTOL = 1e-8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--grid", type=int, default=128, help="cells per side of the lognormal system")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu_index)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = max(smax, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timings (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+def oracle_setup_and_iter_times(sys_, iters: int):
+    """Oracle setup time and mean time of one PCG iteration (`iters` samples).
+    Each sample is a call of the oracle PCG with max_iter = 1 from x = 0, i.e.
+    the initial residual, one V-cycle, one SpMV and the vector updates."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    oh = O.Hierarchy(sys_.rp, sys_.ci, sys_.val)
+    t_setup = time.perf_counter() - t0
+    ts = []
+    for _ in range(iters):
+        t0 = time.perf_counter()
+        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
+        ts.append(time.perf_counter() - t0)
+    return oh, t_setup, ts
+
+
+def run_reference(args, sys_):
+    """Oracle arm: the serial FP64 oracle on one host core, same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+
+    # warm-up 1: setup and a full solve fix the setup time and the iteration count
+    t0 = time.perf_counter()
+    oh = O.Hierarchy(sys_.rp, sys_.ci, sys_.val)
+    t_setup = time.perf_counter() - t0
+    _, info = oh.pcg(sys_.b, rtol=RTOL, flexible=True)
+    iters = info.iterations
+    for _ in range(max(0, args.warmup - 1)):
+        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
+        ts.append(time.perf_counter() - t0)
+    t_iter = statistics.mean(ts)
+    t_solve = t_setup + iters * t_iter
+    value = 1.0 / t_solve
+    sample = (f"oracle setup of the full system ({t_setup:.2f} s, measured once) + {args.steps} timed one-iteration "
+              f"PCG samples ({t_iter:.3f} s each), extrapolated to the oracle's own {iters} iterations to 1e-8")
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": sys_.n, "nnz": sys_.nnz, "rtol": RTOL},
+        "time_to_solution_s": t_solve, "iterations": iters,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse_args()
+    from paper_2007_00056_gb300 import workloads as W
+
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        run_reference(args, W.lognormal3d(args.grid, seed=1))
+        return
+
+    rank, world, local = dist_setup(args)
+    import numpy as np
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    amg.lib(build_if_missing=True)
+    sys_ = W.lognormal3d(args.grid, seed=1)
+    rp = torch.from_numpy(sys_.rp).to(dev)
+    ci = torch.from_numpy(sys_.ci).to(dev)
+    val = torch.from_numpy(sys_.val).to(dev)
+    b = torch.from_numpy(sys_.b).to(dev)
+    x = torch.zeros_like(b)
+    params = amg.amg_default_params()
+    stream = torch.cuda.current_stream()
+
+    def step(profile=False):
+        h = amg.amg_setup(rp, ci, val, params)
+        if profile:
+            amg.amg_profile_enable(h, True)
+        x.zero_()
+        ev_mid = torch.cuda.Event(enable_timing=True)
+        ev_mid.record(stream)
+        info = amg.pcg_solve(h, b, x, rtol=RTOL, max_iter=1000, flexible=True)
+        return h, info, ev_mid
+
+    # warm-up
+    for _ in range(max(args.warmup, 1)):
+        h, info, _ = step()
+        h.close()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = amg.amg_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    setup_ms, iters = [], []
+    ev0.record(stream)
+    last = ev0
+    for _ in range(args.steps):
+        h, info, ev_mid = step()
+        ev_end = torch.cuda.Event(enable_timing=True)
+        ev_end.record(stream)
+        setup_ms.append((last, ev_mid))
+        iters.append(info.iterations)
+        if info.status != amg.AMG_OK:
+            raise RuntimeError(f"PCG did not converge: {info}")
+        h.close()
+        last = ev_end
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = amg.amg_kernel_launches() - launches0
+    clocks = sampler.stop() if sampler else None
+    total_ms = ev0.elapsed_time(ev1)
+    setup_t = [a.elapsed_time(bv) for a, bv in setup_ms]
+    max_ms = allreduce_max(total_ms, world)
+    ms_per_step = max_ms / args.steps
+    value = world * args.steps / (max_ms * 1e-3)
+    setup_mean = statistics.mean(setup_t)
+    solve_mean = ms_per_step - setup_mean
+
+    # live per-kernel timing of the same step (CUDA events on the launching stream)
+    peak, peak_kind = measured_peaks()
+    table_acc = {}
+    vc_bytes = vc_ms = 0.0
+    for _ in range(args.profile_steps):
+        h, info, _ = step(profile=True)
+        for r in amg.amg_profile_table(h):
+            key = (r["kind"], r["level"])
+            acc = table_acc.setdefault(key, dict(kind=r["kind"], level=r["level"], ms=0.0, bytes=0.0, launches=0))
+            acc["ms"] += r["ms"]
+            acc["bytes"] += r["bytes"]
+            acc["launches"] += r["launches"]
+        levels = h.sizes()
+        h.close()
+    table = sorted(table_acc.values(), key=lambda r: -r["ms"])
+    vcycle_kinds = {"jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
+                    "coarse_cg", "cast"}
+    for r in table:
+        if r["kind"] in vcycle_kinds:
+            vc_bytes += r["bytes"]
+            vc_ms += r["ms"]
+    top = table[0] if table else None
+    roofline = None
+    if top:
+        per_launch_bytes = top["bytes"] / top["launches"]
+        per_launch_ms = top["ms"] / top["launches"]
+        achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{top['kind']}@level{top['level']}", "achieved": achieved,
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": peak_kind, "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+    kernels = [dict(kernel=f"{r['kind']}@{r['level']}", ms_per_step=r["ms"] / args.profile_steps,
+                    launches_per_step=r["launches"] / args.profile_steps,
+                    gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:12]]
+
+    # end to end through the public API from pinned host buffers
+    h_rp = torch.from_numpy(sys_.rp).pin_memory()
+    h_ci = torch.from_numpy(sys_.ci).pin_memory()
+    h_val = torch.from_numpy(sys_.val).pin_memory()
+    h_b = torch.from_numpy(sys_.b).pin_memory()
+    h_x = torch.empty_like(h_b).pin_memory()
+    d_rp, d_ci, d_val, d_b = (torch.empty_like(t, device=dev) for t in (h_rp, h_ci, h_val, h_b))
+    h2d = sum(t.numel() * t.element_size() for t in (h_rp, h_ci, h_val, h_b))
+    d2h = h_x.numel() * h_x.element_size()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        for d, hsrc in ((d_rp, h_rp), (d_ci, h_ci), (d_val, h_val), (d_b, h_b)):
+            d.copy_(hsrc, non_blocking=True)
+        he = amg.amg_setup(d_rp, d_ci, d_val, params)
+        xe = torch.zeros_like(d_b)
+        inf = amg.pcg_solve(he, d_b, xe, rtol=RTOL, max_iter=1000, flexible=True)
+        h_x.copy_(xe, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        he.close()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
+    e2e_value = world * args.e2e_steps / (e2e_ms * 1e-3)
+
+    # CPU baseline: the oracle on this host's cores (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oh, t_setup, ts = oracle_setup_and_iter_times(sys_, 3)
+        it_gpu = int(round(statistics.mean(iters)))
+        t_solve = t_setup + it_gpu * statistics.mean(ts)
+        cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": (f"oracle setup of the full 128^3 system ({t_setup:.2f} s) + 3 one-iteration PCG "
+                          f"samples ({statistics.mean(ts):.3f} s each), extrapolated to {it_gpu} iterations"),
+               "time_to_solution_s": t_solve}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": sys_.n, "nnz": sys_.nnz, "rtol": RTOL, "precision": "fp64",
+                       "krylov": "flexible PCG", "levels": levels, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (level-0 CSR 183 MB > 129 MB); no flush"},
+            "time_to_solution_ms": ms_per_step, "setup_ms": setup_mean, "solve_ms": solve_mean,
+            "iterations": iters[0],
+            "vcycle": {"gbs": vc_bytes / (vc_ms * 1e-3) / 1e9 if vc_ms > 0 else None,
+                       "ms_per_step": vc_ms / max(1, args.profile_steps), "peak": peak,
+                       "frac": (vc_bytes / (vc_ms * 1e-3) / 1e9) / peak if vc_ms > 0 else None},
+            "roofline": roofline, "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

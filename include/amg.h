@@ -1,0 +1,207 @@
+/*
+ * amg.h -- C ABI of the GB300 aggregation-AMG preconditioned Krylov library.
+ *
+ * Method: Ganesan & Shah, "SParSH-AMG: a library for hybrid CPU-GPU algebraic
+ * multigrid and preconditioned iterative methods" (arXiv 2007.00056):
+ *   - problem statement A u = f, A sparse N x N in CSR (Sec. 2, Sec. 2.1);
+ *   - setup: pairwise heavy-edge matching (Sec. 2.1.1-2.1.2, Algorithms 2-3),
+ *     piecewise-constant prolongation P, Galerkin A_c = P^T A P (Sec. 2.1.1),
+ *     coarsest factorisation once (Sec. 2), all split from the solve (Sec. 3);
+ *   - solve: V-cycle (Algorithm 1), AMG-preconditioned CG (Algorithm 4) and
+ *     BiCG(Stab) (Algorithm 5), stopping on ||b - A x||_2 (Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers on the current CUDA device
+ *     (for example torch tensors' data_ptr()).  No entry point reads host
+ *     arrays except where stated (amg_params, amg_solve_info are host structs).
+ *   - CSR: 0-based, int32 row pointers (n+1) and column indices (nnz), columns
+ *     strictly ascending within each row, square n x n, values FP64.
+ *   - Work is ordered on the caller's stream; functions that return results
+ *     on the host (solver info, level sizes) synchronise that stream.
+ *   - The caller owns every array it passes.  amg_setup copies A; the
+ *     hierarchy owns all of its device memory until amg_destroy.
+ *   - No function throws, aborts or traps.  Each returns an amg_status; on an
+ *     error the output arrays are unspecified.  Device-side waits are bounded
+ *     and report AMG_ERR_TIMEOUT instead of hanging.
+ *   - One hierarchy serves any number of right-hand sides, one call at a
+ *     time: calls on the same hierarchy share its work vectors and must not
+ *     overlap on the GPU.  Different hierarchies are independent.
+ */
+#ifndef AMG_GB300_H
+#define AMG_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *amg_stream_t; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  AMG_OK = 0,
+  AMG_ERR_INVALID_ARG = 1,   /* null pointer, negative size, bad parameter, NaN/Inf input */
+  AMG_ERR_INVALID_CSR = 2,   /* row pointers / column indices violate the CSR conventions */
+  AMG_ERR_ZERO_DIAG = 3,     /* a row of some level has no (or a zero) diagonal entry */
+  AMG_ERR_OOM = 4,           /* device allocation failed */
+  AMG_ERR_BREAKDOWN = 5,     /* Krylov breakdown: a denominator vanished or became non-finite */
+  AMG_ERR_NOT_CONVERGED = 6, /* max_iter reached before the tolerance (x still holds the last iterate) */
+  AMG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
+  AMG_ERR_CUDA = 8,          /* a CUDA runtime call failed */
+  AMG_ERR_UNSUPPORTED = 9    /* valid input outside what this build implements */
+} amg_status;
+
+typedef enum {
+  AMG_FP64 = 0,          /* hierarchy values and V-cycle in FP64 */
+  AMG_FP32 = 1,          /* values rounded to FP32 after the FP64 setup; V-cycle in FP32 */
+  AMG_FP16_STORAGE = 2   /* D^-1/2 A D^-1/2 values stored in FP16, FP32 arithmetic */
+} amg_precision;
+
+typedef enum { AMG_COARSE_AUTO = 0, AMG_COARSE_DENSE = 1, AMG_COARSE_CG = 2 } amg_coarse_solver;
+
+/* Setup and cycle parameters (amg_default_params fills the defaults).
+ *   passes       pairwise matching passes per level (2: aggregates of <= 4; Table 2 /
+ *                "pairwise, 2 passes")
+ *   max_levels   levels including the finest (10; the paper's Table 2 uses 6)
+ *   coarse_max   stop coarsening once a level has <= coarse_max rows; also the
+ *                largest coarsest level solved by a dense factorisation (4096)
+ *   stall_ratio  do not add a level whose size ratio N_{k+1}/N_k exceeds this (0.85)
+ *   omega        damped-Jacobi weight of the smoother S_k (2/3)
+ *   nu_pre, nu_post  pre- and post-smoothing sweeps (1, 1; Table 2 uses 6, 6)
+ *   coarse_solver    AMG_COARSE_AUTO: dense if the coarsest level has <= coarse_max
+ *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2)
+ *   precision    value storage / arithmetic of the V-cycle (outer Krylov is FP64) */
+typedef struct {
+  int passes;
+  int max_levels;
+  int coarse_max;
+  double stall_ratio;
+  double omega;
+  int nu_pre;
+  int nu_post;
+  int coarse_solver;
+  int precision;
+} amg_params;
+
+/* Result of a Krylov solve.  iterations counts completed iterations (a
+ * BiCGStab half step that meets the tolerance counts as one).
+ * rel_res_recurrence is ||r||_2/||b||_2 of the recurrence residual at exit,
+ * rel_res_true is ||b - A x||_2/||b||_2 recomputed from x. */
+typedef struct {
+  int iterations;
+  double rel_res_recurrence;
+  double rel_res_true;
+  amg_status status;
+} amg_solve_info;
+
+typedef struct amg_hierarchy amg_hierarchy; /* opaque, device-resident */
+
+/* Fills *p with the defaults listed above.  AMG_ERR_INVALID_ARG if p is NULL. */
+amg_status amg_default_params(amg_params *p);
+
+/* Setup phase (Sec. 3; coarsening Sec. 2.1, Algorithms 2-3; Galerkin Sec. 2.1.1).
+ * Builds the hierarchy of A (n rows, nnz stored entries, device CSR arrays) on
+ * the device: for each level, `passes` rounds-to-fixed-point of mutual-
+ * heaviest-neighbour handshakes (edge weight max(|a_ij|,|a_ji|), equal weights
+ * broken toward the smaller index; unmatched nodes stay single), aggregate ids
+ * by smallest member, A_{k+1} = P^T A_k P with a fixed summation order; then
+ * the coarsest solver (dense inverse, or CG).  params may be NULL (defaults).
+ * The pattern of A must be structurally symmetric (AMG_ERR_UNSUPPORTED
+ * otherwise).  On success *out owns a new hierarchy; on failure *out = NULL.
+ * Errors: INVALID_ARG (n <= 0, nnz < 0, NULL pointers, bad params),
+ * INVALID_CSR, ZERO_DIAG, OOM, CUDA, TIMEOUT, UNSUPPORTED. */
+amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                     const double *d_val, const amg_params *params, amg_stream_t stream,
+                     amg_hierarchy **out);
+
+/* One V-cycle from a zero initial guess (Algorithm 1 with x_0 = 0, as used
+ * for z = M^{-1} r in Algorithms 4-5): d_z = M^{-1} d_r, both length n.  The
+ * two arrays must not overlap.  In FP32 / FP16-storage precision the input
+ * is rounded to FP32 and the output widened back to FP64. */
+amg_status amg_vcycle(const amg_hierarchy *h, const double *d_r, double *d_z, amg_stream_t stream);
+
+/* AMG-preconditioned CG (Sec. 3.2, Algorithm 4; residual update read as
+ * r_{j+1} = r_j - alpha A p_j).  d_x holds x_0 on entry, the solution on exit.
+ * Stops when ||r||_2 <= rtol ||b||_2 (recurrence residual) or after max_iter
+ * iterations.  flexible != 0 uses beta = (z_{j+1}, r_{j+1} - r_j)/(z_j, r_j),
+ * which stays valid when M varies slightly (mixed precision, CG coarse solve).
+ * rtol = 0 runs exactly max_iter iterations unless r becomes exactly zero.
+ * b = 0 gives x = 0 and 0 iterations.  info may be NULL.
+ * Errors: INVALID_ARG, BREAKDOWN, NOT_CONVERGED, TIMEOUT, CUDA. */
+amg_status pcg_solve(const amg_hierarchy *h, const double *d_b, double *d_x, double rtol,
+                     int max_iter, int flexible, amg_stream_t stream, amg_solve_info *info);
+
+/* AMG-preconditioned BiCGStab (Sec. 3.2, Algorithm 5), right preconditioned,
+ * rbar_0 = r_0 and p_0 = r_0; p_{j+1} = r_{j+1} + beta (p_j - omega A p~_j).
+ * A half step whose ||s|| meets rtol ends the solve with x += alpha p~.
+ * Same argument and error conventions as pcg_solve. */
+amg_status bicgstab_solve(const amg_hierarchy *h, const double *d_b, double *d_x, double rtol,
+                          int max_iter, amg_stream_t stream, amg_solve_info *info);
+
+/* Number of levels (finest included) of h, or -1 if h is NULL. */
+int amg_num_levels(const amg_hierarchy *h);
+
+/* Size of level k (0 = finest): *n rows and *nnz stored entries (either
+ * pointer may be NULL).  d_agg_out, if not NULL, receives the level's
+ * fine-to-coarse aggregate map (length n, ids in [0, n_{k+1})); it must be
+ * NULL for the coarsest level.  Synchronises the stream. */
+amg_status amg_level_info(const amg_hierarchy *h, int level, int *n, int64_t *nnz,
+                          int32_t *d_agg_out, amg_stream_t stream);
+
+/* Copies level k's CSR (FP64 values) into caller arrays of sizes n+1, nnz, nnz. */
+amg_status amg_export_level(const amg_hierarchy *h, int level, int32_t *d_row_ptr, int32_t *d_col,
+                            double *d_val, amg_stream_t stream);
+
+/* Handshake rounds run by pass p of level k during setup (the final round that
+ * matched nothing included), or -1 if out of range. */
+int amg_setup_rounds(const amg_hierarchy *h, int level, int pass);
+
+/* ---- Instrumentation (no counterpart in the paper; used for measurement) ---- */
+
+/* Kernel kinds reported by the per-kernel profiler.  Each kind is tracked per
+ * level (0 = finest); Krylov kinds are reported at level 0. */
+typedef enum {
+  AMG_K_JACOBI0 = 0,        /* first presmoothing sweep from x = 0 (vector pass)      */
+  AMG_K_JACOBI = 1,         /* further damped-Jacobi sweeps (matrix pass)              */
+  AMG_K_RESIDUAL = 2,       /* t = f - A x (matrix pass)                               */
+  AMG_K_RESTRICT = 3,       /* f_{k+1} = P^T t                                         */
+  AMG_K_PROLONG_JACOBI = 4, /* x + P x_{k+1} fused with the first postsmoothing sweep  */
+  AMG_K_PROLONG = 5,        /* x + P x_{k+1} alone (nu_post = 0)                       */
+  AMG_K_COARSE_DENSE = 6,   /* coarsest solve, dense inverse times vector              */
+  AMG_K_COARSE_CG = 7,      /* coarsest solve, persistent Jacobi-PCG                   */
+  AMG_K_CAST = 8,           /* FP64 <-> FP32 conversions of the mixed-precision cycle  */
+  AMG_K_KRYLOV_SPMV = 9,    /* outer Krylov SpMV with fused dot products               */
+  AMG_K_KRYLOV_VEC = 10     /* outer Krylov vector updates with fused dot products     */
+} amg_kernel_kind;
+
+/* Total kernel launches this library has issued since it was loaded (a graph
+ * replay counts each kernel it runs). */
+unsigned long long amg_kernel_launches(void);
+
+/* Turns per-launch CUDA-event timing of the solve phase on (on != 0) or off.
+ * While on, Krylov iterations run as direct launches rather than graph
+ * replays.  AMG_ERR_INVALID_ARG if h is NULL. */
+amg_status amg_profile_enable(amg_hierarchy *h, int on);
+
+/* Clears the accumulated timings of h. */
+amg_status amg_profile_reset(amg_hierarchy *h);
+
+/* Accumulated totals for one kernel kind at one level since the last reset:
+ * device milliseconds (sum over launches, CUDA events on the launching
+ * stream), algorithmic bytes (sum over launches: what the kernel must read and
+ * write, each vector entry counted once) and launch count.  Any output pointer
+ * may be NULL.  Waits for pending timed launches. */
+amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, double *bytes, long long *launches);
+
+/* Frees every device allocation of h (NULL is a no-op).  Synchronises the
+ * device work of h first. */
+void amg_destroy(amg_hierarchy *h);
+
+/* Static English text for a status code. */
+const char *amg_status_string(amg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_GB300_H */

@@ -1,0 +1,187 @@
+// api.cu -- small C-ABI entry points and host helpers shared by the library.
+#include <cstring>
+
+#include "common.cuh"
+
+unsigned long long g_amg_launches = 0;
+
+void prof_begin(amg_hierarchy *h, cudaStream_t s, int id, double bytes) {
+  Profiler &p = h->prof;
+  if (p.pool.size() < 2) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+      p.pool.push_back(e);
+    }
+  }
+  Profiler::Rec r;
+  r.id = id;
+  r.bytes = bytes;
+  r.a = p.pool.back(); p.pool.pop_back();
+  r.b = p.pool.back(); p.pool.pop_back();
+  cudaEventRecord(r.a, s);
+  p.pending.push_back(r);
+}
+
+void prof_end(amg_hierarchy *h, cudaStream_t s) {
+  Profiler &p = h->prof;
+  if (!p.pending.empty()) cudaEventRecord(p.pending.back().b, s);
+}
+
+// Accumulates the timings of every recorded launch (waits for them).
+amg_status prof_flush(amg_hierarchy *h) {
+  Profiler &p = h->prof;
+  for (auto &r : p.pending) {
+    cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess && r.id >= 0 && r.id < AMG_PROF_IDS) {
+      p.ms[r.id] += ms;
+      p.bytes[r.id] += r.bytes;
+      p.launches[r.id] += 1;
+    }
+    cudaGetLastError();
+    p.pool.push_back(r.a);
+    p.pool.push_back(r.b);
+  }
+  p.pending.clear();
+  return AMG_OK;
+}
+
+amg_status amg_cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return AMG_OK;
+  if (e == cudaErrorMemoryAllocation) return AMG_ERR_OOM;
+  return AMG_ERR_CUDA;
+}
+
+amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return AMG_ERR_OOM;
+  }
+  h->allocs.push_back(*p);
+  return AMG_OK;
+}
+
+// Reads and clears the device error bits (synchronises the stream).
+amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags) {
+  AMG_CUDA(cudaMemcpyAsync(h->eflags_host, h->eflags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  *flags = h->eflags_host[0];
+  if (*flags) AMG_CUDA(cudaMemsetAsync(h->eflags, 0, sizeof(unsigned), s));
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_default_params(amg_params *p) {
+  if (!p) return AMG_ERR_INVALID_ARG;
+  p->passes = 2;
+  p->max_levels = 10;
+  p->coarse_max = 4096;
+  p->stall_ratio = 0.85;
+  p->omega = 2.0 / 3.0;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->coarse_solver = AMG_COARSE_AUTO;
+  p->precision = AMG_FP64;
+  return AMG_OK;
+}
+
+extern "C" const char *amg_status_string(amg_status s) {
+  switch (s) {
+    case AMG_OK: return "ok";
+    case AMG_ERR_INVALID_ARG: return "invalid argument";
+    case AMG_ERR_INVALID_CSR: return "invalid CSR structure";
+    case AMG_ERR_ZERO_DIAG: return "zero or missing diagonal entry";
+    case AMG_ERR_OOM: return "device out of memory";
+    case AMG_ERR_BREAKDOWN: return "Krylov breakdown";
+    case AMG_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case AMG_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AMG_ERR_CUDA: return "CUDA runtime error";
+    case AMG_ERR_UNSUPPORTED: return "unsupported input or option";
+  }
+  return "unknown status";
+}
+
+extern "C" int amg_num_levels(const amg_hierarchy *h) { return h ? h->L + 1 : -1; }
+
+extern "C" amg_status amg_level_info(const amg_hierarchy *h, int level, int *n, int64_t *nnz, int32_t *d_agg_out,
+                                     amg_stream_t stream) {
+  if (!h || level < 0 || level > h->L) return AMG_ERR_INVALID_ARG;
+  if (d_agg_out && level == h->L) return AMG_ERR_INVALID_ARG;
+  const Level &l = h->lev[level];
+  if (n) *n = l.n;
+  if (nnz) *nnz = l.nnz;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (d_agg_out) {
+    AMG_CUDA(cudaMemcpyAsync(d_agg_out, l.agg, sizeof(int32_t) * l.n, cudaMemcpyDeviceToDevice, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+  }
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_export_level(const amg_hierarchy *h, int level, int32_t *d_row_ptr, int32_t *d_col,
+                                       double *d_val, amg_stream_t stream) {
+  if (!h || level < 0 || level > h->L || !d_row_ptr) return AMG_ERR_INVALID_ARG;
+  const Level &l = h->lev[level];
+  if (l.nnz > 0 && (!d_col || !d_val)) return AMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  AMG_CUDA(cudaMemcpyAsync(d_row_ptr, l.rp, sizeof(int32_t) * (l.n + 1), cudaMemcpyDeviceToDevice, s));
+  if (l.nnz > 0) {
+    AMG_CUDA(cudaMemcpyAsync(d_col, l.ci, sizeof(int32_t) * l.nnz, cudaMemcpyDeviceToDevice, s));
+    AMG_CUDA(cudaMemcpyAsync(d_val, l.val, sizeof(double) * l.nnz, cudaMemcpyDeviceToDevice, s));
+  }
+  AMG_CUDA(cudaStreamSynchronize(s));
+  return AMG_OK;
+}
+
+extern "C" void amg_destroy(amg_hierarchy *h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  if (h->g_vcycle) cudaGraphExecDestroy(h->g_vcycle);
+  if (h->g_pcg) cudaGraphExecDestroy(h->g_pcg);
+  if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
+  prof_flush(h);
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->eflags_host) cudaFreeHost(h->eflags_host);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaGetLastError();
+  delete h;
+}
+
+extern "C" unsigned long long amg_kernel_launches(void) { return __atomic_load_n(&g_amg_launches, __ATOMIC_RELAXED); }
+
+extern "C" amg_status amg_profile_enable(amg_hierarchy *h, int on) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  prof_flush(h);
+  h->prof.on = on != 0;
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_profile_reset(amg_hierarchy *h) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  prof_flush(h);
+  for (int i = 0; i < AMG_PROF_IDS; ++i) { h->prof.ms[i] = 0; h->prof.bytes[i] = 0; h->prof.launches[i] = 0; }
+  if (h->cg.iters_total) cudaMemset(h->cg.iters_total, 0, sizeof(unsigned long long));
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, double *bytes,
+                                       long long *launches) {
+  if (!h || kind < 0 || kind >= PK_COUNT || level < 0 || level >= AMG_MAX_LEVELS) return AMG_ERR_INVALID_ARG;
+  prof_flush(h);
+  int id = kind * AMG_MAX_LEVELS + level;
+  double b = h->prof.bytes[id];
+  if (kind == PK_COARSE_CG && h->cg.iters_total) {
+    // bytes of the coarse CG depend on its iteration count, summed on the device
+    unsigned long long it = 0;
+    cudaMemcpy(&it, h->cg.iters_total, sizeof(it), cudaMemcpyDeviceToHost);
+    b = h->prof.launches[id] > 0 ? (double)it * (h->prof.bytes[id] / (double)h->prof.launches[id]) : 0.0;
+  }
+  if (ms) *ms = h->prof.ms[id];
+  if (bytes) *bytes = b;
+  if (launches) *launches = h->prof.launches[id];
+  return AMG_OK;
+}

@@ -1,0 +1,252 @@
+// common.cuh -- internal declarations of the GB300 aggregation-AMG library.
+//
+// Device data layout (all in HBM, owned by the hierarchy):
+//   level k:  rp[n+1], ci[nnz] (int32), val[nnz] (FP64) + val32[nnz] (FP32
+//             copy for the mixed-precision V-cycle) + val16/dscale (FP16
+//             storage of D^-1/2 A D^-1/2), dinv[n] = 1/a_ii (FP64 and FP32);
+//             agg[n] fine->coarse map and the member lists of every coarse
+//             aggregate (mrp[n_c+1], mem[n]; members ascending) for k < L;
+//             per-level V-cycle vectors f, x, t.
+//   coarsest: dense inverse A_L^{-1} (row-major FP64) or the coarse-CG work
+//             vectors.
+//   Krylov:   level-0 FP64 work vectors and a device-resident scalar block
+//             (KState) so an iteration runs without host round trips.
+// Every CSR array is padded by AMG_PAD elements so that vector loads of a
+// tile never leave the allocation.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "amg.h"
+
+#define AMG_MAX_LEVELS 32
+#define AMG_MAX_PASSES 8
+#define AMG_PAD 64
+#define AMG_THREADS 256
+#define AMG_MAX_BLOCKS 2432  // 152 SMs x 16 resident 256-thread blocks (upper bound of any grid)
+
+// Device error flags (bit set, read back by the host at the next sync point).
+#define AMG_EFLAG_ZERO_DIAG 1u
+#define AMG_EFLAG_NONSYM 2u
+#define AMG_EFLAG_TIMEOUT 4u
+#define AMG_EFLAG_BAD_CSR 8u
+#define AMG_EFLAG_BREAKDOWN 16u
+#define AMG_EFLAG_NONFINITE 32u
+
+// Krylov state held on the device; kernels read the scalars they need and the
+// reduction finalisers write the next ones.  `done` makes every later kernel
+// of the solve a no-op, so the host can enqueue several iterations at once.
+struct KState {
+  double rz, pq, alpha, beta, omega, rho, bnorm, rel, rtol, srel, rel_true;
+  int it, max_iter, done, status, flexible, half;
+};
+
+struct Level {
+  int n = 0;
+  int64_t nnz = 0;
+  int32_t *rp = nullptr, *ci = nullptr;
+  double *val = nullptr, *dinv = nullptr;
+  float *val32 = nullptr, *dinv32 = nullptr;
+  __half *val16 = nullptr;   // values of D^-1/2 A D^-1/2
+  float *dsq = nullptr;      // d_i^{-1/2}
+  int32_t *agg = nullptr;    // n, into level k+1
+  int32_t *mrp = nullptr;    // n_{k+1}+1
+  int32_t *mem = nullptr;    // n
+  double *f = nullptr, *x = nullptr, *t = nullptr, *y = nullptr;
+  float *f32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
+  int rounds[AMG_MAX_PASSES] = {0};
+  int tpr = 1;               // threads per row of this level's row kernels
+};
+
+// Kernel kinds of the per-kernel profiler (id = kind * AMG_MAX_LEVELS + level).
+enum ProfKind {
+  PK_JACOBI0 = 0, PK_JACOBI, PK_RESIDUAL, PK_RESTRICT, PK_PROLONG_JACOBI, PK_PROLONG, PK_COARSE_DENSE,
+  PK_COARSE_CG, PK_CAST, PK_KRYLOV_SPMV, PK_KRYLOV_VEC, PK_COUNT
+};
+#define AMG_PROF_IDS (PK_COUNT * AMG_MAX_LEVELS)
+
+// Optional CUDA-event timing of every solve-phase launch (off by default;
+// while on, iterations run as direct launches instead of graph replays).
+struct Profiler {
+  bool on = false;
+  struct Rec { int id; double bytes; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  double ms[AMG_PROF_IDS] = {0};
+  double bytes[AMG_PROF_IDS] = {0};
+  long long launches[AMG_PROF_IDS] = {0};
+};
+
+struct CoarseCG {
+  int n = 0, grid = 0;
+  unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
+  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *p2 = nullptr, *q = nullptr, *part = nullptr;
+  unsigned *bar = nullptr;   // [0] arrival counter, [1] generation
+  int *iters = nullptr;
+};
+
+struct amg_hierarchy {
+  amg_params prm{};
+  int device = 0;
+  int num_sms = 152;
+  int L = 0;                 // index of the coarsest level
+  Level lev[AMG_MAX_LEVELS];
+  int dense = 0;
+  double *ainv = nullptr;    // n_L x n_L, row-major
+  CoarseCG cg;
+  // Krylov work vectors (level 0, FP64)
+  double *kb = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
+  double *krold = nullptr, *ks = nullptr, *kt = nullptr, *krb = nullptr, *kph = nullptr, *ksh = nullptr;
+  double *part = nullptr;    // reduction partials, 8 x AMG_MAX_BLOCKS
+  unsigned *counter = nullptr;  // last-block counters, 8 slots
+  KState *st = nullptr;      // device
+  KState *st_host = nullptr; // pinned host mirror
+  unsigned *eflags = nullptr;   // device error bits
+  unsigned *eflags_host = nullptr;
+  std::vector<void *> allocs;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr;
+  long long g_pcg_nodes = 0, g_bicg_nodes = 0;
+  int graphs_ok = 1;
+  Profiler prof;
+};
+
+// Kernel launches issued by this library since it was loaded (graph replays
+// count every kernel node they run).
+extern unsigned long long g_amg_launches;
+static inline void count_launch(long long k = 1) { __atomic_add_fetch(&g_amg_launches, (unsigned long long)k, __ATOMIC_RELAXED); }
+
+void prof_begin(amg_hierarchy *h, cudaStream_t s, int id, double bytes);
+void prof_end(amg_hierarchy *h, cudaStream_t s);
+amg_status prof_flush(amg_hierarchy *h);
+// Brackets one launch: counts it and, when profiling is on, times it.
+struct LaunchScope {
+  amg_hierarchy *h;
+  cudaStream_t s;
+  bool on;
+  LaunchScope(amg_hierarchy *h_, cudaStream_t s_, int kind, int level, double bytes)
+      : h(h_), s(s_), on(h_ != nullptr && h_->prof.on) {
+    count_launch();
+    if (on) prof_begin(h, s, kind * AMG_MAX_LEVELS + level, bytes);
+  }
+  ~LaunchScope() {
+    if (on) prof_end(h, s);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Host helpers (defined in api.cu)
+// ---------------------------------------------------------------------------
+amg_status amg_cuda_status(cudaError_t e);
+amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes);
+#define AMG_TRY(x)                              \
+  do {                                          \
+    amg_status _s = (x);                        \
+    if (_s != AMG_OK) return _s;                \
+  } while (0)
+#define AMG_CUDA(x)                             \
+  do {                                          \
+    cudaError_t _e = (x);                       \
+    if (_e != cudaSuccess) return amg_cuda_status(_e); \
+  } while (0)
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+static inline int grid_for(long long n, int per_block, int max_blocks = AMG_MAX_BLOCKS) {
+  long long g = (n + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// Shared device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of NV per-thread values over the block, fixed tree order; result valid in
+// thread 0.  sh must hold NV * 32 doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nw ? sh[k * 32 + lane] : 0.0;
+      v[k] = warp_sum(s);
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic grid reduction: every block stores its NV partial sums in
+// part[k * gridDim.x + blockIdx.x]; the last block to arrive (by an atomic
+// counter) sums the partials in index order and returns true with the totals
+// in `tot` (valid in thread 0 of that block).  The counter is reset for reuse.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double *part, unsigned *counter,
+                                              double (&tot)[NV]) {
+  __shared__ double sh[NV * 32];
+  __shared__ bool last;
+  block_sum<NV>(v, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * gridDim.x + blockIdx.x] = v[k];
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double s[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    s[k] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s[k] += __ldcg(&part[k * gridDim.x + b]);
+  }
+  block_sum<NV>(s, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) tot[k] = s[k];
+    *counter = 0u;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool is_done(const KState *st) {
+  return st != nullptr && *((volatile const int *)&st->done) != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Cross-TU host entry points
+// ---------------------------------------------------------------------------
+// V-cycle of level `k` with right-hand side f and output x (FP64 or FP32 per
+// the hierarchy's precision); `st` may be a Krylov state whose done flag
+// turns every kernel into a no-op.
+amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st);
+amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s);
+amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
+amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
+amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
+void launch_residual_f64(const Level &l, const double *b, const double *x, double *r, cudaStream_t s);

@@ -1,0 +1,744 @@
+// setup.cu -- device setup phase (Sec. 3 "setup phase"; coarsening Sec. 2.1).
+//
+// Per level: `passes` pairwise heavy-edge matchings, each run as synchronous
+// rounds of mutual-heaviest-neighbour handshakes until a round pairs nothing
+// (the fixed point equals the greedy edge-order matching of Algorithm 3 with
+// ties broken toward the smaller index), aggregate ids by smallest member,
+// and the Galerkin product A_c = P^T A P (Sec. 2.1.1) with a fixed summation
+// order: coarse row I, its members ascending, each member row in stored order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+#define HEM_FREE (-2)
+
+// ---------------------------------------------------------------------------
+// CSR checks and diagonal
+// ---------------------------------------------------------------------------
+__global__ void k_check_csr(int n, long long nnz, const int32_t *__restrict__ rp,
+                            const int32_t *__restrict__ ci, unsigned *eflags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && (rp[0] != 0 || (long long)rp[n] != nnz)) atomicOr(eflags, AMG_EFLAG_BAD_CSR);
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  if (b < 0 || e < b || (long long)e > nnz) { atomicOr(eflags, AMG_EFLAG_BAD_CSR); return; }
+  int prev = -1;
+  for (int k = b; k < e; ++k) {
+    int c = ci[k];
+    if (c < 0 || c >= n || c <= prev) { atomicOr(eflags, AMG_EFLAG_BAD_CSR); return; }
+    prev = c;
+  }
+}
+
+__device__ __forceinline__ int find_col(const int32_t *ci, int b, int e, int j) {
+  int lo = b, hi = e - 1;
+  while (lo <= hi) {
+    int mid = (lo + hi) >> 1;
+    int c = ci[mid];
+    if (c == j) return mid;
+    if (c < j) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+// dinv_i = 1 / a_ii; a missing, zero or non-finite diagonal sets a flag.
+__global__ void k_diag(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ val, double *dinv, unsigned *eflags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int p = find_col(ci, rp[i], rp[i + 1], i);
+  double d = p >= 0 ? val[p] : 0.0;
+  if (d == 0.0 || !isfinite(d)) { atomicOr(eflags, AMG_EFLAG_ZERO_DIAG); dinv[i] = 0.0; return; }
+  dinv[i] = 1.0 / d;
+}
+
+__global__ void k_nonfinite(long long nnz, const double *__restrict__ val, unsigned *eflags) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
+       e += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(val[e])) { atomicOr(eflags, AMG_EFLAG_NONFINITE); return; }
+}
+
+// ---------------------------------------------------------------------------
+// Edge weights: w_e = max(|a_ij|, |a_ji|) for e = (i, j), j != i; 0 = no edge.
+// (Sec. 2.1: a_ij is the edge weight; Algorithm 3 lists both directions.)
+// ---------------------------------------------------------------------------
+__global__ void k_weights(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ val, double *__restrict__ w, unsigned *eflags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    int j = ci[e];
+    if (j == i) { w[e] = 0.0; continue; }
+    int q = find_col(ci, rp[j], rp[j + 1], i);
+    if (q < 0) { atomicOr(eflags, AMG_EFLAG_NONSYM); w[e] = fabs(val[e]); continue; }
+    w[e] = fmax(fabs(val[e]), fabs(val[q]));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Handshake rounds
+// ---------------------------------------------------------------------------
+__global__ void k_hem_init(int n, int32_t *mate, int32_t *frontier) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { mate[i] = HEM_FREE; frontier[i] = i; }
+}
+
+// Each free node of the frontier picks its heaviest free neighbour (equal
+// weights: smaller index); -1 if it has none.
+__global__ void k_hem_pick(int nf, const int32_t *__restrict__ frontier, const int32_t *__restrict__ rp,
+                           const int32_t *__restrict__ ci, const double *__restrict__ w,
+                           const int32_t *__restrict__ mate, int32_t *__restrict__ pick) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nf) return;
+  int i = frontier[t];
+  int best = -1;
+  double bw = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    double we = w[e];
+    if (we <= 0.0) continue;
+    int j = ci[e];
+    if (mate[j] != HEM_FREE) continue;
+    // columns ascend, so on equal weight the first one met is the smaller index
+    if (best < 0 || we > bw) { best = j; bw = we; }
+  }
+  pick[i] = best;
+}
+
+// Mutual picks become pairs; nodes that still had a free neighbour stay in the
+// frontier.  cnt[0] += pairs formed, cnt[1] = size of the next frontier.
+__global__ void k_hem_match(int nf, const int32_t *__restrict__ frontier, const int32_t *__restrict__ pick,
+                            int32_t *__restrict__ mate, int32_t *__restrict__ next, int *cnt) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nf) return;
+  int i = frontier[t];
+  int j = pick[i];
+  if (j < 0) return;
+  if (pick[j] == i) {
+    mate[i] = j;
+    if (i < j) atomicAdd(&cnt[0], 1);
+  } else {
+    int slot = atomicAdd(&cnt[1], 1);
+    next[slot] = i;
+  }
+}
+
+__global__ void k_hem_finish(int n, int32_t *mate) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && mate[i] == HEM_FREE) mate[i] = -1;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of int32 (three kernels: tile scan, scan of tile sums, add)
+// ---------------------------------------------------------------------------
+#define SCAN_ITEMS 8
+#define SCAN_TILE (AMG_THREADS * SCAN_ITEMS)
+
+__device__ __forceinline__ int block_excl_scan(int v, int *sh, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;  // inclusive over warps
+  }
+  __syncthreads();
+  int warp_off = wid > 0 ? sh[wid - 1] : 0;
+  *total = sh[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return warp_off + x - v;
+}
+
+__global__ void k_scan_tile(const int *in, int *out, int n, int *tile_sums) {
+  __shared__ int sh[32];
+  int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int total;
+  int off = block_excl_scan(s, sh, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) out[base + k] = off;
+    off += v[k];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the tile sums in chunks, carrying the running total.
+__global__ void k_scan_sums(int *sums, int ntiles, int *total_out) {
+  __shared__ int sh[32];
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < ntiles ? sums[i] : 0;
+    int tot;
+    int ex = block_excl_scan(v, sh, &tot);
+    if (i < ntiles) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *sums) {
+  int base = blockIdx.x * SCAN_TILE;
+  int add = sums[blockIdx.x];
+  for (int k = threadIdx.x; k < SCAN_TILE; k += blockDim.x)
+    if (base + k < n) out[base + k] += add;
+}
+
+// out[0..n-1] = exclusive scan of in, out[n] (if write_last) and *d_total = sum.
+static void scan_excl(const int *in, int *out, int n, int *d_total, int *tiles, cudaStream_t s) {
+  int nt = cdiv(std::max(n, 1), SCAN_TILE);
+  k_scan_tile<<<nt, AMG_THREADS, 0, s>>>(in, out, n, tiles); count_launch();
+  k_scan_sums<<<1, 1024, 0, s>>>(tiles, nt, d_total); count_launch();
+  k_scan_add<<<nt, AMG_THREADS, 0, s>>>(out, n, tiles); count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Aggregate numbering: id = rank of the aggregate's smallest member
+// ---------------------------------------------------------------------------
+__global__ void k_agg_flags(int n, const int32_t *__restrict__ mate, int *flag) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) { int m = mate[i]; flag[i] = (m < 0 || i < m) ? 1 : 0; }
+}
+
+__global__ void k_agg_assign(int n, const int32_t *__restrict__ mate, const int *__restrict__ id,
+                             int32_t *__restrict__ agg, int32_t *__restrict__ first) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int m = mate[i];
+  if (m < 0 || i < m) { agg[i] = id[i]; first[id[i]] = i; }
+  else agg[i] = id[m];
+}
+
+// ---------------------------------------------------------------------------
+// Galerkin product of one pairwise pass: coarse row I has members i0 = first[I]
+// and i1 = mate[i0] (if paired, i1 > i0).  Its entries, in the order
+// (row i0 in stored order, then row i1 in stored order), map to coarse columns
+// J = agg[j]; distinct J are stored ascending, each value summed in that order
+// starting from its first contribution.  One warp per coarse row.
+// ---------------------------------------------------------------------------
+struct PairRow {
+  int b0, n0, b1, n1;
+  __device__ __forceinline__ int m() const { return n0 + n1; }
+  __device__ __forceinline__ int pos(int k) const { return k < n0 ? b0 + k : b1 + (k - n0); }
+};
+
+__device__ __forceinline__ PairRow pair_row(int I, const int32_t *first, const int32_t *mate, const int32_t *rp) {
+  PairRow r;
+  int i0 = first[I];
+  int i1 = mate[i0];
+  r.b0 = rp[i0];
+  r.n0 = rp[i0 + 1] - r.b0;
+  if (i1 > i0) { r.b1 = rp[i1]; r.n1 = rp[i1 + 1] - r.b1; }
+  else { r.b1 = 0; r.n1 = 0; }
+  return r;
+}
+
+template <bool FILL>
+__global__ void k_galerkin(int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ mate,
+                           const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ val, const int32_t *__restrict__ agg,
+                           int *__restrict__ count, const int32_t *__restrict__ rpc,
+                           int32_t *__restrict__ cic, double *__restrict__ valc) {
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += warps) {
+    PairRow r = pair_row(I, first, mate, rp);
+    const int m = r.m();
+    int distinct = 0;
+    const int out0 = FILL ? rpc[I] : 0;
+    if (m <= 32) {
+      // each lane holds one entry; compare through shuffles
+      int J = lane < m ? agg[ci[r.pos(lane)]] : 0x7fffffff;
+      double v = lane < m ? val[r.pos(lane)] : 0.0;
+      bool firstJ = lane < m;
+      int rank = 0;
+      double sum = v;
+      for (int k = 0; k < m; ++k) {
+        int Jk = __shfl_sync(0xffffffffu, J, k);
+        double vk = __shfl_sync(0xffffffffu, v, k);
+        if (k < lane && Jk == J) firstJ = false;
+        if (k > lane && Jk == J) sum = __dadd_rn(sum, vk);
+      }
+      // rank among distinct columns: count first-occurrences with a smaller column
+      unsigned fm = __ballot_sync(0xffffffffu, firstJ);
+      for (int k = 0; k < m; ++k) {
+        int Jk = __shfl_sync(0xffffffffu, J, k);
+        if (((fm >> k) & 1u) && Jk < J) ++rank;
+      }
+      distinct = __popc(fm);
+      if (FILL && firstJ) { cic[out0 + rank] = J; valc[out0 + rank] = sum; }
+    } else {
+      // long rows: same definition, operands re-read from memory (cached)
+      for (int k = lane; k < m; k += 32) {
+        int J = agg[ci[r.pos(k)]];
+        bool firstJ = true;
+        for (int q = 0; q < k && firstJ; ++q)
+          if (agg[ci[r.pos(q)]] == J) firstJ = false;
+        if (!firstJ) continue;
+        ++distinct;
+        if (FILL) {
+          int rank = 0;
+          double sum = val[r.pos(k)];
+          for (int q = 0; q < m; ++q) {
+            int Jq = agg[ci[r.pos(q)]];
+            if (Jq < J) {
+              bool fq = true;
+              for (int u = 0; u < q && fq; ++u)
+                if (agg[ci[r.pos(u)]] == Jq) fq = false;
+              if (fq) ++rank;
+            } else if (Jq == J && q > k) {
+              sum = __dadd_rn(sum, val[r.pos(q)]);
+            }
+          }
+          cic[out0 + rank] = J;
+          valc[out0 + rank] = sum;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
+    }
+    if (!FILL && lane == 0) count[I] = distinct;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Composition of pass maps and member lists of the level's aggregates
+// ---------------------------------------------------------------------------
+__global__ void k_iota(int n, int32_t *a) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = i;
+}
+__global__ void k_compose(int n, int32_t *agg, const int32_t *__restrict__ pass_agg) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) agg[i] = pass_agg[agg[i]];
+}
+__global__ void k_count_members(int n, const int32_t *__restrict__ agg, int *cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicAdd(&cnt[agg[i]], 1);
+}
+__global__ void k_fill_members(int n, const int32_t *__restrict__ agg, const int32_t *__restrict__ mrp,
+                               int *cursor, int32_t *mem) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int I = agg[i];
+  int slot = atomicAdd(&cursor[I], 1);
+  mem[mrp[I] + slot] = i;
+}
+// members ascending (insertion sort; aggregates hold at most 2^passes nodes)
+__global__ void k_sort_members(int nc, const int32_t *__restrict__ mrp, int32_t *mem) {
+  int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  int b = mrp[I], e = mrp[I + 1];
+  for (int a = b + 1; a < e; ++a) {
+    int v = mem[a], c = a - 1;
+    while (c >= b && mem[c] > v) { mem[c + 1] = mem[c]; --c; }
+    mem[c + 1] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense coarsest inverse: Gauss-Jordan with partial pivoting (pivot = largest
+// |entry| of the column at or below the diagonal, smallest row on ties).
+// The direct coarsest solve of Sec. 2 and Algorithm 1, factored once at setup;
+// each cycle then applies A_L^{-1} as a matrix-vector product.
+// ---------------------------------------------------------------------------
+__global__ void k_csr_to_dense(int m, const int32_t *rp, const int32_t *ci, const double *val, double *M,
+                               double *Inv) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long mm = (long long)m * m;
+  for (long long t = idx; t < mm; t += (long long)gridDim.x * blockDim.x) {
+    M[t] = 0.0;
+    Inv[t] = (t / m == t % m) ? 1.0 : 0.0;
+  }
+}
+__global__ void k_csr_scatter(int m, const int32_t *rp, const int32_t *ci, const double *val, double *M) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) M[(size_t)i * m + ci[e]] = val[e];
+}
+
+// one block: pivot search in column k, row swap in M and Inv, copy of the
+// pivot row and of the column factors for the elimination step
+__global__ void k_gj_pivot(int m, int k, double *M, double *Inv, double *prow, double *pinv, double *fac,
+                           unsigned *eflags) {
+  __shared__ double bv[1024];
+  __shared__ int bi[1024];
+  double best = -1.0;
+  int bidx = m;
+  for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+    double a = fabs(M[(size_t)i * m + k]);
+    if (a > best || (a == best && i < bidx)) { best = a; bidx = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      double a = bv[threadIdx.x + s];
+      int ia = bi[threadIdx.x + s];
+      if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) {
+        bv[threadIdx.x] = a;
+        bi[threadIdx.x] = ia;
+      }
+    }
+    __syncthreads();
+  }
+  int p = bi[0];
+  if (!(bv[0] > 0.0) || p >= m) {
+    if (threadIdx.x == 0) atomicOr(eflags, AMG_EFLAG_BREAKDOWN);
+    p = k;
+  }
+  if (p != k) {
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      double t = M[(size_t)k * m + j]; M[(size_t)k * m + j] = M[(size_t)p * m + j]; M[(size_t)p * m + j] = t;
+      t = Inv[(size_t)k * m + j]; Inv[(size_t)k * m + j] = Inv[(size_t)p * m + j]; Inv[(size_t)p * m + j] = t;
+    }
+  }
+  __syncthreads();
+  double piv = M[(size_t)k * m + k];
+  double rpiv = piv != 0.0 ? 1.0 / piv : 0.0;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    prow[j] = M[(size_t)k * m + j] * rpiv;
+    pinv[j] = Inv[(size_t)k * m + j] * rpiv;
+    fac[j] = M[(size_t)j * m + k];
+  }
+}
+
+// rows i != k: row_i -= fac_i * (pivot row / pivot); row k = pivot row / pivot
+__global__ void k_gj_eliminate(int m, int k, double *M, double *Inv, const double *__restrict__ prow,
+                               const double *__restrict__ pinv, const double *__restrict__ fac) {
+  long long mm = (long long)m * m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < mm;
+       t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t / m), j = (int)(t % m);
+    if (i == k) {
+      if (j >= k) M[t] = prow[j];
+      Inv[t] = pinv[j];
+    } else {
+      double f = fac[i];
+      if (j > k) M[t] = M[t] - f * prow[j];
+      else if (j == k) M[t] = 0.0;
+      Inv[t] = Inv[t] - f * pinv[j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Scratch {
+  double *w = nullptr;
+  int32_t *mate = nullptr, *pick = nullptr, *fa = nullptr, *fb = nullptr, *first = nullptr;
+  int *flag = nullptr, *id = nullptr, *tiles = nullptr, *cnt = nullptr, *count = nullptr;
+  int *host = nullptr;  // pinned: [0] pairs, [1] frontier, [2] scan total
+  size_t cap_n = 0, cap_nnz = 0;
+};
+
+struct Csr {
+  int n = 0;
+  long long nnz = 0;
+  int32_t *rp = nullptr, *ci = nullptr;
+  double *val = nullptr;
+};
+
+amg_status dev_alloc(void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+  if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; return AMG_ERR_OOM; }
+  return AMG_OK;
+}
+
+void free_csr(Csr &c) {
+  cudaFree(c.rp); cudaFree(c.ci); cudaFree(c.val);
+  c = Csr();
+}
+
+amg_status scratch_alloc(Scratch &s, int n, long long nnz) {
+  int tiles = cdiv(std::max(n, 1), SCAN_TILE);
+  AMG_TRY(dev_alloc((void **)&s.w, sizeof(double) * (nnz + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.mate, sizeof(int32_t) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.pick, sizeof(int32_t) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.fa, sizeof(int32_t) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.fb, sizeof(int32_t) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.first, sizeof(int32_t) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.flag, sizeof(int) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.id, sizeof(int) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.count, sizeof(int) * (n + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&s.tiles, sizeof(int) * (tiles + 8)));
+  AMG_TRY(dev_alloc((void **)&s.cnt, sizeof(int) * 8));
+  if (cudaMallocHost((void **)&s.host, sizeof(int) * 8) != cudaSuccess) { cudaGetLastError(); return AMG_ERR_OOM; }
+  s.cap_n = n;
+  s.cap_nnz = nnz;
+  return AMG_OK;
+}
+
+void scratch_free(Scratch &s) {
+  cudaFree(s.w); cudaFree(s.mate); cudaFree(s.pick); cudaFree(s.fa); cudaFree(s.fb); cudaFree(s.first);
+  cudaFree(s.flag); cudaFree(s.id); cudaFree(s.count); cudaFree(s.tiles); cudaFree(s.cnt);
+  if (s.host) cudaFreeHost(s.host);
+  s = Scratch();
+}
+
+// Synchronous read of the device error bits (and reset).
+amg_status check_flags(amg_hierarchy *h, cudaStream_t st) {
+  unsigned f = 0;
+  AMG_TRY(read_eflags(h, st, &f));
+  if (f & AMG_EFLAG_BAD_CSR) return AMG_ERR_INVALID_CSR;
+  if (f & AMG_EFLAG_NONFINITE) return AMG_ERR_INVALID_ARG;
+  if (f & AMG_EFLAG_ZERO_DIAG) return AMG_ERR_ZERO_DIAG;
+  if (f & AMG_EFLAG_NONSYM) return AMG_ERR_UNSUPPORTED;
+  if (f & AMG_EFLAG_BREAKDOWN) return AMG_ERR_ZERO_DIAG;
+  if (f & AMG_EFLAG_TIMEOUT) return AMG_ERR_TIMEOUT;
+  return AMG_OK;
+}
+
+// One pairwise pass on `in`: matching rounds, numbering, Galerkin product.
+// pass_agg (n entries) receives the map; `out` the coarse CSR (allocated here).
+amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pass_agg, Csr &out,
+                        int *rounds, cudaStream_t st) {
+  const int n = in.n;
+  const int T = AMG_THREADS;
+  k_weights<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, in.val, S.w, h->eflags); count_launch();
+  AMG_TRY(check_flags(h, st));
+  k_hem_init<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.fa); count_launch();
+  int nf = n, r = 0;
+  int32_t *fa = S.fa, *fb = S.fb;
+  const int round_cap = 4 * n + 16;  // each productive round pairs >= 1 node
+  for (;;) {
+    ++r;
+    if (r > round_cap) return AMG_ERR_TIMEOUT;
+    cudaMemsetAsync(S.cnt, 0, sizeof(int) * 2, st);
+    if (nf > 0) {
+      k_hem_pick<<<cdiv(nf, T), T, 0, st>>>(nf, fa, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
+      k_hem_match<<<cdiv(nf, T), T, 0, st>>>(nf, fa, S.pick, S.mate, fb, S.cnt); count_launch();
+    }
+    cudaMemcpyAsync(S.host, S.cnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st);
+    AMG_CUDA(cudaStreamSynchronize(st));
+    int pairs = S.host[0];
+    nf = S.host[1];
+    std::swap(fa, fb);
+    if (pairs == 0) break;
+  }
+  *rounds = r;
+  k_hem_finish<<<cdiv(n, T), T, 0, st>>>(n, S.mate); count_launch();
+  // numbering
+  k_agg_flags<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.flag); count_launch();
+  scan_excl(S.flag, S.id, n, S.cnt + 2, S.tiles, st);
+  k_agg_assign<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.id, pass_agg, S.first); count_launch();
+  cudaMemcpyAsync(S.host + 2, S.cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+  AMG_CUDA(cudaStreamSynchronize(st));
+  const int nc = S.host[2];
+  // Galerkin: count, scan, fill
+  out.n = nc;
+  AMG_TRY(dev_alloc((void **)&out.rp, sizeof(int32_t) * (nc + 1 + AMG_PAD)));
+  const int gwarps_blocks = grid_for((long long)nc * 32, T, 152 * 16);
+  k_galerkin<false><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, S.count,
+                                                  nullptr, nullptr, nullptr); count_launch();
+  scan_excl(S.count, out.rp, nc, S.cnt + 3, S.tiles, st);
+  cudaMemcpyAsync(out.rp + nc, S.cnt + 3, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(S.host + 3, S.cnt + 3, sizeof(int), cudaMemcpyDeviceToHost, st);
+  AMG_CUDA(cudaStreamSynchronize(st));
+  out.nnz = S.host[3];
+  AMG_TRY(dev_alloc((void **)&out.ci, sizeof(int32_t) * (out.nnz + AMG_PAD)));
+  AMG_TRY(dev_alloc((void **)&out.val, sizeof(double) * (out.nnz + AMG_PAD)));
+  cudaMemsetAsync(out.ci + out.nnz, 0, sizeof(int32_t) * AMG_PAD, st);
+  cudaMemsetAsync(out.val + out.nnz, 0, sizeof(double) * AMG_PAD, st);
+  k_galerkin<true><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, nullptr,
+                                                 out.rp, out.ci, out.val); count_launch();
+  AMG_CUDA(cudaGetLastError());
+  return AMG_OK;
+}
+
+amg_status validate_params(const amg_params *p) {
+  if (p->passes < 1 || p->passes > AMG_MAX_PASSES) return AMG_ERR_INVALID_ARG;
+  if (p->max_levels < 1 || p->max_levels > AMG_MAX_LEVELS) return AMG_ERR_INVALID_ARG;
+  if (p->coarse_max < 1) return AMG_ERR_INVALID_ARG;
+  if (!(p->stall_ratio > 0.0) || !(p->stall_ratio <= 1.0)) return AMG_ERR_INVALID_ARG;
+  if (!(p->omega > 0.0) || !(p->omega < 2.0)) return AMG_ERR_INVALID_ARG;
+  if (p->nu_pre < 1 || p->nu_post < 0 || p->nu_pre > 64 || p->nu_post > 64) return AMG_ERR_INVALID_ARG;
+  if (p->coarse_solver < 0 || p->coarse_solver > 2) return AMG_ERR_INVALID_ARG;
+  if (p->precision < 0 || p->precision > 2) return AMG_ERR_INVALID_ARG;
+  return AMG_OK;
+}
+
+amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp, const int32_t *ci,
+                      const double *val, cudaStream_t st) {
+  const int T = AMG_THREADS;
+  // level 0: owned, padded copy of A
+  Level &l0 = h->lev[0];
+  l0.n = n;
+  l0.nnz = nnz;
+  AMG_TRY(hier_alloc(h, (void **)&l0.rp, sizeof(int32_t) * (n + 1 + AMG_PAD)));
+  AMG_TRY(hier_alloc(h, (void **)&l0.ci, sizeof(int32_t) * (nnz + AMG_PAD)));
+  AMG_TRY(hier_alloc(h, (void **)&l0.val, sizeof(double) * (nnz + AMG_PAD)));
+  AMG_CUDA(cudaMemcpyAsync(l0.rp, rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToDevice, st));
+  if (nnz) {
+    AMG_CUDA(cudaMemcpyAsync(l0.ci, ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
+    AMG_CUDA(cudaMemcpyAsync(l0.val, val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, st));
+  }
+  cudaMemsetAsync(l0.ci + nnz, 0, sizeof(int32_t) * AMG_PAD, st);
+  cudaMemsetAsync(l0.val + nnz, 0, sizeof(double) * AMG_PAD, st);
+  k_check_csr<<<cdiv(n, T), T, 0, st>>>(n, nnz, l0.rp, l0.ci, h->eflags); count_launch();
+  k_nonfinite<<<grid_for(nnz, T), T, 0, st>>>(nnz, l0.val, h->eflags); count_launch();
+  AMG_TRY(check_flags(h, st));
+
+  Scratch S;
+  amg_status rs = scratch_alloc(S, n, nnz);
+  if (rs != AMG_OK) { scratch_free(S); return rs; }
+  int k = 0;
+  const amg_params &p = h->prm;
+  while (k + 1 < p.max_levels && h->lev[k].n > p.coarse_max) {
+    Level &f = h->lev[k];
+    Csr cur{f.n, f.nnz, f.rp, f.ci, f.val};
+    bool owned = false;
+    int32_t *agg = nullptr, *pass_agg = nullptr;
+    rs = dev_alloc((void **)&agg, sizeof(int32_t) * (f.n + AMG_PAD));
+    if (rs == AMG_OK) rs = dev_alloc((void **)&pass_agg, sizeof(int32_t) * (f.n + AMG_PAD));
+    if (rs != AMG_OK) { cudaFree(agg); scratch_free(S); return rs; }
+    k_iota<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg); count_launch();
+    int rounds[AMG_MAX_PASSES] = {0};
+    for (int pass = 0; pass < p.passes; ++pass) {
+      Csr nxt;
+      rs = coarsen_pass(h, S, cur, pass_agg, nxt, &rounds[pass], st);
+      if (rs != AMG_OK) {
+        free_csr(nxt);
+        if (owned) free_csr(cur);
+        cudaFree(agg); cudaFree(pass_agg); scratch_free(S);
+        return rs;
+      }
+      k_compose<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, pass_agg); count_launch();
+      if (owned) { AMG_CUDA(cudaStreamSynchronize(st)); free_csr(cur); }
+      cur = nxt;
+      owned = true;
+    }
+    cudaFree(pass_agg);
+    if ((double)cur.n / (double)f.n > p.stall_ratio) {
+      AMG_CUDA(cudaStreamSynchronize(st));
+      free_csr(cur);
+      cudaFree(agg);
+      break;
+    }
+    // adopt the coarse level; record allocations for amg_destroy
+    Level &c = h->lev[k + 1];
+    c.n = cur.n;
+    c.nnz = cur.nnz;
+    c.rp = cur.rp; c.ci = cur.ci; c.val = cur.val;
+    h->allocs.push_back(cur.rp); h->allocs.push_back(cur.ci); h->allocs.push_back(cur.val);
+    f.agg = agg;
+    h->allocs.push_back(agg);
+    memcpy(f.rounds, rounds, sizeof(rounds));
+    // member lists of the level's aggregates
+    AMG_TRY(hier_alloc(h, (void **)&f.mrp, sizeof(int32_t) * (c.n + 1 + AMG_PAD)));
+    AMG_TRY(hier_alloc(h, (void **)&f.mem, sizeof(int32_t) * (f.n + AMG_PAD)));
+    cudaMemsetAsync(S.count, 0, sizeof(int) * c.n, st);
+    k_count_members<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, S.count); count_launch();
+    scan_excl(S.count, f.mrp, c.n, S.cnt + 4, S.tiles, st);
+    cudaMemcpyAsync(f.mrp + c.n, S.cnt + 4, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(S.count, 0, sizeof(int) * c.n, st);
+    k_fill_members<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, f.mrp, S.count, f.mem); count_launch();
+    k_sort_members<<<cdiv(c.n, T), T, 0, st>>>(c.n, f.mrp, f.mem); count_launch();
+    AMG_CUDA(cudaGetLastError());
+    ++k;
+  }
+  scratch_free(S);
+  h->L = k;
+  // diagonals of every level
+  for (int j = 0; j <= h->L; ++j) {
+    Level &l = h->lev[j];
+    AMG_TRY(hier_alloc(h, (void **)&l.dinv, sizeof(double) * (l.n + AMG_PAD)));
+    k_diag<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.dinv, h->eflags); count_launch();
+  }
+  AMG_TRY(check_flags(h, st));
+  return AMG_OK;
+}
+
+}  // namespace
+
+// Dense inverse of the coarsest matrix (Gauss-Jordan, partial pivoting).
+amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
+  const Level &c = h->lev[h->L];
+  const int m = c.n;
+  double *M = nullptr, *prow = nullptr, *pinv = nullptr, *fac = nullptr;
+  AMG_TRY(hier_alloc(h, (void **)&h->ainv, sizeof(double) * ((size_t)m * m + AMG_PAD)));
+  if (dev_alloc((void **)&M, sizeof(double) * (size_t)m * m) != AMG_OK) return AMG_ERR_OOM;
+  if (dev_alloc((void **)&prow, sizeof(double) * 3 * (m + AMG_PAD)) != AMG_OK) { cudaFree(M); return AMG_ERR_OOM; }
+  pinv = prow + (m + AMG_PAD);
+  fac = pinv + (m + AMG_PAD);
+  const int T = AMG_THREADS;
+  long long mm = (long long)m * m;
+  k_csr_to_dense<<<grid_for(mm, T), T, 0, st>>>(m, c.rp, c.ci, c.val, M, h->ainv); count_launch();
+  k_csr_scatter<<<cdiv(m, T), T, 0, st>>>(m, c.rp, c.ci, c.val, M); count_launch();
+  for (int k = 0; k < m; ++k) {
+    k_gj_pivot<<<1, 1024, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac, h->eflags); count_launch();
+    k_gj_eliminate<<<grid_for(mm, T), T, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac); count_launch();
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(M);
+  cudaFree(prow);
+  if (e != cudaSuccess) return amg_cuda_status(e);
+  return AMG_OK;
+}
+
+extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                                const double *d_val, const amg_params *params, amg_stream_t stream,
+                                amg_hierarchy **out) {
+  if (!out) return AMG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n <= 0 || nnz < 0 || nnz >= (1ll << 31) - AMG_PAD || !d_row_ptr || (nnz > 0 && (!d_col || !d_val)))
+    return AMG_ERR_INVALID_ARG;
+  amg_params p;
+  amg_default_params(&p);
+  if (params) p = *params;
+  AMG_TRY(validate_params(&p));
+  cudaStream_t st = (cudaStream_t)stream;
+  amg_hierarchy *h = new amg_hierarchy();
+  h->prm = p;
+  amg_status s = AMG_OK;
+  do {
+    if (cudaGetDevice(&h->device) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
+    s = hier_alloc(h, (void **)&h->eflags, sizeof(unsigned) * 4);
+    if (s) break;
+    if (cudaMallocHost((void **)&h->eflags_host, sizeof(unsigned) * 4) != cudaSuccess) { s = AMG_ERR_OOM; break; }
+    cudaMemsetAsync(h->eflags, 0, sizeof(unsigned) * 4, st);
+    s = setup_impl(h, n, nnz, d_row_ptr, d_col, d_val, st);
+    if (s) break;
+    s = coarse_setup(h, st);
+    if (s) break;
+    s = precision_setup(h, st);
+    if (s) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
+  } while (0);
+  if (s != AMG_OK) {
+    cudaGetLastError();
+    amg_destroy(h);
+    return s;
+  }
+  *out = h;
+  return AMG_OK;
+}
+
+extern "C" int amg_setup_rounds(const amg_hierarchy *h, int level, int pass) {
+  if (!h || level < 0 || level >= h->L || pass < 0 || pass >= h->prm.passes) return -1;
+  return h->lev[level].rounds[pass];
+}
