@@ -79,7 +79,14 @@ def test_bicgstab_matches_oracle_convdiff(pe):
     x = torch.zeros_like(b)
     info = amg.bicgstab_solve(h, b, x, rtol=0.0, max_iter=info_o.iterations)
     assert info.iterations == info_o.iterations
-    x_o2, _ = oh.bicgstab(s.b, rtol=0.0, max_iter=info_o.iterations)
+    # BiCGStab on a convection-dominated operator amplifies rounding-order
+    # differences along the iteration (no error-norm monotonicity as in CG),
+    # so the 1e-10 solution check is made on solves run to 1e-12: both are
+    # then within about cond(A) * 1e-12 of the exact solution.
+    x = torch.zeros_like(b)
+    info = amg.bicgstab_solve(h, b, x, rtol=1e-12, max_iter=500)
+    x_o2, info_o2 = oh.bicgstab(s.b, rtol=1e-12, max_iter=500)
+    assert info.status == amg.AMG_OK and abs(info.iterations - info_o2.iterations) <= 1
     assert rel_err(x.cpu().numpy(), x_o2) < SOLUTION_TOL
 
 
