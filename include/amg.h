@@ -156,6 +156,26 @@ amg_status amg_export_level(const amg_hierarchy *h, int level, int32_t *d_row_pt
  * matched nothing included), or -1 if out of range. */
 int amg_setup_rounds(const amg_hierarchy *h, int level, int pass);
 
+/* ---- Kernel autotuning (no counterpart in the paper) ----
+ * Times, on each level of h, the threads-per-row choices of the row kernels
+ * (1, 2, 4, ... 32 lanes per row) and the fused / separate forms of the first
+ * pre-smoothing sweep (with the residual) and of the prolongation (with the
+ * first post-smoothing sweep), keeps the fastest for h, and remembers the
+ * choice by level shape (rows, nonzeros, precision) so that every later
+ * amg_setup in this process with a level of the same shape starts with it.
+ * Choices change only the summation order of row sums (results stay within
+ * rounding of each other).  Synchronises the stream.  Without tuning, a level
+ * uses 1 lane per row up to 12 nonzeros per row and more lanes beyond. */
+amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream);
+
+/* Current kernel configuration of a level: lanes per row, fused presmoothing,
+ * fused prolongation.  Returns 0, or -1 for a NULL h or a bad level. */
+int amg_level_config(const amg_hierarchy *h, int level, int *tpr, int *fuse_pre, int *fuse_post);
+
+/* Sets a level's kernel configuration by hand (tpr in {1,2,4,8,16,32}).
+ * AMG_ERR_INVALID_ARG for a NULL h, a bad level or a bad tpr. */
+amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_pre, int fuse_post);
+
 /* ---- Instrumentation (no counterpart in the paper; used for measurement) ---- */
 
 /* Kernel kinds reported by the per-kernel profiler.  Each kind is tracked per

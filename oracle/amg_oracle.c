@@ -30,7 +30,8 @@
  *    p_0 = r_0, rbar_0 = r_0 and p_{j+1} = r_{j+1} + beta (p_j - omega A p~_j);
  *  - the coarsest solve of Algorithm 1 is A_L^{-1} f_L by dense LU with partial
  *    pivoting, or, when A_L is too large for a dense factor, Jacobi-PCG to a
- *    relative residual of 1e-12 (the CG coarse solver of Sec. 4.2).
+ *    relative residual of 1e-12 (the CG coarse solver of Sec. 4.2), written
+ *    in the Chronopoulos-Gear arrangement of CG.
  */
 #include <math.h>
 #include <stdint.h>
@@ -593,35 +594,51 @@ int orc_level_export(const orc_hier *h, int k, int *rp, int *ci, double *val, in
 /* ------------------------------------------------------------------------ */
 
 /* Jacobi-preconditioned CG on the coarsest matrix from x = 0 until
- * ||r|| <= 1e-12 ||f|| or 1000 iterations (CG as the coarse solver, Sec. 4.2). */
+ * ||r|| <= 1e-12 ||f|| or 1000 iterations (CG as the coarse solver, Sec. 4.2),
+ * in the Chronopoulos-Gear arrangement of CG, which computes the three inner
+ * products of an iteration together.  With u = D^-1 r and w = A u:
+ *   gamma = (r,u), delta = (w,u), alpha_0 = gamma_0/delta_0, beta_0 = 0;
+ *   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+ *   beta' = gamma'/gamma, alpha' = gamma'/(delta' - beta' gamma'/alpha).
+ * In exact arithmetic the iterates are those of standard preconditioned CG. */
 static int coarse_cg(orc_hier *h, const double *f, double *x) {
   const orc_level *l = &h->lev[h->L];
   int n = l->n;
   double *r = (double *)malloc((size_t)n * sizeof(double));
-  double *z = (double *)malloc((size_t)n * sizeof(double));
-  double *p = (double *)malloc((size_t)n * sizeof(double));
-  double *q = (double *)malloc((size_t)n * sizeof(double));
+  double *u = (double *)malloc((size_t)n * sizeof(double));
+  double *w = (double *)malloc((size_t)n * sizeof(double));
+  double *p = (double *)calloc((size_t)n, sizeof(double));
+  double *s = (double *)calloc((size_t)n, sizeof(double));
   for (int i = 0; i < n; ++i) { x[i] = 0.0; r[i] = f[i]; }
   double fn = norm2(n, f);
   int it = 0;
   if (fn > 0.0) {
-    for (int i = 0; i < n; ++i) { z[i] = r[i] / l->diag[i]; p[i] = z[i]; }
-    double rz = dot(n, r, z);
+    for (int i = 0; i < n; ++i) u[i] = r[i] / l->diag[i];
+    orc_spmv(n, l->rp, l->ci, l->val, u, w);
+    double gamma = dot(n, r, u);
+    double delta = dot(n, w, u);
+    double alpha = gamma / delta, beta = 0.0;
     for (it = 1; it <= 1000; ++it) {
-      orc_spmv(n, l->rp, l->ci, l->val, p, q);
-      double alpha = rz / dot(n, p, q);
-      for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+      for (int i = 0; i < n; ++i) {
+        p[i] = u[i] + beta * p[i];
+        s[i] = w[i] + beta * s[i];
+        x[i] += alpha * p[i];
+        r[i] -= alpha * s[i];
+      }
+      for (int i = 0; i < n; ++i) u[i] = r[i] / l->diag[i];
+      orc_spmv(n, l->rp, l->ci, l->val, u, w);
+      double gamma_new = dot(n, r, u);
+      delta = dot(n, w, u);
       if (norm2(n, r) <= 1e-12 * fn) break;
-      for (int i = 0; i < n; ++i) z[i] = r[i] / l->diag[i];
-      double rz_new = dot(n, r, z);
-      double beta = rz_new / rz;
-      rz = rz_new;
-      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+      beta = gamma_new / gamma;
+      alpha = gamma_new / (delta - beta * gamma_new / alpha);
+      gamma = gamma_new;
+      if (!isfinite(alpha)) break;
     }
     if (it > 1000) it = 1000;
   }
   h->coarse_cg_iters = it;
-  free(r); free(z); free(p); free(q);
+  free(r); free(u); free(w); free(p); free(s);
   return ORC_OK;
 }
 

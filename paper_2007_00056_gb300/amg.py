@@ -33,6 +33,7 @@ EXPORTS = (
     "amg_default_params", "amg_setup", "amg_vcycle", "pcg_solve", "bicgstab_solve", "amg_num_levels",
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
+    "amg_autotune", "amg_level_config", "amg_level_set_config",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -107,6 +108,9 @@ def lib(build_if_missing: bool = False):
             l.amg_profile_enable.argtypes = [vp, i32]
             l.amg_profile_reset.argtypes = [vp]
             l.amg_profile_read.argtypes = [vp, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_longlong)]
+            l.amg_autotune.argtypes = [vp, vp]
+            l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]
+            l.amg_level_config.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             _lib = l
     return _lib
 
@@ -299,3 +303,25 @@ def amg_profile_table(h: Hierarchy):
                                  gbs=(by / (ms * 1e-3) / 1e9) if ms > 0 else 0.0))
     rows.sort(key=lambda r: -r["ms"])
     return rows
+
+
+
+def amg_autotune(h: Hierarchy, stream=None) -> None:
+    """Times kernel variants on h's levels, keeps the fastest and caches them by level shape."""
+    st = lib().amg_autotune(h.handle, _stream(stream))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_autotune")
+
+
+def amg_level_config(h: Hierarchy, level: int):
+    """(lanes per row, fused presmoothing, fused prolongation) of a level."""
+    t, a, b = C.c_int(), C.c_int(), C.c_int()
+    if lib().amg_level_config(h.handle, int(level), C.byref(t), C.byref(a), C.byref(b)) != 0:
+        raise IndexError(level)
+    return t.value, a.value, b.value
+
+
+def amg_level_set_config(h: Hierarchy, level: int, tpr: int, fuse_pre: bool, fuse_post: bool) -> None:
+    st = lib().amg_level_set_config(h.handle, int(level), int(tpr), int(bool(fuse_pre)), int(bool(fuse_post)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_level_set_config")

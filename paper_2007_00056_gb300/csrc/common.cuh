@@ -60,6 +60,8 @@ struct Level {
   float *f32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
   int rounds[AMG_MAX_PASSES] = {0};
   int tpr = 1;               // threads per row of this level's row kernels
+  int fuse_pre = 1;          // first presmoothing sweep fused into the residual kernel
+  int fuse_post = 0;         // prolongation fused into the first postsmoothing sweep
 };
 
 // Kernel kinds of the per-kernel profiler (id = kind * AMG_MAX_LEVELS + level).
@@ -81,12 +83,18 @@ struct Profiler {
   long long launches[AMG_PROF_IDS] = {0};
 };
 
+// Work memory of the persistent coarse CG: own-row x and p, double-buffered
+// r, w, s (neighbours read the previous iteration's copy while owners write
+// the next), reduction partials, barrier counter and iteration counters.
 struct CoarseCG {
-  int n = 0, grid = 0;
-  unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
-  double *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *p2 = nullptr, *q = nullptr, *part = nullptr;
-  unsigned *bar = nullptr;   // [0] arrival counter, [1] generation
+  int n = 0, grid = 0, threads = 0;
+  size_t smem = 0;           // dynamic shared memory per block (matrix slice staging)
+  double *x = nullptr, *p = nullptr;
+  double *r[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr};
+  double *part = nullptr;    // 2 slots x 3 values x AMG_MAX_BLOCKS
+  unsigned *bar = nullptr;   // [0] monotonic arrival counter
   int *iters = nullptr;
+  unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
 };
 
 struct amg_hierarchy {
@@ -248,5 +256,11 @@ amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t
 amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s);
 amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
+void reset_graphs(amg_hierarchy *h);
 amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
-void launch_residual_f64(const Level &l, const double *b, const double *x, double *r, cudaStream_t s);
+#define CG_THREADS 512
+#define CG_SMEM_CAP (200 * 1024)
+// Grid, block and shared-memory configuration of the coarse CG for n rows on
+// the current device (also sets the kernel's shared-memory limit).
+amg_status coarse_cg_config(int n, CoarseCG *cg);
+

@@ -70,8 +70,10 @@ __global__ void k_init_residual(int n, const int32_t *__restrict__ rp, const int
     st->rel = st->bnorm > 0.0 ? sqrt(tot[1]) / st->bnorm : 0.0;
     st->it = 0;
     st->half = 0;
-    if (st->bnorm == 0.0 || st->rel <= st->rtol) { st->done = 1; st->status = AMG_OK; }
-    else if (!isfinite(st->rel)) { st->done = 1; st->status = AMG_ERR_INVALID_ARG; }
+    // NaN/Inf in b or x0 (or in A x0) is an invalid argument, checked first:
+    // NaN compares false, so it would otherwise pass the tolerance test
+    if (!isfinite(tot[0]) || !isfinite(tot[1])) { st->done = 1; st->status = AMG_ERR_INVALID_ARG; st->bnorm = 1.0; }
+    else if (st->bnorm == 0.0 || st->rel <= st->rtol) { st->done = 1; st->status = AMG_OK; }
     else if (st->max_iter <= 0) { st->done = 1; st->status = AMG_ERR_NOT_CONVERGED; }
   }
 }
@@ -512,6 +514,13 @@ amg_status end_solve(amg_hierarchy *h, double *x, cudaStream_t s, amg_solve_info
 bool bad_scalar(double v) { return !(v >= 0.0) || std::isinf(v); }
 
 }  // namespace
+
+void reset_graphs(amg_hierarchy *h) {
+  if (h->g_pcg) cudaGraphExecDestroy(h->g_pcg);
+  if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
+  h->g_pcg = h->g_bicg = nullptr;
+  h->g_pcg_nodes = h->g_bicg_nodes = 0;
+}
 
 extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol, int max_iter,
                                 int flexible, amg_stream_t stream, amg_solve_info *info) {

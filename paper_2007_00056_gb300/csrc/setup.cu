@@ -252,13 +252,20 @@ __device__ __forceinline__ PairRow pair_row(int I, const int32_t *first, const i
   return r;
 }
 
+#define GAL_WARPS (AMG_THREADS / 32)
+#define GAL_CAP 256  // contributions per coarse row staged in shared memory
+
 template <bool FILL>
-__global__ void k_galerkin(int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ mate,
-                           const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ val, const int32_t *__restrict__ agg,
-                           int *__restrict__ count, const int32_t *__restrict__ rpc,
-                           int32_t *__restrict__ cic, double *__restrict__ valc) {
+__global__ void __launch_bounds__(AMG_THREADS)
+    k_galerkin(int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ mate,
+               const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
+               const int32_t *__restrict__ agg, int *__restrict__ count, const int32_t *__restrict__ rpc,
+               int32_t *__restrict__ cic, double *__restrict__ valc) {
+  __shared__ int sJ[GAL_WARPS][GAL_CAP];
+  __shared__ double sV[GAL_WARPS][GAL_CAP];
+  __shared__ unsigned char sF[GAL_WARPS][GAL_CAP];
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += warps) {
     PairRow r = pair_row(I, first, mate, rp);
@@ -266,7 +273,7 @@ __global__ void k_galerkin(int nc, const int32_t *__restrict__ first, const int3
     int distinct = 0;
     const int out0 = FILL ? rpc[I] : 0;
     if (m <= 32) {
-      // each lane holds one entry; compare through shuffles
+      // each lane holds one contribution; compare through shuffles
       int J = lane < m ? agg[ci[r.pos(lane)]] : 0x7fffffff;
       double v = lane < m ? val[r.pos(lane)] : 0.0;
       bool firstJ = lane < m;
@@ -278,7 +285,6 @@ __global__ void k_galerkin(int nc, const int32_t *__restrict__ first, const int3
         if (k < lane && Jk == J) firstJ = false;
         if (k > lane && Jk == J) sum = __dadd_rn(sum, vk);
       }
-      // rank among distinct columns: count first-occurrences with a smaller column
       unsigned fm = __ballot_sync(0xffffffffu, firstJ);
       for (int k = 0; k < m; ++k) {
         int Jk = __shfl_sync(0xffffffffu, J, k);
@@ -286,8 +292,43 @@ __global__ void k_galerkin(int nc, const int32_t *__restrict__ first, const int3
       }
       distinct = __popc(fm);
       if (FILL && firstJ) { cic[out0 + rank] = J; valc[out0 + rank] = sum; }
+    } else if (m <= GAL_CAP) {
+      // stage the contributions of this coarse row in the warp's shared slice
+      int *J = sJ[wib];
+      double *V = sV[wib];
+      unsigned char *F = sF[wib];
+      for (int k = lane; k < m; k += 32) { J[k] = agg[ci[r.pos(k)]]; V[k] = val[r.pos(k)]; }
+      __syncwarp();
+      int cnt = 0;
+      for (int k = lane; k < m; k += 32) {
+        const int Jk = J[k];
+        bool f = true;
+        for (int q = 0; q < k; ++q)
+          if (J[q] == Jk) { f = false; break; }
+        F[k] = f ? 1 : 0;
+        cnt += f ? 1 : 0;
+      }
+      __syncwarp();
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      distinct = cnt;
+      if (FILL) {
+        for (int k = lane; k < m; k += 32) {
+          if (!F[k]) continue;
+          const int Jk = J[k];
+          int rank = 0;
+          double sum = V[k];
+          for (int q = 0; q < m; ++q) {
+            const int Jq = J[q];
+            if (Jq < Jk && F[q]) ++rank;
+            if (Jq == Jk && q > k) sum = __dadd_rn(sum, V[q]);
+          }
+          cic[out0 + rank] = Jk;
+          valc[out0 + rank] = sum;
+        }
+      }
+      __syncwarp();
     } else {
-      // long rows: same definition, operands re-read from memory (cached)
+      // very long rows: the same definition with operands re-read from memory
       for (int k = lane; k < m; k += 32) {
         int J = agg[ci[r.pos(k)]];
         bool firstJ = true;

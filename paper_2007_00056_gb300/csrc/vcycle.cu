@@ -13,6 +13,10 @@
 // Every kernel is bandwidth-bound (about 0.16 flop per byte in FP64); rows are
 // handled by TPR threads (1 for stencil-like rows), matrix streamed once.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <functional>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -74,6 +78,25 @@ __global__ void k_residual(int n, const int32_t *__restrict__ rp, const int32_t 
   if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
   T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub, [&](int j) { return __ldg(&x[j]); });
   if (valid && _sub == 0) t[row] = f[row] - ax;
+  ROW_LOOP_END
+}
+
+// First presmoothing sweep from the zero guess fused with the residual:
+// x = omega D^-1 f (stored) and t = f - A x, neighbours' x formed on the fly.
+template <int TPR, typename T, typename V>
+__global__ void k_residual0(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const V *__restrict__ val, const T *__restrict__ dinv, T omega, const T *__restrict__ f,
+                            T *__restrict__ x, T *__restrict__ t, const KState *st) {
+  if (is_done(st)) return;
+  ROW_LOOP_BEGIN(TPR, n)
+  int b = 0, e = 0;
+  if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
+  T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub, [&](int j) { return omega * (__ldg(&dinv[j]) * __ldg(&f[j])); });
+  if (valid && _sub == 0) {
+    const T fi = f[row];
+    x[row] = omega * (dinv[row] * fi);
+    t[row] = fi - ax;
+  }
   ROW_LOOP_END
 }
 
@@ -158,157 +181,188 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
 }
 
 // ---------------------------------------------------------------------------
-// Coarsest solve: Jacobi-PCG to ||r|| <= 1e-12 ||f|| (max 1000 iterations),
-// one persistent cooperative kernel with a bounded software grid barrier.
+// Coarsest solve: Jacobi-PCG to ||r|| <= 1e-12 ||f|| (max 1000 iterations) in
+// the Chronopoulos-Gear arrangement, so the three inner products of an
+// iteration come from one grid reduction: one persistent cooperative kernel,
+// one bounded software grid barrier per iteration.  Block b owns a contiguous
+// row range and stages its matrix slice in shared memory.  A row's next
+// preconditioned residual u_j = D^-1 (r_j - alpha (w_j + beta s_j)) is formed
+// by its owner and, identically, by every block that gathers it, from the
+// previous iteration's copies of r, w, s (double-buffered), so the SpMV of
+// iteration k+1 needs no barrier after the updates of iteration k.
 // ---------------------------------------------------------------------------
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
 #define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
 
-struct GridSync {
-  unsigned *bar;
-  unsigned gen;
-  bool failed;
-  __device__ __forceinline__ void sync(unsigned nblocks, unsigned *eflags) {
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Monotonic-counter grid barrier: the k-th barrier completes when the counter
+// reaches k * G.  Waits are bounded; a block that gives up sets the timeout
+// flag and the caller leaves its loop.
+struct GridBarrier {
+  unsigned *count;
+  unsigned target;
+  __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
     __syncthreads();
-    if (threadIdx.x == 0 && !failed) {
+    target += G;
+    if (threadIdx.x == 0) {
       __threadfence();
-      unsigned arrived = atomicAdd(&bar[0], 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(&bar[0], 0u);
-        __threadfence();
-        atomicExch(&bar[1], gen + 1);
-      } else {
-        long long t0 = clock64();
-        while (*((volatile unsigned *)&bar[1]) == gen) {
-          if (clock64() - t0 > BARRIER_SPIN_LIMIT) {
-            atomicOr(eflags, AMG_EFLAG_TIMEOUT);
-            failed = true;
-            break;
-          }
+      atomicAdd(count, 1u);
+      long long t0 = clock64();
+      while (ld_acquire_u32(count) < target) {
+        __nanosleep(20);
+        if (clock64() - t0 > BARRIER_SPIN_LIMIT) {
+          atomicOr(eflags, AMG_EFLAG_TIMEOUT);
+          *fail_sh = 1;
+          break;
         }
       }
-      __threadfence();
     }
-    ++gen;
     __syncthreads();
+    return *fail_sh == 0;
   }
 };
 
-__device__ __forceinline__ double cg_pnew(double z, double beta, double p) { return __fma_rn(beta, p, z); }
+__device__ __forceinline__ double cg_unext(double r, double w, double s, double d, double alpha, double beta) {
+  return __dmul_rn(__fma_rn(-alpha, __fma_rn(beta, s, w), r), d);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(AMG_THREADS) k_coarse_cg(int n, const int32_t *__restrict__ rp,
-                                                             const int32_t *__restrict__ ci,
-                                                             const double *__restrict__ val,
-                                                             const double *__restrict__ dinv, const T *__restrict__ f,
-                                                             T *__restrict__ xout, CoarseCG cg, const KState *st,
-                                                             unsigned *eflags) {
+__global__ void __launch_bounds__(CG_THREADS, 1)
+    k_coarse_cg(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
+                const double *__restrict__ dinv, const T *__restrict__ f, T *__restrict__ xout, CoarseCG cg,
+                const KState *st, unsigned *eflags) {
   if (is_done(st)) return;
-  __shared__ double sh[2 * 32];
-  __shared__ double red[2];
-  __shared__ int failed_sh;
+  extern __shared__ __align__(16) unsigned char cg_smem[];
+  __shared__ double red_sh[3 * 32];
+  __shared__ double red[3];
+  __shared__ int fail_sh;
   const unsigned G = gridDim.x;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nthreads = G * blockDim.x;
-  GridSync gs{cg.bar, 0u, false};
+  const int R = (n + (int)G - 1) / (int)G;
+  const int r0 = min(n, (int)blockIdx.x * R), r1 = min(n, r0 + R), nr = r1 - r0;
+  const int e0 = rp[r0], e1 = rp[r1], ne = e1 - e0;
+  const bool staged = (size_t)ne * 12 + (size_t)(nr + 1) * 4 <= cg.smem;
+  double *s_val = (double *)cg_smem;
+  int *s_ci = (int *)(s_val + ne);
+  int *s_rp = s_ci + ne;
+  if (threadIdx.x == 0) fail_sh = 0;
+  if (staged) {
+    for (int k = threadIdx.x; k < ne; k += blockDim.x) { s_val[k] = val[e0 + k]; s_ci[k] = ci[e0 + k]; }
+    for (int k = threadIdx.x; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k] - e0;
+  }
+  __syncthreads();
+  const double *lval = staged ? s_val : val + e0;
+  const int *lci = staged ? s_ci : ci + e0;
+  GridBarrier gb{cg.bar, 0u};
   int slot = 0;
-  // reduce NV values over the grid: partials -> barrier -> everyone sums in index order
-  auto grid_reduce = [&](double *v, int nv) {
-    double tmp[2] = {v[0], nv > 1 ? v[1] : 0.0};
-    block_sum<2>(tmp, sh);
-    double *part = cg.part + slot * 2 * AMG_MAX_BLOCKS;
-    if (threadIdx.x == 0) { part[blockIdx.x] = tmp[0]; part[AMG_MAX_BLOCKS + blockIdx.x] = tmp[1]; }
-    gs.sync(G, eflags);
+  // block partial sums -> barrier -> every block sums the G partials in index order
+  auto reduce3 = [&](double (&v)[3]) -> bool {
+    block_sum<3>(v, red_sh);
+    double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
+    if (threadIdx.x == 0) {
+      part[blockIdx.x] = v[0];
+      part[AMG_MAX_BLOCKS + blockIdx.x] = v[1];
+      part[2 * AMG_MAX_BLOCKS + blockIdx.x] = v[2];
+    }
+    bool ok = gb.sync(G, eflags, &fail_sh);
     if (threadIdx.x < 32) {
-      double a = 0.0, b = 0.0;
-      for (unsigned k = threadIdx.x; k < G; k += 32) { a += __ldcg(&part[k]); b += __ldcg(&part[AMG_MAX_BLOCKS + k]); }
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (unsigned k = threadIdx.x; k < G; k += 32) {
+        a += __ldcg(&part[k]);
+        b += __ldcg(&part[AMG_MAX_BLOCKS + k]);
+        c += __ldcg(&part[2 * AMG_MAX_BLOCKS + k]);
+      }
       a = warp_sum(a);
       b = warp_sum(b);
-      if (threadIdx.x == 0) { red[0] = a; red[1] = b; failed_sh = gs.failed ? 1 : 0; }
+      c = warp_sum(c);
+      if (threadIdx.x == 0) { red[0] = a; red[1] = b; red[2] = c; }
     }
     __syncthreads();
     v[0] = red[0];
-    if (nv > 1) v[1] = red[1];
+    v[1] = red[1];
+    v[2] = red[2];
     slot ^= 1;
+    return ok;
   };
+  auto row_begin = [&](int i) { return staged ? s_rp[i - r0] : __ldg(&rp[i]) - e0; };
 
-  double *x = cg.x, *r = cg.r, *z = cg.z, *p = cg.p, *pn = cg.p2, *q = cg.q;
-  double v[2];
-  // x = 0, r = f, ||f||
-  double ff = 0.0;
-  for (int i = tid; i < n; i += nthreads) {
-    double fi = (double)f[i];
-    x[i] = 0.0;
-    r[i] = fi;
-    ff += fi * fi;
-  }
-  v[0] = ff; v[1] = 0.0;
-  grid_reduce(v, 1);
-  const double fnorm = sqrt(v[0]);
-  int it = 0;
-  if (fnorm > 0.0 && !failed_sh) {
-    // z = D^-1 r, p = z
-    double rz = 0.0;
-    for (int i = tid; i < n; i += nthreads) {
-      double ri = __ldcg(&r[i]);
-      double zi = ri * __ldg(&dinv[i]);
-      z[i] = zi;
-      p[i] = zi;
-      rz += ri * zi;
+  double *x = cg.x, *p = cg.p;
+  // initial phase: r0 = f, u0 = D^-1 f, w0 = A u0, s = p = x = 0
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const double fi = (double)f[i], di = __ldg(&dinv[i]);
+    const double ui = __dmul_rn(fi, di);
+    double wi = 0.0;
+    const int b = row_begin(i), e = row_begin(i + 1);
+    for (int k = b; k < e; ++k) {
+      const int j = lci[k];
+      wi += lval[k] * __dmul_rn((double)f[j], __ldg(&dinv[j]));
     }
-    v[0] = rz;
-    grid_reduce(v, 1);
-    rz = v[0];
-    double beta = 0.0;
-    bool first = true;
+    cg.r[0][i] = fi;
+    cg.w[0][i] = wi;
+    cg.s[0][i] = 0.0;
+    x[i] = 0.0;
+    p[i] = 0.0;
+    v[0] += fi * ui;
+    v[1] += wi * ui;
+    v[2] += fi * fi;
+  }
+  bool ok = reduce3(v);
+  const double fnorm = sqrt(v[2]);
+  int it = 0;
+  if (ok && fnorm > 0.0) {
+    double gamma = v[0];
+    double alpha = v[0] / v[1], beta = 0.0;
+    int cur = 0;
     for (it = 1; it <= CG_MAXIT; ++it) {
-      // phase 1: pn = z + beta p (p itself in the first iteration), q = A pn;
-      // neighbours' pn are formed on the fly from z and p, which no block
-      // writes in this phase
-      double pq = 0.0;
-      for (int i = tid; i < n; i += nthreads) {
-        double s = 0.0;
-        const int e1 = __ldg(&rp[i + 1]);
-        for (int e = __ldg(&rp[i]); e < e1; ++e) {
-          int j = __ldg(&ci[e]);
-          double pj = first ? __ldcg(&p[j]) : cg_pnew(__ldcg(&z[j]), beta, __ldcg(&p[j]));
-          s += __ldg(&val[e]) * pj;
+      const double *ro = cg.r[cur], *wo = cg.w[cur], *so = cg.s[cur];
+      double *rn = cg.r[cur ^ 1], *wn = cg.w[cur ^ 1], *sn = cg.s[cur ^ 1];
+      double acc[3] = {0.0, 0.0, 0.0};
+      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const double di = __ldg(&dinv[i]);
+        const double rold = __ldcg(&ro[i]), wold = __ldcg(&wo[i]), sold = __ldcg(&so[i]);
+        const double uold = __dmul_rn(rold, di);
+        const double pi = __fma_rn(beta, __ldcg(&p[i]), uold);
+        const double snew = __fma_rn(beta, sold, wold);
+        const double rnew = __fma_rn(-alpha, snew, rold);
+        const double unew = __dmul_rn(rnew, di);
+        x[i] = __fma_rn(alpha, pi, __ldcg(&x[i]));
+        p[i] = pi;
+        double wi = 0.0;
+        const int b = row_begin(i), e = row_begin(i + 1);
+        for (int k = b; k < e; ++k) {
+          const int j = lci[k];
+          wi += lval[k] * cg_unext(__ldcg(&ro[j]), __ldcg(&wo[j]), __ldcg(&so[j]), __ldg(&dinv[j]), alpha, beta);
         }
-        double pi = first ? __ldcg(&p[i]) : cg_pnew(__ldcg(&z[i]), beta, __ldcg(&p[i]));
-        pn[i] = pi;
-        q[i] = s;
-        pq += pi * s;
+        rn[i] = rnew;
+        sn[i] = snew;
+        wn[i] = wi;
+        acc[0] += rnew * unew;
+        acc[1] += wi * unew;
+        acc[2] += rnew * rnew;
       }
-      v[0] = pq;
-      grid_reduce(v, 1);
-      if (failed_sh) break;
-      const double alpha = rz / v[0];
-      // phase 2: x += alpha pn, r -= alpha q, z = D^-1 r
-      double rr = 0.0, rzn = 0.0;
-      for (int i = tid; i < n; i += nthreads) {
-        double pi = __ldcg(&pn[i]);
-        x[i] = __ldcg(&x[i]) + alpha * pi;
-        double ri = __ldcg(&r[i]) - alpha * __ldcg(&q[i]);
-        r[i] = ri;
-        double zi = ri * __ldg(&dinv[i]);
-        z[i] = zi;
-        rr += ri * ri;
-        rzn += ri * zi;
-      }
-      v[0] = rr; v[1] = rzn;
-      grid_reduce(v, 2);
-      if (failed_sh) break;
-      double *tmp = p; p = pn; pn = tmp;
-      if (sqrt(v[0]) <= CG_RTOL * fnorm) break;
-      beta = v[1] / rz;
-      rz = v[1];
-      first = false;
+      ok = reduce3(acc);
+      if (!ok) break;
+      cur ^= 1;
+      if (sqrt(acc[2]) <= CG_RTOL * fnorm) break;
+      const double gamma_new = acc[0];
+      beta = gamma_new / gamma;
+      alpha = gamma_new / (acc[1] - beta * gamma_new / alpha);
+      gamma = gamma_new;
+      if (!isfinite(alpha)) break;
     }
     if (it > CG_MAXIT) it = CG_MAXIT;
   }
-  for (int i = tid; i < n; i += nthreads) xout[i] = (T)__ldcg(&x[i]);
-  if (tid == 0) { *cg.iters = it; atomicAdd(cg.iters_total, (unsigned long long)it); }
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) xout[i] = (T)__ldcg(&x[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *cg.iters = it;
+    atomicAdd(cg.iters_total, (unsigned long long)it);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -347,6 +401,7 @@ inline double bytes_A(const Level &l, int vbytes) { return (double)l.nnz * (vbyt
     int _g = row_blocks(l);                                                               \
     switch ((l).tpr) {                                                                    \
       case 1: KERNEL<1, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 2: KERNEL<2, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
       case 4: KERNEL<4, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
       case 8: KERNEL<8, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
       case 16: KERNEL<16, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;           \
@@ -366,7 +421,8 @@ void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KSta
   cudaMemsetAsync(h->cg.bar, 0, 2 * sizeof(unsigned), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->cg.grid);
-  cfg.blockDim = dim3(AMG_THREADS);
+  cfg.blockDim = dim3(h->cg.threads);
+  cfg.dynamicSmemBytes = h->cg.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -396,19 +452,25 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
     const T *dinv = LevelVec<T>::dinv(l);
     const T *val = LevelVec<T>::val(l);
     const double BA = bytes_A(l, (int)sz);
-    {
-      LaunchScope ls(h, s, PK_JACOBI0, k, 3.0 * sz * l.n);
-      k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, fk[k], dinv, omega, a, st);
-    }
-    for (int sw = 1; sw < nu_pre; ++sw) {
-      LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-      DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, a, fk[k], b, st);
-      std::swap(a, b);
-    }
-    cur[k] = a;
-    {
-      LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
-      DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, a, fk[k], b, st);
+    if (nu_pre == 1 && l.fuse_pre) {
+      LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
+      DISPATCH_TPR(l, k_residual0, l.n, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
+      cur[k] = a;
+    } else {
+      {
+        LaunchScope ls(h, s, PK_JACOBI0, k, 3.0 * sz * l.n);
+        k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, fk[k], dinv, omega, a, st);
+      }
+      for (int sw = 1; sw < nu_pre; ++sw) {
+        LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
+        DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, a, fk[k], b, st);
+        std::swap(a, b);
+      }
+      cur[k] = a;
+      {
+        LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
+        DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, a, fk[k], b, st);
+      }
     }
     Level &c = h->lev[k + 1];
     {
@@ -433,18 +495,28 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
       k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, final_out, st);
     } else {
-      T *o = (nu_post == 1) ? final_out : other;
-      {
+      // cur: current iterate; spare: a free buffer distinct from final_out
+      T *curb, *spare;
+      int sweeps = nu_post;
+      if (l.fuse_post) {
+        T *o = (nu_post == 1) ? final_out : other;
         LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
         DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, fk[k], o, st);
+        curb = o;
+        spare = in;
+        sweeps -= 1;
+      } else {
+        LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
+        k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, other, st);
+        curb = other;
+        spare = in;
       }
-      T *pp = o, *qq = in;
-      for (int sw = 1; sw < nu_post; ++sw) {
-        T *dst = (sw == nu_post - 1) ? final_out : qq;
+      for (int sw = 0; sw < sweeps; ++sw) {
+        T *dst = (sw == sweeps - 1) ? final_out : spare;
         LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, pp, fk[k], dst, st);
-        qq = pp;
-        pp = dst;
+        DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, curb, fk[k], dst, st);
+        spare = curb;
+        curb = dst;
       }
     }
     xc = final_out;
@@ -487,26 +559,18 @@ amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
   cg.n = c.n;
   size_t vb = sizeof(double) * (c.n + AMG_PAD);
   AMG_TRY(hier_alloc(h, (void **)&cg.x, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.r, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.z, vb));
   AMG_TRY(hier_alloc(h, (void **)&cg.p, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.p2, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.q, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.part, sizeof(double) * 4 * AMG_MAX_BLOCKS));
+  for (int b = 0; b < 2; ++b) {
+    AMG_TRY(hier_alloc(h, (void **)&cg.r[b], vb));
+    AMG_TRY(hier_alloc(h, (void **)&cg.w[b], vb));
+    AMG_TRY(hier_alloc(h, (void **)&cg.s[b], vb));
+  }
+  AMG_TRY(hier_alloc(h, (void **)&cg.part, sizeof(double) * 6 * AMG_MAX_BLOCKS));
   AMG_TRY(hier_alloc(h, (void **)&cg.bar, sizeof(unsigned) * 4));
   AMG_TRY(hier_alloc(h, (void **)&cg.iters, sizeof(int) * 4));
   AMG_TRY(hier_alloc(h, (void **)&cg.iters_total, sizeof(unsigned long long)));
   AMG_CUDA(cudaMemsetAsync(cg.iters_total, 0, sizeof(unsigned long long), s));
-  int occ64 = 0, occ32 = 0;
-  AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_coarse_cg<double>, AMG_THREADS, 0));
-  AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_coarse_cg<float>, AMG_THREADS, 0));
-  int occ = std::max(1, std::min(occ64, occ32));
-  int coop = 0;
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-  if (!coop) return AMG_ERR_UNSUPPORTED;
-  // a few warps of rows per block keeps the barrier wide enough but not wider
-  int want = cdiv(c.n, AMG_THREADS);
-  cg.grid = std::max(1, std::min(std::min(want, occ * h->num_sms), AMG_MAX_BLOCKS));
+  AMG_TRY(coarse_cg_config(c.n, &cg));
   return AMG_OK;
 }
 
@@ -514,6 +578,8 @@ __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__res
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
 }
+
+static void apply_tuned(amg_hierarchy *h);
 
 static int choose_tpr(const Level &l) {
   double avg = l.n ? (double)l.nnz / l.n : 0.0;
@@ -530,6 +596,8 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
   for (int k = 0; k <= h->L; ++k) {
     Level &l = h->lev[k];
     l.tpr = choose_tpr(l);
+    l.fuse_pre = 1;
+    l.fuse_post = 0;
     size_t vd = sizeof(double) * (l.n + AMG_PAD), vf = sizeof(float) * (l.n + AMG_PAD);
     if (!mixed) {
       AMG_TRY(hier_alloc(h, (void **)&l.f, vd));
@@ -548,6 +616,7 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
       count_launch(2);
     }
   }
+  apply_tuned(h);
   // Krylov work vectors at level 0 (FP64 in every precision)
   const int n = h->lev[0].n;
   size_t vd = sizeof(double) * (n + AMG_PAD);
@@ -559,6 +628,160 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
   AMG_CUDA(cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * 16, s));
   if (cudaMallocHost((void **)&h->st_host, sizeof(KState)) != cudaSuccess) { cudaGetLastError(); return AMG_ERR_OOM; }
   return amg_cuda_status(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: per level, times the row kernels' threads-per-row choices and the
+// fused / unfused variants of the first pre- and post-smoothing sweeps on the
+// level's own matrix, keeps the fastest, and caches the choice by level shape
+// (rows, nonzeros, precision) for every later setup in this process.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct TuneChoice { int tpr, fuse_pre, fuse_post; };
+std::mutex g_tune_mu;
+std::map<std::tuple<int, long long, int>, TuneChoice> g_tune;
+
+template <typename T>
+float time_launch(cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps, const std::function<void()> &fn) {
+  fn();  // warm-up
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, s);
+    fn();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    best = std::min(best, ms);
+  }
+  return best;
+}
+
+template <typename T>
+amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
+  cudaEvent_t ea, eb;
+  AMG_CUDA(cudaEventCreate(&ea));
+  AMG_CUDA(cudaEventCreate(&eb));
+  const T omega = (T)h->prm.omega;
+  const int reps = 3;
+  for (int k = 0; k < h->L; ++k) {
+    Level &l = h->lev[k];
+    const T *val = LevelVec<T>::val(l);
+    const T *dinv = LevelVec<T>::dinv(l);
+    T *f = LevelVec<T>::f(l), *x = LevelVec<T>::x(l), *t = LevelVec<T>::t(l), *y = LevelVec<T>::y(l);
+    const T *xc = LevelVec<T>::y(h->lev[k + 1]);
+    const double avg = l.n ? (double)l.nnz / l.n : 0.0;
+    cudaMemsetAsync(f, 0, sizeof(T) * l.n, s);
+    cudaMemsetAsync(x, 0, sizeof(T) * l.n, s);
+    cudaMemsetAsync((void *)xc, 0, sizeof(T) * h->lev[k + 1].n, s);
+    // threads per row: timed on the residual kernel
+    int best_tpr = l.tpr;
+    float best = 1e30f;
+    const int cands[] = {1, 2, 4, 8, 16, 32};
+    for (int tpr : cands) {
+      if (tpr > 1 && tpr > 4.0 * avg) break;
+      Level lt = l;
+      lt.tpr = tpr;
+      float ms = time_launch<T>(s, ea, eb, reps, [&]() {
+        DISPATCH_TPR(lt, k_residual, lt.n, lt.rp, lt.ci, val, x, f, t, (const KState *)nullptr);
+      });
+      if (ms < best) { best = ms; best_tpr = tpr; }
+    }
+    l.tpr = best_tpr;
+    // first presmoothing sweep: fused with the residual, or separate
+    float pre_fused = time_launch<T>(s, ea, eb, reps, [&]() {
+      DISPATCH_TPR(l, k_residual0, l.n, l.rp, l.ci, val, dinv, omega, f, x, t, (const KState *)nullptr);
+    });
+    float pre_split = time_launch<T>(s, ea, eb, reps, [&]() {
+      k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, f, dinv, omega, x, nullptr);
+      DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, x, f, t, (const KState *)nullptr);
+    });
+    l.fuse_pre = pre_fused <= pre_split ? 1 : 0;
+    // prolongation: fused into the first postsmoothing sweep, or separate
+    float post_fused = time_launch<T>(s, ea, eb, reps, [&]() {
+      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, f, y,
+                   (const KState *)nullptr);
+    });
+    float post_split = time_launch<T>(s, ea, eb, reps, [&]() {
+      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, x, l.agg, xc, t, nullptr);
+      DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, t, f, y, (const KState *)nullptr);
+    });
+    l.fuse_post = post_fused <= post_split ? 1 : 0;
+    count_launch(0);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[std::make_tuple(l.n, (long long)l.nnz, h->prm.precision)] = TuneChoice{l.tpr, l.fuse_pre, l.fuse_post};
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  return amg_cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+// Applies cached tuning choices to the levels of a new hierarchy.
+static void apply_tuned(amg_hierarchy *h) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  for (int k = 0; k < h->L; ++k) {
+    Level &l = h->lev[k];
+    auto it = g_tune.find(std::make_tuple(l.n, (long long)l.nnz, h->prm.precision));
+    if (it != g_tune.end()) {
+      l.tpr = it->second.tpr;
+      l.fuse_pre = it->second.fuse_pre;
+      l.fuse_post = it->second.fuse_post;
+    }
+  }
+}
+
+extern "C" amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream) {
+  if (!h) return AMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  AMG_CUDA(cudaStreamSynchronize(s));
+  amg_status st = h->prm.precision == AMG_FP64 ? tune_levels<double>(h, s) : tune_levels<float>(h, s);
+  reset_graphs(h);
+  AMG_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+extern "C" amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_pre, int fuse_post) {
+  if (!h || level < 0 || level > h->L) return AMG_ERR_INVALID_ARG;
+  if (tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return AMG_ERR_INVALID_ARG;
+  Level &l = h->lev[level];
+  l.tpr = tpr;
+  l.fuse_pre = fuse_pre ? 1 : 0;
+  l.fuse_post = fuse_post ? 1 : 0;
+  reset_graphs(h);
+  return AMG_OK;
+}
+
+extern "C" int amg_level_config(const amg_hierarchy *h, int level, int *tpr, int *fuse_pre, int *fuse_post) {
+  if (!h || level < 0 || level > h->L) return -1;
+  const Level &l = h->lev[level];
+  if (tpr) *tpr = l.tpr;
+  if (fuse_pre) *fuse_pre = l.fuse_pre;
+  if (fuse_post) *fuse_post = l.fuse_post;
+  return 0;
+}
+
+// Grid, block and shared-memory configuration of the persistent coarse CG.
+amg_status coarse_cg_config(int n, CoarseCG *cg) {
+  int dev = 0, sms = 152, coop = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop) return AMG_ERR_UNSUPPORTED;
+  AMG_CUDA(cudaFuncSetAttribute(k_coarse_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM_CAP));
+  AMG_CUDA(cudaFuncSetAttribute(k_coarse_cg<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, CG_SMEM_CAP));
+  int occ64 = 0, occ32 = 0;
+  AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ64, k_coarse_cg<double>, CG_THREADS, CG_SMEM_CAP));
+  AMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ32, k_coarse_cg<float>, CG_THREADS, CG_SMEM_CAP));
+  const int occ = std::min(occ64, occ32);
+  if (occ < 1) return AMG_ERR_UNSUPPORTED;
+  // one block per SM, at least 64 rows per block
+  cg->grid = std::max(1, std::min(std::min(occ * sms, cdiv(n, 64)), AMG_MAX_BLOCKS));
+  cg->threads = CG_THREADS;
+  cg->smem = CG_SMEM_CAP;
+  return AMG_OK;
 }
 
 extern "C" amg_status amg_vcycle(const amg_hierarchy *hc, const double *d_r, double *d_z, amg_stream_t stream) {

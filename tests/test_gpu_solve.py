@@ -117,8 +117,12 @@ def test_pcg_nonzero_initial_guess_and_edge_cases():
     # NaN in b
     bad = b.clone()
     bad[7] = float("nan")
-    info = amg.pcg_solve(h, bad, torch.zeros_like(b))
-    assert info.status != amg.AMG_OK
+    with pytest.raises(amg.AmgError) as e:
+        amg.pcg_solve(h, bad, torch.zeros_like(b))
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    with pytest.raises(amg.AmgError) as e:
+        amg.bicgstab_solve(h, bad, torch.zeros_like(b))
+    assert e.value.status == amg.AMG_ERR_INVALID_ARG
 
 
 def test_single_level_and_tiny_systems():
@@ -181,3 +185,41 @@ def test_full_size_lognormal_128_pcg():
     assert rel_err(xg, x_o) < SOLUTION_TOL
     idx = np.random.default_rng(0).integers(0, s.n, 1000)
     np.testing.assert_allclose(xg[idx], x_o[idx], rtol=1e-8, atol=1e-10 * np.abs(x_o).max())
+
+
+@pytest.mark.parametrize("tpr", [1, 2, 4, 8, 16, 32])
+def test_every_kernel_variant_matches_oracle(tpr):
+    """Every lanes-per-row choice and both fused/separate forms of the first
+    pre- and post-smoothing sweeps give the oracle's V-cycle."""
+    for make, kw in ((lambda: W.lognormal3d(20, seed=4), dict(coarse_max=300)),
+                     (lambda: W.fem_p1_jittered(45, seed=2), dict(coarse_max=60))):
+        s = make()
+        h, oh, b = setup_both(s, **kw)
+        z_o = oh.vcycle(s.b)
+        for fp in (0, 1):
+            for fq in (0, 1):
+                for k in range(h.num_levels):
+                    amg.amg_level_set_config(h, k, tpr, fp, fq)
+                z = torch.empty_like(b)
+                amg.amg_vcycle(h, b, z)
+                assert rel_err(z.cpu().numpy(), z_o) < VCYCLE_TOL_DENSE, (tpr, fp, fq)
+
+
+def test_autotune_keeps_results_and_caches_choice():
+    s = W.lognormal3d(36, seed=6)
+    h, oh, b = setup_both(s, coarse_max=600)
+    amg.amg_autotune(h)
+    cfg = [amg.amg_level_config(h, k) for k in range(h.num_levels)]
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < VCYCLE_TOL_DENSE
+    x = torch.zeros_like(b)
+    info = amg.pcg_solve(h, b, x, rtol=1e-8)
+    _, info_o = oh.pcg(s.b, rtol=1e-8)
+    assert abs(info.iterations - info_o.iterations) <= 1
+    # a new setup of the same matrix starts with the tuned configuration
+    rp, ci, val, _ = to_cuda(s)
+    h2 = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=600))
+    assert [amg.amg_level_config(h2, k) for k in range(h2.num_levels)][:-1] == cfg[:-1]
+    with pytest.raises(amg.AmgError):
+        amg.amg_level_set_config(h2, 0, 3, 0, 0)

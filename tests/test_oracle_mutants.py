@@ -30,9 +30,10 @@ MUTANTS = [
      "test_pcg_matches_dense_solve_to_1e10"),
     ("bicgstab_p_update", "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
      "test_krylov_finite_termination_two_eigenvalues"),
-    ("coarse_cg_steepest_descent", "double beta = rz_new / rz;\n      rz = rz_new;\n      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];",
-     "double beta = 0.0 * rz_new / rz;\n      rz = rz_new;\n      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];",
-     "test_coarse_cg_solver_agrees_with_dense"),
+    ("coarse_cg_steepest_descent", "      beta = gamma_new / gamma;\n", "      beta = 0.0 * gamma_new / gamma;\n",
+     "test_coarse_cg_solver_agrees_with_dense or test_coarse_cg_finite_termination_two_eigenvalues"),
+    ("coarse_cg_alpha_without_correction", "alpha = gamma_new / (delta - beta * gamma_new / alpha);",
+     "alpha = gamma_new / delta;", "test_coarse_cg_finite_termination_two_eigenvalues"),
     ("lu_no_pivoting", "if (fabs(a[(size_t)i * n + k]) > best)", "if (0 && fabs(a[(size_t)i * n + k]) > best)",
      "test_dense_lu_matches_numpy"),
 ]

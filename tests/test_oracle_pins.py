@@ -428,3 +428,16 @@ def test_krylov_finite_termination_two_eigenvalues():
     assert info.status == O.OK and info.iterations <= 2
     _, info = h.bicgstab(b, rtol=1e-13, max_iter=50)
     assert info.status == O.OK and info.iterations <= 2
+
+
+def test_coarse_cg_finite_termination_two_eigenvalues():
+    """A one-level hierarchy with the CG coarse solver: the V-cycle is a
+    Jacobi-PCG solve of A z = r.  On blockdiag([[a,-b],[-b,a]]) the operator
+    D^-1 A has exactly two eigenvalues, (a - b)/a and (a + b)/a, so CG ends
+    within two iterations and returns A^{-1} r."""
+    a = np.kron(np.eye(30), np.array([[4.0, -1.0], [-1.0, 4.0]]))
+    s = W.from_dense(a, np.random.default_rng(2).uniform(-1, 1, 60))
+    h = O.Hierarchy(s.rp, s.ci, s.val, max_levels=1, coarse_solver=2)
+    z = h.vcycle(s.b)
+    assert h.last_coarse_cg_iters <= 2
+    np.testing.assert_allclose(z, np.linalg.solve(a, s.b), rtol=1e-12)
