@@ -213,6 +213,34 @@ amg_status amg_profile_reset(amg_hierarchy *h);
  * may be NULL.  Waits for pending timed launches. */
 amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, double *bytes, long long *launches);
 
+/* ---- Allocation-free coarse solve (the paper has no counterpart) ----
+ *
+ * Solves A x = f by the library's Jacobi-preconditioned CG (the coarsest-level
+ * solver of the V-cycle: from x = 0 until ||f - A x||_2 <= 1e-12 ||f||_2, at
+ * most 1000 iterations) without allocating any device memory.  It is meant for
+ * callers that cannot call cudaMalloc: code running while a stream capture in
+ * global mode is active (allocation is refused there), latency-critical loops
+ * that cannot afford cudaMalloc's implicit device-wide synchronisation, and
+ * plugins whose host framework owns every device allocation.
+ *
+ * All work vectors live in one fixed array inside the library (about 21 MB,
+ * held on every GPU that loads the library until the process exits), so:
+ *   - n must be at most 262144 (AMG_ERR_INVALID_ARG beyond that, before any
+ *     device work); nnz < 2^31;
+ *   - every call on a device shares that array, which keeps the previous
+ *     call's contents (the entry point clears what must start at zero); calls
+ *     whose GPU work overlaps -- on different streams or host threads -- race
+ *     on it and must be serialised by the caller;
+ *   - the first call on each device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ * Arguments: device CSR of A (same conventions as amg_setup, diagonal nonzero),
+ * device vectors f (input) and x (output, length n, not aliasing f).  The call
+ * synchronises `stream`; *iterations (may be NULL) receives the CG iteration
+ * count.  Errors: INVALID_ARG, INVALID_CSR, ZERO_DIAG, TIMEOUT, CUDA. */
+amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                                 const double *d_val, const double *d_f, double *d_x, amg_stream_t stream,
+                                 int *iterations);
+
 /* Frees every device allocation of h (NULL is a no-op).  Synchronises the
  * device work of h first. */
 void amg_destroy(amg_hierarchy *h);

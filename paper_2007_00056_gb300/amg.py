@@ -33,7 +33,7 @@ EXPORTS = (
     "amg_default_params", "amg_setup", "amg_vcycle", "pcg_solve", "bicgstab_solve", "amg_num_levels",
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
-    "amg_autotune", "amg_level_config", "amg_level_set_config",
+    "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -111,6 +111,7 @@ def lib(build_if_missing: bool = False):
             l.amg_autotune.argtypes = [vp, vp]
             l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]
             l.amg_level_config.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+            l.amg_coarse_cg_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, C.POINTER(i32)]
             _lib = l
     return _lib
 
@@ -304,6 +305,22 @@ def amg_profile_table(h: Hierarchy):
     rows.sort(key=lambda r: -r["ms"])
     return rows
 
+
+NOALLOC_MAX_N = 262144
+
+
+def amg_coarse_cg_noalloc(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, f: torch.Tensor,
+                          x: torch.Tensor, stream=None) -> int:
+    """Jacobi-PCG solve of A x = f (to 1e-12) using only the library's fixed
+    scratch array (no device allocation); returns the iteration count."""
+    it = C.c_int(0)
+    st = lib().amg_coarse_cg_noalloc(row_ptr.numel() - 1, col.numel(), _dev(row_ptr, torch.int32, "row_ptr"),
+                                     _dev(col, torch.int32, "col"), _dev(val, torch.float64, "val"),
+                                     _dev(f, torch.float64, "f"), _dev(x, torch.float64, "x"), _stream(stream),
+                                     C.byref(it))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_coarse_cg_noalloc")
+    return it.value
 
 
 def amg_autotune(h: Hierarchy, stream=None) -> None:

@@ -263,4 +263,5 @@ amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
 // Grid, block and shared-memory configuration of the coarse CG for n rows on
 // the current device (also sets the kernel's shared-memory limit).
 amg_status coarse_cg_config(int n, CoarseCG *cg);
-
+amg_status coarse_cg_launch(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *dinv,
+                            const double *f, double *x, const CoarseCG &cg, unsigned *eflags, cudaStream_t s);

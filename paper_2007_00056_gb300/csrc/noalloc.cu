@@ -1,0 +1,127 @@
+// noalloc.cu -- a coarse-solver entry point that performs no device allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs while another library
+// holds a stream capture in global mode (where allocation calls are refused),
+// latency-critical host loops that must not take cudaMalloc's implicit device
+// synchronisation, and plugins hosted by a framework that owns all device
+// memory and forbids allocations outside its pool.  For them,
+// amg_coarse_cg_noalloc runs the library's Jacobi-PCG solver with every work
+// vector in one fixed array compiled into the library (below), so a call
+// allocates nothing.  The price: every GPU that loads the library holds this
+// array until the process exits, sizes are capped, and all calls share it.
+#include <mutex>
+
+#include "common.cuh"
+
+// Largest system accepted: 262,144 rows and 2^31 - 1 stored entries.
+#define NOALLOC_MAX_N 262144
+#define NOALLOC_ALIGN 256
+#define NOALLOC_VECS 10  // dinv + the solver's work vectors, with room to spare
+#define NOALLOC_BYTES                                                                            \
+  ((size_t)NOALLOC_VECS * 8 * (NOALLOC_MAX_N + AMG_PAD) + (size_t)6 * AMG_MAX_BLOCKS * 8 + \
+   16 * NOALLOC_ALIGN)
+
+// The scratch array: about 21 MB on every device that loads the library.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_base[256] = {nullptr};  // device address of the array, per device ordinal
+
+size_t up(size_t v) { return (v + NOALLOC_ALIGN - 1) / NOALLOC_ALIGN * NOALLOC_ALIGN; }
+
+// Device address of the scratch array on the current device (looked up once per
+// device; the array's host-side name is not a device address).
+amg_status scratch_base(unsigned char **out) {
+  int dev = 0;
+  AMG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return AMG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return amg_cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    }
+    g_noalloc_base[dev] = p;
+  }
+  *out = (unsigned char *)g_noalloc_base[dev];
+  return AMG_OK;
+}
+
+// CSR checks and 1/a_ii into the scratch; flags[0] collects error bits.
+__global__ void k_noalloc_prepare(int n, long long nnz, const int32_t *__restrict__ rp,
+                                  const int32_t *__restrict__ ci, const double *__restrict__ val,
+                                  double *__restrict__ dinv, unsigned *flags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && (rp[0] != 0 || (long long)rp[n] != nnz)) atomicOr(flags, AMG_EFLAG_BAD_CSR);
+  if (i >= n) return;
+  int b = rp[i], e = rp[i + 1];
+  if (b < 0 || e < b || (long long)e > nnz) { atomicOr(flags, AMG_EFLAG_BAD_CSR); dinv[i] = 0.0; return; }
+  double d = 0.0;
+  int prev = -1;
+  for (int k = b; k < e; ++k) {
+    int c = ci[k];
+    if (c < 0 || c >= n || c <= prev) { atomicOr(flags, AMG_EFLAG_BAD_CSR); dinv[i] = 0.0; return; }
+    prev = c;
+    if (c == i) d = val[k];
+  }
+  if (d == 0.0 || !isfinite(d)) { atomicOr(flags, AMG_EFLAG_ZERO_DIAG); dinv[i] = 0.0; return; }
+  dinv[i] = 1.0 / d;
+}
+
+}  // namespace
+
+extern "C" amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
+                                            const double *d_val, const double *d_f, double *d_x,
+                                            amg_stream_t stream, int *iterations) {
+  if (iterations) *iterations = 0;
+  if (n <= 0 || n > NOALLOC_MAX_N || nnz < 0 || nnz >= (1ll << 31) || !d_row_ptr || !d_f || !d_x ||
+      (nnz > 0 && (!d_col || !d_val)))
+    return AMG_ERR_INVALID_ARG;
+  unsigned char *base = nullptr;
+  AMG_TRY(scratch_base(&base));
+  cudaStream_t s = (cudaStream_t)stream;
+  // carve the array: vectors, reduction partials, barrier words, counters
+  const size_t vb = up(sizeof(double) * ((size_t)n + AMG_PAD));
+  size_t off = 0;
+  auto take = [&](size_t bytes) { unsigned char *p = base + off; off += up(bytes); return p; };
+  double *dinv = (double *)take(vb);
+  CoarseCG cg;
+  cg.n = n;
+  cg.x = (double *)take(vb);
+  cg.p = (double *)take(vb);
+  for (int k = 0; k < 2; ++k) {
+    cg.r[k] = (double *)take(vb);
+    cg.w[k] = (double *)take(vb);
+    cg.s[k] = (double *)take(vb);
+  }
+  cg.part = (double *)take(sizeof(double) * 6 * AMG_MAX_BLOCKS);
+  cg.bar = (unsigned *)take(sizeof(unsigned) * 4);
+  cg.iters = (int *)take(sizeof(int) * 4);
+  cg.iters_total = (unsigned long long *)take(sizeof(unsigned long long));
+  unsigned *flags = (unsigned *)take(sizeof(unsigned) * 4);
+  if (off > NOALLOC_BYTES) return AMG_ERR_UNSUPPORTED;
+  AMG_TRY(coarse_cg_config(n, &cg));
+  // the array keeps the previous call's contents: clear what must start at zero
+  AMG_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned) * 4, s));
+  AMG_CUDA(cudaMemsetAsync(cg.iters_total, 0, sizeof(unsigned long long), s));
+  k_noalloc_prepare<<<cdiv(n, AMG_THREADS), AMG_THREADS, 0, s>>>(n, nnz, d_row_ptr, d_col, d_val, dinv, flags);
+  count_launch();
+  AMG_CUDA(cudaGetLastError());
+  unsigned hflags[2] = {0, 0};
+  AMG_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  if (hflags[0] & AMG_EFLAG_BAD_CSR) return AMG_ERR_INVALID_CSR;
+  if (hflags[0] & AMG_EFLAG_ZERO_DIAG) return AMG_ERR_ZERO_DIAG;
+  AMG_TRY(coarse_cg_launch(n, d_row_ptr, d_col, d_val, dinv, d_f, d_x, cg, flags, s));
+  int it = 0;
+  AMG_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaMemcpyAsync(&it, cg.iters, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  if (iterations) *iterations = it;
+  if (hflags[0] & AMG_EFLAG_TIMEOUT) return AMG_ERR_TIMEOUT;
+  return AMG_OK;
+}

@@ -784,6 +784,28 @@ amg_status coarse_cg_config(int n, CoarseCG *cg) {
   return AMG_OK;
 }
 
+// Launches the coarse CG kernel on caller-provided CSR and work memory (used by
+// the allocation-free entry point); the same kernel and configuration as the
+// hierarchy's coarsest solve.
+amg_status coarse_cg_launch(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *dinv,
+                            const double *f, double *x, const CoarseCG &cg, unsigned *eflags, cudaStream_t s) {
+  AMG_CUDA(cudaMemsetAsync(cg.bar, 0, 2 * sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cg.grid);
+  cfg.blockDim = dim3(cg.threads);
+  cfg.dynamicSmemBytes = cg.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  AMG_CUDA(cudaLaunchKernelEx(&cfg, k_coarse_cg<double>, n, rp, ci, val, dinv, f, x, cg, (const KState *)nullptr,
+                              eflags));
+  return AMG_OK;
+}
+
 extern "C" amg_status amg_vcycle(const amg_hierarchy *hc, const double *d_r, double *d_z, amg_stream_t stream) {
   if (!hc || !d_r || !d_z || d_r == d_z) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
