@@ -139,14 +139,26 @@ def barrier(world):
 
 
 def allreduce_max(v: float, world: int) -> float:
+    """Max of a per-rank value over all ranks (the slowest rank's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
+def shard(items, rank: int, world: int):
+    """Round-robin share of independent work items for one rank (replicas)."""
+    return items[rank::world]
 
 
 # ---------------------------------------------------------------------------
@@ -288,7 +300,7 @@ def main():
     setup_t = [a.elapsed_time(bv) for a, bv in setup_ms]
     max_ms = allreduce_max(total_ms, world)
     ms_per_step = max_ms / args.steps
-    value = world * args.steps / (max_ms * 1e-3)
+    value = job_throughput(args.steps, world, max_ms)
     setup_mean = statistics.mean(setup_t)
     solve_mean = ms_per_step - setup_mean
 
@@ -352,7 +364,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
-    e2e_value = world * e2e_steps / (e2e_ms * 1e-3)
+    e2e_value = job_throughput(e2e_steps, world, e2e_ms)
 
     # CPU baseline: the oracle on this host's cores (rank 0, one GPU only)
     cpu = None
