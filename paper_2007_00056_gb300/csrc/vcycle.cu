@@ -260,7 +260,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   const int *lci = staged ? s_ci : ci + e0;
   GridBarrier gb{cg.bar, 0u};
   int slot = 0;
-  // block partial sums -> barrier -> every block sums the G partials in index order
+  // block partial sums -> barrier -> warp 0 sums the G partials in index order;
+  // the totals are valid in thread 0 only (it alone evaluates the scalars)
   auto reduce3 = [&](double (&v)[3]) -> bool {
     block_sum<3>(v, red_sh);
     double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
@@ -277,21 +278,18 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
         b += __ldcg(&part[AMG_MAX_BLOCKS + k]);
         c += __ldcg(&part[2 * AMG_MAX_BLOCKS + k]);
       }
-      a = warp_sum(a);
-      b = warp_sum(b);
-      c = warp_sum(c);
-      if (threadIdx.x == 0) { red[0] = a; red[1] = b; red[2] = c; }
+      v[0] = warp_sum(a);
+      v[1] = warp_sum(b);
+      v[2] = warp_sum(c);
     }
-    __syncthreads();
-    v[0] = red[0];
-    v[1] = red[1];
-    v[2] = red[2];
     slot ^= 1;
     return ok;
   };
   auto row_begin = [&](int i) { return staged ? s_rp[i - r0] : __ldg(&rp[i]) - e0; };
 
   double *x = cg.x, *p = cg.p;
+  // scalars broadcast from thread 0: [0] alpha, [1] beta, [2] stop flag
+  __shared__ double sc[3];
   // initial phase: r0 = f, u0 = D^-1 f, w0 = A u0, s = p = x = 0
   double v[3] = {0.0, 0.0, 0.0};
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
@@ -313,13 +311,22 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     v[2] += fi * fi;
   }
   bool ok = reduce3(v);
-  const double fnorm = sqrt(v[2]);
+  // thread 0 keeps the recurrence scalars
+  double fnorm = 0.0, gamma = 0.0, alpha_t = 0.0, beta_t = 0.0;
+  if (threadIdx.x == 0) {
+    fnorm = sqrt(v[2]);
+    gamma = v[0];
+    alpha_t = v[0] / v[1];
+    sc[0] = alpha_t;
+    sc[1] = 0.0;
+    sc[2] = (fnorm > 0.0 && ok && fail_sh == 0) ? 0.0 : 1.0;
+  }
+  __syncthreads();
   int it = 0;
-  if (ok && fnorm > 0.0) {
-    double gamma = v[0];
-    double alpha = v[0] / v[1], beta = 0.0;
+  if (sc[2] == 0.0) {
     int cur = 0;
     for (it = 1; it <= CG_MAXIT; ++it) {
+      const double alpha = sc[0], beta = sc[1];
       const double *ro = cg.r[cur], *wo = cg.w[cur], *so = cg.s[cur];
       double *rn = cg.r[cur ^ 1], *wn = cg.w[cur ^ 1], *sn = cg.s[cur ^ 1];
       double acc[3] = {0.0, 0.0, 0.0};
@@ -347,14 +354,22 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
         acc[2] += rnew * rnew;
       }
       ok = reduce3(acc);
-      if (!ok) break;
       cur ^= 1;
-      if (sqrt(acc[2]) <= CG_RTOL * fnorm) break;
-      const double gamma_new = acc[0];
-      beta = gamma_new / gamma;
-      alpha = gamma_new / (acc[1] - beta * gamma_new / alpha);
-      gamma = gamma_new;
-      if (!isfinite(alpha)) break;
+      if (threadIdx.x == 0) {
+        bool stop = !ok || fail_sh != 0 || sqrt(acc[2]) <= CG_RTOL * fnorm;
+        if (!stop) {
+          const double gamma_new = acc[0];
+          beta_t = gamma_new / gamma;
+          alpha_t = gamma_new / (acc[1] - beta_t * gamma_new / alpha_t);
+          gamma = gamma_new;
+          stop = !isfinite(alpha_t);
+        }
+        sc[0] = alpha_t;
+        sc[1] = beta_t;
+        sc[2] = stop ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      if (sc[2] != 0.0) break;
     }
     if (it > CG_MAXIT) it = CG_MAXIT;
   }
