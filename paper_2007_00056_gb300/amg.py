@@ -33,7 +33,7 @@ EXPORTS = (
     "amg_default_params", "amg_setup", "amg_vcycle", "pcg_solve", "bicgstab_solve", "amg_num_levels",
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
-    "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config",
+    "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -109,6 +109,8 @@ def lib(build_if_missing: bool = False):
             l.amg_profile_reset.argtypes = [vp]
             l.amg_profile_read.argtypes = [vp, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_longlong)]
             l.amg_autotune.argtypes = [vp, vp]
+            l.amg_batch_pcg.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, i32, i32, vp,
+                                        C.POINTER(amg_solve_info)]
             l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]
             l.amg_level_config.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             l.amg_coarse_cg_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, C.POINTER(i32)]
@@ -342,3 +344,20 @@ def amg_level_set_config(h: Hierarchy, level: int, tpr: int, fuse_pre: bool, fus
     st = lib().amg_level_set_config(h.handle, int(level), int(tpr), int(bool(fuse_pre)), int(bool(fuse_post)))
     if st != AMG_OK:
         raise AmgError(st, "amg_level_set_config")
+
+
+def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible: bool = False, stream=None):
+    """Solves len(hs) systems in one launch (one thread block per system).
+    Returns the list of per-system solve infos; raises AmgError only for
+    errors other than non-convergence or breakdown."""
+    k = len(hs)
+    if not (len(bs) == len(xs) == k) or k == 0:
+        raise ValueError("hs, bs and xs must have the same non-zero length")
+    H = (C.c_void_p * k)(*[h.handle for h in hs])
+    B = (C.c_void_p * k)(*[_dev(b, torch.float64, "b") for b in bs])
+    X = (C.c_void_p * k)(*[_dev(x, torch.float64, "x") for x in xs])
+    infos = (amg_solve_info * k)()
+    st = lib().amg_batch_pcg(k, H, B, X, float(rtol), int(max_iter), int(bool(flexible)), _stream(stream), infos)
+    if st not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN):
+        raise AmgError(st, "amg_batch_pcg")
+    return list(infos)

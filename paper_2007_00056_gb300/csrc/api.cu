@@ -1,5 +1,7 @@
 // api.cu -- small C-ABI entry points and host helpers shared by the library.
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -53,13 +55,75 @@ amg_status amg_cuda_status(cudaError_t e) {
   return AMG_ERR_CUDA;
 }
 
-amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+namespace {
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[256] = {nullptr};
+
+// The library's memory pool on the current device, created on first use with
+// a release threshold that keeps freed blocks for reuse by later setups.
+cudaMemPool_t lib_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) { cudaGetLastError(); return nullptr; }
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+}  // namespace
+
+amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = lib_pool();
+  cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes ? bytes : 16, pool, s) : cudaMalloc(p, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
     return AMG_ERR_OOM;
   }
+  return AMG_OK;
+}
+
+void pool_free(void *p, cudaStream_t s) {
+  if (p && cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
+}
+
+// Small pinned host buffers (<= 256 bytes) for device-to-host status reads,
+// carved from 64 KB pinned chunks and recycled, so a setup pays no
+// cudaMallocHost.
+namespace {
+std::mutex g_pin_mu;
+std::vector<void *> g_pin_free;
+}  // namespace
+
+void *pinned_small_alloc() {
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  if (g_pin_free.empty()) {
+    void *chunk = nullptr;
+    if (cudaMallocHost(&chunk, 65536) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    for (int k = 0; k < 256; ++k) g_pin_free.push_back((char *)chunk + 256 * k);
+  }
+  void *p = g_pin_free.back();
+  g_pin_free.pop_back();
+  memset(p, 0, 256);
+  return p;
+}
+
+void pinned_small_free(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pin_mu);
+  g_pin_free.push_back(p);
+}
+
+amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes) {
+  AMG_TRY(pool_alloc(p, bytes, h->stream));
   h->allocs.push_back(*p);
   return AMG_OK;
 }
@@ -143,9 +207,9 @@ extern "C" void amg_destroy(amg_hierarchy *h) {
   if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
   prof_flush(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
-  for (void *p : h->allocs) cudaFree(p);
-  if (h->st_host) cudaFreeHost(h->st_host);
-  if (h->eflags_host) cudaFreeHost(h->eflags_host);
+  for (void *p : h->allocs) pool_free(p, nullptr);
+  pinned_small_free(h->st_host);
+  pinned_small_free(h->eflags_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   cudaGetLastError();
   delete h;

@@ -1,0 +1,366 @@
+// batch.cu -- many AMG-PCG solves in one persistent launch.
+//
+// Each thread block owns one system of the batch and runs its whole flexible
+// PCG (Algorithm 4) with the V-cycle of Algorithm 1 as preconditioner: every
+// level of the hierarchy, smoothing, residual, restriction, dense coarsest
+// solve and prolongation, separated by block barriers only.  All reductions
+// are block reductions in a fixed order, so a system's iterates do not depend
+// on which other systems share the launch: a solve in a batch is bitwise the
+// solve alone.  Systems are read through per-hierarchy device descriptors
+// (the levels' CSR arrays and work vectors already owned by each hierarchy),
+// i.e. the batch is the block-diagonal concatenation of its systems without
+// copying any of them.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+#define BATCH_THREADS 512
+#define BATCH_MAX_COARSE 2048  // largest dense coarsest level a batched system may have
+
+struct BatchLevel {
+  int n, nc;
+  const int32_t *rp, *ci;
+  const void *val, *dinv;  // T-typed (double or float)
+  const int32_t *agg, *mrp, *mem;
+  void *f, *x, *t, *y;     // T-typed level vectors
+};
+
+struct BatchSys {
+  int L, n, nL;
+  double omega;
+  int nu_pre, nu_post;
+  BatchLevel lev[AMG_MAX_LEVELS];
+  const double *ainv;                      // dense inverse of the coarsest level
+  const int32_t *rp0, *ci0;
+  const double *val0;                      // level-0 FP64 matrix for the outer iteration
+  double *r, *z, *p, *q, *rold;            // FP64 Krylov vectors
+  double *f64c, *x64c;                     // FP64 coarse right-hand side / solution (FP32 mode)
+};
+
+struct BatchJob {
+  const BatchSys *sys;
+  const double *b;
+  double *x;
+};
+
+struct BatchInfo {
+  int iterations, status;
+  double rel, rel_true;
+};
+
+// ---------------------------------------------------------------------------
+// block-scope helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bsum(double v, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double s = lane < nw ? sh[lane] : 0.0;
+  s = warp_sum(s);
+  return s;  // every warp computes the same total in the same order
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ T brow(const int32_t *rp, const int32_t *ci, const V *val, const T *x, int i) {
+  T s = T(0);
+  for (int e = rp[i]; e < rp[i + 1]; ++e) s += (T)val[e] * x[ci[e]];
+  return s;
+}
+
+// One V-cycle of the system from a zero guess: out0 = M^{-1} f0 (level-0 vectors of type T).
+template <typename T>
+__device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
+  const int L = S.L;
+  const T omega = (T)S.omega;
+  const T *fk[AMG_MAX_LEVELS];
+  T *cur[AMG_MAX_LEVELS];
+  for (int k = 0; k <= L; ++k) fk[k] = k == 0 ? f0 : (const T *)S.lev[k].f;
+  for (int k = 0; k < L; ++k) {
+    const BatchLevel &l = S.lev[k];
+    const T *val = (const T *)l.val, *dinv = (const T *)l.dinv;
+    T *a = (T *)l.x, *b = (T *)l.t;
+    const T *f = fk[k];
+    for (int i = threadIdx.x; i < l.n; i += blockDim.x) a[i] = omega * (dinv[i] * f[i]);
+    __syncthreads();
+    for (int sw = 1; sw < S.nu_pre; ++sw) {
+      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+        b[i] = a[i] + omega * (dinv[i] * (f[i] - brow<T, T>(l.rp, l.ci, val, a, i)));
+      __syncthreads();
+      T *tmp = a; a = b; b = tmp;
+    }
+    cur[k] = a;
+    for (int i = threadIdx.x; i < l.n; i += blockDim.x) b[i] = f[i] - brow<T, T>(l.rp, l.ci, val, a, i);
+    __syncthreads();
+    T *fc = (T *)S.lev[k + 1].f;
+    for (int I = threadIdx.x; I < l.nc; I += blockDim.x) {
+      int e0 = l.mrp[I], e1 = l.mrp[I + 1];
+      T s = b[l.mem[e0]];
+      for (int m = e0 + 1; m < e1; ++m) s += b[l.mem[m]];
+      fc[I] = s;
+    }
+    __syncthreads();
+  }
+  // coarsest level: x_L = A_L^{-1} f_L (FP64 accumulation), warp per row
+  T *xL = (L == 0) ? out0 : (T *)S.lev[L].y;
+  {
+    const T *fL = fk[L];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < S.nL; i += nw) {
+      const double *row = S.ainv + (size_t)i * S.nL;
+      double s = 0.0;
+      for (int j = lane; j < S.nL; j += 32) s += row[j] * (double)fL[j];
+      s = warp_sum(s);
+      if (lane == 0) xL[i] = (T)s;
+    }
+    __syncthreads();
+  }
+  T *xc = xL;
+  for (int k = L - 1; k >= 0; --k) {
+    const BatchLevel &l = S.lev[k];
+    const T *val = (const T *)l.val, *dinv = (const T *)l.dinv;
+    const T *f = fk[k];
+    T *fin = (k == 0) ? out0 : (T *)l.y;
+    T *in = cur[k];
+    T *other = (in == (T *)l.x) ? (T *)l.t : (T *)l.x;
+    // prolongation into `other`, then the post-smoothing sweeps, the last into fin
+    T *dst0 = S.nu_post == 0 ? fin : other;
+    for (int i = threadIdx.x; i < l.n; i += blockDim.x) dst0[i] = in[i] + xc[l.agg[i]];
+    __syncthreads();
+    T *c = dst0, *spare = in;
+    for (int sw = 0; sw < S.nu_post; ++sw) {
+      T *dst = (sw == S.nu_post - 1) ? fin : spare;
+      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+        dst[i] = c[i] + omega * (dinv[i] * (f[i] - brow<T, T>(l.rp, l.ci, val, c, i)));
+      __syncthreads();
+      spare = c;
+      c = dst;
+    }
+    xc = fin;
+  }
+}
+
+// z = M^{-1} r in FP64 at the interface; T is the V-cycle's arithmetic type.
+template <typename T>
+__device__ void b_precond(const BatchSys &S, const double *r, double *z);
+
+template <>
+__device__ void b_precond<double>(const BatchSys &S, const double *r, double *z) {
+  b_vcycle<double>(S, r, z);
+}
+
+template <>
+__device__ void b_precond<float>(const BatchSys &S, const double *r, double *z) {
+  float *f0 = (float *)S.lev[0].f, *y0 = (float *)S.lev[0].y;
+  for (int i = threadIdx.x; i < S.n; i += blockDim.x) f0[i] = (float)r[i];
+  __syncthreads();
+  b_vcycle<float>(S, f0, y0);
+  for (int i = threadIdx.x; i < S.n; i += blockDim.x) z[i] = (double)y0[i];
+  __syncthreads();
+}
+
+// Flexible (or not) AMG-PCG of Algorithm 4 for the block's system.
+template <typename T>
+__global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const BatchJob *__restrict__ jobs,
+                                                              double rtol, int max_iter, int flexible,
+                                                              BatchInfo *__restrict__ info) {
+  __shared__ double sh[32];
+  const int sidx = blockIdx.x;
+  if (sidx >= nsys) return;
+  const BatchSys &S = *jobs[sidx].sys;
+  const double *b = jobs[sidx].b;
+  double *x = jobs[sidx].x;
+  const int n = S.n;
+  double *r = S.r, *z = S.z, *p = S.p, *q = S.q, *rold = S.rold;
+  // r = b - A x
+  double bb = 0.0, rr = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
+    r[i] = ri;
+    bb += b[i] * b[i];
+    rr += ri * ri;
+  }
+  bb = bsum(bb, sh);
+  rr = bsum(rr, sh);
+  const double bnorm = sqrt(bb);
+  double rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
+  int it = 0, status = AMG_ERR_NOT_CONVERGED;
+  if (!isfinite(bb) || !isfinite(rr)) {
+    status = AMG_ERR_INVALID_ARG;
+  } else if (bnorm == 0.0) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    status = AMG_OK;
+  } else if (rel <= rtol) {
+    status = AMG_OK;
+  } else if (max_iter > 0) {
+    __syncthreads();
+    b_precond<T>(S, r, z);
+    double rz = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
+    rz = bsum(rz, sh);
+    for (it = 1; it <= max_iter; ++it) {
+      __syncthreads();
+      double pq = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double qi = brow<double, double>(S.rp0, S.ci0, S.val0, p, i);
+        q[i] = qi;
+        pq += p[i] * qi;
+      }
+      pq = bsum(pq, sh);
+      if (pq == 0.0 || !isfinite(pq) || !isfinite(rz)) { status = AMG_ERR_BREAKDOWN; break; }
+      const double alpha = rz / pq;
+      double r2 = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        x[i] = x[i] + alpha * p[i];
+        double ri = r[i];
+        if (flexible) rold[i] = ri;
+        ri = ri - alpha * q[i];
+        r[i] = ri;
+        r2 += ri * ri;
+      }
+      r2 = bsum(r2, sh);
+      rel = sqrt(r2) / bnorm;
+      if (rel <= rtol) { status = AMG_OK; break; }
+      if (!isfinite(rel)) { status = AMG_ERR_BREAKDOWN; break; }
+      if (it == max_iter) break;
+      __syncthreads();
+      b_precond<T>(S, r, z);
+      double rzn = 0.0, zd = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        rzn += r[i] * z[i];
+        if (flexible) zd += z[i] * (r[i] - rold[i]);
+      }
+      rzn = bsum(rzn, sh);
+      if (flexible) zd = bsum(zd, sh);
+      const double beta = (flexible ? zd : rzn) / rz;
+      if (!isfinite(beta)) { status = AMG_ERR_BREAKDOWN; break; }
+      rz = rzn;
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+    }
+    if (it > max_iter) it = max_iter;
+  }
+  __syncthreads();
+  // true relative residual from x
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
+    tr += ri * ri;
+  }
+  tr = bsum(tr, sh);
+  if (threadIdx.x == 0) {
+    info[sidx].iterations = it;
+    info[sidx].status = status;
+    info[sidx].rel = rel;
+    info[sidx].rel_true = bnorm > 0.0 ? sqrt(tr) / bnorm : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+// Builds (once) the device descriptor of a hierarchy for batched solves.
+amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **out) {
+  if (h->batch_desc) { *out = (const BatchSys *)h->batch_desc; return AMG_OK; }
+  if (!h->dense || h->lev[h->L].n > BATCH_MAX_COARSE) return AMG_ERR_UNSUPPORTED;
+  if (h->prm.precision == AMG_FP16_STORAGE) return AMG_ERR_UNSUPPORTED;
+  const bool f32 = h->prm.precision == AMG_FP32;
+  BatchSys d = {};
+  d.L = h->L;
+  d.n = h->lev[0].n;
+  d.nL = h->lev[h->L].n;
+  d.omega = h->prm.omega;
+  d.nu_pre = h->prm.nu_pre;
+  d.nu_post = h->prm.nu_post;
+  for (int k = 0; k <= h->L; ++k) {
+    Level &l = h->lev[k];
+    BatchLevel &b = d.lev[k];
+    b.n = l.n;
+    b.nc = k < h->L ? h->lev[k + 1].n : 0;
+    b.rp = l.rp;
+    b.ci = l.ci;
+    b.val = f32 ? (const void *)l.val32 : (const void *)l.val;
+    b.dinv = f32 ? (const void *)l.dinv32 : (const void *)l.dinv;
+    b.agg = l.agg;
+    b.mrp = l.mrp;
+    b.mem = l.mem;
+    b.f = f32 ? (void *)l.f32 : (void *)l.f;
+    b.x = f32 ? (void *)l.x32 : (void *)l.x;
+    b.t = f32 ? (void *)l.t32 : (void *)l.t;
+    b.y = f32 ? (void *)l.y32 : (void *)l.y;
+  }
+  d.ainv = h->ainv;
+  d.rp0 = h->lev[0].rp;
+  d.ci0 = h->lev[0].ci;
+  d.val0 = h->lev[0].val;
+  d.r = h->kr;
+  d.z = h->kz;
+  d.p = h->kp;
+  d.q = h->kq;
+  d.rold = h->krold;
+  void *dev = nullptr;
+  AMG_TRY(hier_alloc(h, &dev, sizeof(BatchSys)));
+  AMG_CUDA(cudaMemcpyAsync(dev, &d, sizeof(BatchSys), cudaMemcpyHostToDevice, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  h->batch_desc = dev;
+  *out = (const BatchSys *)dev;
+  return AMG_OK;
+}
+
+}  // namespace
+
+extern "C" amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const double *const *d_b,
+                                    double *const *d_x, double rtol, int max_iter, int flexible,
+                                    amg_stream_t stream, amg_solve_info *infos) {
+  if (nsys <= 0 || !hs || !d_b || !d_x || !(rtol >= 0.0) || max_iter < 0) return AMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int prec = -1;
+  std::vector<BatchJob> jobs(nsys);
+  for (int i = 0; i < nsys; ++i) {
+    if (!hs[i] || !d_b[i] || !d_x[i]) return AMG_ERR_INVALID_ARG;
+    if (prec < 0) prec = hs[i]->prm.precision;
+    if (hs[i]->prm.precision != prec) return AMG_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return AMG_ERR_INVALID_ARG;  // a hierarchy's work vectors serve one solve
+    AMG_TRY(batch_descriptor(hs[i], s, &jobs[i].sys));
+    jobs[i].b = d_b[i];
+    jobs[i].x = d_x[i];
+  }
+  BatchJob *d_jobs = nullptr;
+  BatchInfo *d_info = nullptr;
+  AMG_TRY(pool_alloc((void **)&d_jobs, sizeof(BatchJob) * nsys, s));
+  if (pool_alloc((void **)&d_info, sizeof(BatchInfo) * nsys, s) != AMG_OK) {
+    pool_free(d_jobs, s);
+    return AMG_ERR_OOM;
+  }
+  std::vector<BatchInfo> hinfo(nsys);
+  cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(BatchJob) * nsys, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    if (prec == AMG_FP32)
+      k_batch_pcg<float><<<nsys, BATCH_THREADS, 0, s>>>(nsys, d_jobs, rtol, max_iter, flexible, d_info);
+    else
+      k_batch_pcg<double><<<nsys, BATCH_THREADS, 0, s>>>(nsys, d_jobs, rtol, max_iter, flexible, d_info);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo.data(), d_info, sizeof(BatchInfo) * nsys, cudaMemcpyDeviceToHost, s);
+  pool_free(d_jobs, s);
+  pool_free(d_info, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return amg_cuda_status(e);
+  amg_status worst = AMG_OK;
+  for (int i = 0; i < nsys; ++i) {
+    if (infos) {
+      infos[i].iterations = hinfo[i].iterations;
+      infos[i].rel_res_recurrence = hinfo[i].rel;
+      infos[i].rel_res_true = hinfo[i].rel_true;
+      infos[i].status = (amg_status)hinfo[i].status;
+    }
+    if (hinfo[i].status != AMG_OK && worst == AMG_OK) worst = (amg_status)hinfo[i].status;
+  }
+  return worst;
+}

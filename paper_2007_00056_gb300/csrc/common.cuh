@@ -51,8 +51,9 @@ struct Level {
   int32_t *rp = nullptr, *ci = nullptr;
   double *val = nullptr, *dinv = nullptr;
   float *val32 = nullptr, *dinv32 = nullptr;
-  __half *val16 = nullptr;   // values of D^-1/2 A D^-1/2
-  float *dsq = nullptr;      // d_i^{-1/2}
+  __half *val16 = nullptr;   // values of D^-1/2 A D^-1/2 (FP16 storage mode, levels < L)
+  float *sig = nullptr;      // sqrt(a_ii)        (FP16 storage mode)
+  float *isig = nullptr;     // 1 / sqrt(a_ii)    (FP16 storage mode)
   int32_t *agg = nullptr;    // n, into level k+1
   int32_t *mrp = nullptr;    // n_{k+1}+1
   int32_t *mem = nullptr;    // n
@@ -116,11 +117,13 @@ struct amg_hierarchy {
   unsigned *eflags = nullptr;   // device error bits
   unsigned *eflags_host = nullptr;
   std::vector<void *> allocs;
+  cudaStream_t stream = nullptr;       // stream of amg_setup (stream-ordered allocations)
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr;
   long long g_pcg_nodes = 0, g_bicg_nodes = 0;
   int graphs_ok = 1;
   Profiler prof;
+  void *batch_desc = nullptr;  // device descriptor for batched solves (built on first use)
 };
 
 // Kernel launches issued by this library since it was loaded (graph replays
@@ -151,6 +154,13 @@ struct LaunchScope {
 // ---------------------------------------------------------------------------
 amg_status amg_cuda_status(cudaError_t e);
 amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes);
+// Stream-ordered allocation from the library's own device memory pool (freed
+// memory stays in the pool for the next setup; no implicit device sync).
+amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s);
+void pool_free(void *p, cudaStream_t s);
+// Recycled pinned host buffers of 256 bytes (status and counter read-backs).
+void *pinned_small_alloc();
+void pinned_small_free(void *p);
 #define AMG_TRY(x)                              \
   do {                                          \
     amg_status _s = (x);                        \

@@ -85,11 +85,20 @@ __global__ void k_hem_init(int n, int32_t *mate, int32_t *frontier) {
   if (i < n) { mate[i] = HEM_FREE; frontier[i] = i; }
 }
 
+// Rounds run in batches between host checks: a round reads the frontier size
+// left by the previous round (nf_dev) and does nothing once a previous round
+// has paired nobody (prev_pairs == 0), i.e. after the fixed point.
+__device__ __forceinline__ int round_frontier(int nf_host, const int *nf_dev, const int *prev_pairs) {
+  if (prev_pairs && *prev_pairs == 0) return 0;
+  return nf_dev ? *nf_dev : nf_host;
+}
+
 // Each free node of the frontier picks its heaviest free neighbour (equal
 // weights: smaller index); -1 if it has none.
-__global__ void k_hem_pick(int nf, const int32_t *__restrict__ frontier, const int32_t *__restrict__ rp,
-                           const int32_t *__restrict__ ci, const double *__restrict__ w,
+__global__ void k_hem_pick(int nf_host, const int *nf_dev, const int *prev_pairs, const int32_t *__restrict__ frontier,
+                           const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
                            const int32_t *__restrict__ mate, int32_t *__restrict__ pick) {
+  const int nf = round_frontier(nf_host, nf_dev, prev_pairs);
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nf) return;
   int i = frontier[t];
@@ -108,8 +117,10 @@ __global__ void k_hem_pick(int nf, const int32_t *__restrict__ frontier, const i
 
 // Mutual picks become pairs; nodes that still had a free neighbour stay in the
 // frontier.  cnt[0] += pairs formed, cnt[1] = size of the next frontier.
-__global__ void k_hem_match(int nf, const int32_t *__restrict__ frontier, const int32_t *__restrict__ pick,
+__global__ void k_hem_match(int nf_host, const int *nf_dev, const int *prev_pairs,
+                            const int32_t *__restrict__ frontier, const int32_t *__restrict__ pick,
                             int32_t *__restrict__ mate, int32_t *__restrict__ next, int *cnt) {
+  const int nf = round_frontier(nf_host, nf_dev, prev_pairs);
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nf) return;
   int i = frontier[t];
@@ -502,40 +513,35 @@ struct Csr {
   double *val = nullptr;
 };
 
-amg_status dev_alloc(void **p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
-  if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; return AMG_ERR_OOM; }
-  return AMG_OK;
-}
-
-void free_csr(Csr &c) {
-  cudaFree(c.rp); cudaFree(c.ci); cudaFree(c.val);
+void free_csr(Csr &c, cudaStream_t st) {
+  pool_free(c.rp, st); pool_free(c.ci, st); pool_free(c.val, st);
   c = Csr();
 }
 
-amg_status scratch_alloc(Scratch &s, int n, long long nnz) {
+amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
   int tiles = cdiv(std::max(n, 1), SCAN_TILE);
-  AMG_TRY(dev_alloc((void **)&s.w, sizeof(double) * (nnz + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.mate, sizeof(int32_t) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.pick, sizeof(int32_t) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.fa, sizeof(int32_t) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.fb, sizeof(int32_t) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.first, sizeof(int32_t) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.flag, sizeof(int) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.id, sizeof(int) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.count, sizeof(int) * (n + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&s.tiles, sizeof(int) * (tiles + 8)));
-  AMG_TRY(dev_alloc((void **)&s.cnt, sizeof(int) * 8));
-  if (cudaMallocHost((void **)&s.host, sizeof(int) * 8) != cudaSuccess) { cudaGetLastError(); return AMG_ERR_OOM; }
+  AMG_TRY(pool_alloc((void **)&s.w, sizeof(double) * (nnz + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.mate, sizeof(int32_t) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.pick, sizeof(int32_t) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.fa, sizeof(int32_t) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.fb, sizeof(int32_t) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.first, sizeof(int32_t) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.flag, sizeof(int) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.id, sizeof(int) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.count, sizeof(int) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.tiles, sizeof(int) * (tiles + 8), st));
+  AMG_TRY(pool_alloc((void **)&s.cnt, sizeof(int) * 40, st));
+  s.host = (int *)pinned_small_alloc();
+  if (!s.host) return AMG_ERR_OOM;
   s.cap_n = n;
   s.cap_nnz = nnz;
   return AMG_OK;
 }
 
-void scratch_free(Scratch &s) {
-  cudaFree(s.w); cudaFree(s.mate); cudaFree(s.pick); cudaFree(s.fa); cudaFree(s.fb); cudaFree(s.first);
-  cudaFree(s.flag); cudaFree(s.id); cudaFree(s.count); cudaFree(s.tiles); cudaFree(s.cnt);
-  if (s.host) cudaFreeHost(s.host);
+void scratch_free(Scratch &s, cudaStream_t st) {
+  void *ps[] = {s.w, s.mate, s.pick, s.fa, s.fb, s.first, s.flag, s.id, s.count, s.tiles, s.cnt};
+  for (void *p : ps) pool_free(p, st);
+  pinned_small_free(s.host);
   s = Scratch();
 }
 
@@ -564,43 +570,53 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   int nf = n, r = 0;
   int32_t *fa = S.fa, *fb = S.fb;
   const int round_cap = 4 * n + 16;  // each productive round pairs >= 1 node
-  for (;;) {
-    ++r;
+  int batch = 4;                     // rounds per host check: 4, 8, then 16
+  bool finished = false;
+  while (!finished) {
     if (r > round_cap) return AMG_ERR_TIMEOUT;
-    cudaMemsetAsync(S.cnt, 0, sizeof(int) * 2, st);
-    if (nf > 0) {
-      k_hem_pick<<<cdiv(nf, T), T, 0, st>>>(nf, fa, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
-      k_hem_match<<<cdiv(nf, T), T, 0, st>>>(nf, fa, S.pick, S.mate, fb, S.cnt); count_launch();
+    AMG_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 2 * batch, st));
+    const int grid = cdiv(std::max(nf, 1), T);
+    int32_t *ba = fa, *bb = fb;
+    for (int b = 0; b < batch; ++b) {
+      const int *nf_dev = b ? S.cnt + 2 * (b - 1) + 1 : nullptr;
+      const int *prev = b ? S.cnt + 2 * (b - 1) : nullptr;
+      k_hem_pick<<<grid, T, 0, st>>>(nf, nf_dev, prev, ba, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
+      k_hem_match<<<grid, T, 0, st>>>(nf, nf_dev, prev, ba, S.pick, S.mate, bb, S.cnt + 2 * b); count_launch();
+      std::swap(ba, bb);
     }
-    cudaMemcpyAsync(S.host, S.cnt, sizeof(int) * 2, cudaMemcpyDeviceToHost, st);
+    AMG_CUDA(cudaMemcpyAsync(S.host, S.cnt, sizeof(int) * 2 * batch, cudaMemcpyDeviceToHost, st));
     AMG_CUDA(cudaStreamSynchronize(st));
-    int pairs = S.host[0];
-    nf = S.host[1];
-    std::swap(fa, fb);
-    if (pairs == 0) break;
+    for (int b = 0; b < batch; ++b) {
+      ++r;
+      if (S.host[2 * b] == 0) { finished = true; break; }
+      nf = S.host[2 * b + 1];
+    }
+    fa = ba;
+    fb = bb;
+    batch = std::min(batch * 2, 16);
   }
   *rounds = r;
   k_hem_finish<<<cdiv(n, T), T, 0, st>>>(n, S.mate); count_launch();
   // numbering
   k_agg_flags<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.flag); count_launch();
-  scan_excl(S.flag, S.id, n, S.cnt + 2, S.tiles, st);
+  scan_excl(S.flag, S.id, n, S.cnt + 34, S.tiles, st);
   k_agg_assign<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.id, pass_agg, S.first); count_launch();
-  cudaMemcpyAsync(S.host + 2, S.cnt + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(S.host + 34, S.cnt + 34, sizeof(int), cudaMemcpyDeviceToHost, st);
   AMG_CUDA(cudaStreamSynchronize(st));
-  const int nc = S.host[2];
+  const int nc = S.host[34];
   // Galerkin: count, scan, fill
   out.n = nc;
-  AMG_TRY(dev_alloc((void **)&out.rp, sizeof(int32_t) * (nc + 1 + AMG_PAD)));
+  AMG_TRY(pool_alloc((void **)&out.rp, sizeof(int32_t) * (nc + 1 + AMG_PAD), st));
   const int gwarps_blocks = grid_for((long long)nc * 32, T, 152 * 16);
   k_galerkin<false><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, S.count,
                                                   nullptr, nullptr, nullptr); count_launch();
-  scan_excl(S.count, out.rp, nc, S.cnt + 3, S.tiles, st);
-  cudaMemcpyAsync(out.rp + nc, S.cnt + 3, sizeof(int), cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(S.host + 3, S.cnt + 3, sizeof(int), cudaMemcpyDeviceToHost, st);
+  scan_excl(S.count, out.rp, nc, S.cnt + 35, S.tiles, st);
+  cudaMemcpyAsync(out.rp + nc, S.cnt + 35, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(S.host + 35, S.cnt + 35, sizeof(int), cudaMemcpyDeviceToHost, st);
   AMG_CUDA(cudaStreamSynchronize(st));
-  out.nnz = S.host[3];
-  AMG_TRY(dev_alloc((void **)&out.ci, sizeof(int32_t) * (out.nnz + AMG_PAD)));
-  AMG_TRY(dev_alloc((void **)&out.val, sizeof(double) * (out.nnz + AMG_PAD)));
+  out.nnz = S.host[35];
+  AMG_TRY(pool_alloc((void **)&out.ci, sizeof(int32_t) * (out.nnz + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&out.val, sizeof(double) * (out.nnz + AMG_PAD), st));
   cudaMemsetAsync(out.ci + out.nnz, 0, sizeof(int32_t) * AMG_PAD, st);
   cudaMemsetAsync(out.val + out.nnz, 0, sizeof(double) * AMG_PAD, st);
   k_galerkin<true><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, nullptr,
@@ -643,8 +659,8 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
   AMG_TRY(check_flags(h, st));
 
   Scratch S;
-  amg_status rs = scratch_alloc(S, n, nnz);
-  if (rs != AMG_OK) { scratch_free(S); return rs; }
+  amg_status rs = scratch_alloc(S, n, nnz, st);
+  if (rs != AMG_OK) { scratch_free(S, st); return rs; }
   int k = 0;
   const amg_params &p = h->prm;
   while (k + 1 < p.max_levels && h->lev[k].n > p.coarse_max) {
@@ -652,30 +668,29 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
     Csr cur{f.n, f.nnz, f.rp, f.ci, f.val};
     bool owned = false;
     int32_t *agg = nullptr, *pass_agg = nullptr;
-    rs = dev_alloc((void **)&agg, sizeof(int32_t) * (f.n + AMG_PAD));
-    if (rs == AMG_OK) rs = dev_alloc((void **)&pass_agg, sizeof(int32_t) * (f.n + AMG_PAD));
-    if (rs != AMG_OK) { cudaFree(agg); scratch_free(S); return rs; }
+    rs = pool_alloc((void **)&agg, sizeof(int32_t) * (f.n + AMG_PAD), st);
+    if (rs == AMG_OK) rs = pool_alloc((void **)&pass_agg, sizeof(int32_t) * (f.n + AMG_PAD), st);
+    if (rs != AMG_OK) { pool_free(agg, st); scratch_free(S, st); return rs; }
     k_iota<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg); count_launch();
     int rounds[AMG_MAX_PASSES] = {0};
     for (int pass = 0; pass < p.passes; ++pass) {
       Csr nxt;
       rs = coarsen_pass(h, S, cur, pass_agg, nxt, &rounds[pass], st);
       if (rs != AMG_OK) {
-        free_csr(nxt);
-        if (owned) free_csr(cur);
-        cudaFree(agg); cudaFree(pass_agg); scratch_free(S);
+        free_csr(nxt, st);
+        if (owned) free_csr(cur, st);
+        pool_free(agg, st); pool_free(pass_agg, st); scratch_free(S, st);
         return rs;
       }
       k_compose<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, pass_agg); count_launch();
-      if (owned) { AMG_CUDA(cudaStreamSynchronize(st)); free_csr(cur); }
+      if (owned) free_csr(cur, st);  // stream-ordered: after the kernels that read it
       cur = nxt;
       owned = true;
     }
-    cudaFree(pass_agg);
+    pool_free(pass_agg, st);
     if ((double)cur.n / (double)f.n > p.stall_ratio) {
-      AMG_CUDA(cudaStreamSynchronize(st));
-      free_csr(cur);
-      cudaFree(agg);
+      free_csr(cur, st);
+      pool_free(agg, st);
       break;
     }
     // adopt the coarse level; record allocations for amg_destroy
@@ -692,15 +707,15 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
     AMG_TRY(hier_alloc(h, (void **)&f.mem, sizeof(int32_t) * (f.n + AMG_PAD)));
     cudaMemsetAsync(S.count, 0, sizeof(int) * c.n, st);
     k_count_members<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, S.count); count_launch();
-    scan_excl(S.count, f.mrp, c.n, S.cnt + 4, S.tiles, st);
-    cudaMemcpyAsync(f.mrp + c.n, S.cnt + 4, sizeof(int), cudaMemcpyDeviceToDevice, st);
+    scan_excl(S.count, f.mrp, c.n, S.cnt + 36, S.tiles, st);
+    cudaMemcpyAsync(f.mrp + c.n, S.cnt + 36, sizeof(int), cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(S.count, 0, sizeof(int) * c.n, st);
     k_fill_members<<<cdiv(f.n, T), T, 0, st>>>(f.n, agg, f.mrp, S.count, f.mem); count_launch();
     k_sort_members<<<cdiv(c.n, T), T, 0, st>>>(c.n, f.mrp, f.mem); count_launch();
     AMG_CUDA(cudaGetLastError());
     ++k;
   }
-  scratch_free(S);
+  scratch_free(S, st);
   h->L = k;
   // diagonals of every level
   for (int j = 0; j <= h->L; ++j) {
@@ -720,8 +735,8 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
   const int m = c.n;
   double *M = nullptr, *prow = nullptr, *pinv = nullptr, *fac = nullptr;
   AMG_TRY(hier_alloc(h, (void **)&h->ainv, sizeof(double) * ((size_t)m * m + AMG_PAD)));
-  if (dev_alloc((void **)&M, sizeof(double) * (size_t)m * m) != AMG_OK) return AMG_ERR_OOM;
-  if (dev_alloc((void **)&prow, sizeof(double) * 3 * (m + AMG_PAD)) != AMG_OK) { cudaFree(M); return AMG_ERR_OOM; }
+  if (pool_alloc((void **)&M, sizeof(double) * (size_t)m * m, st) != AMG_OK) return AMG_ERR_OOM;
+  if (pool_alloc((void **)&prow, sizeof(double) * 3 * (m + AMG_PAD), st) != AMG_OK) { pool_free(M, st); return AMG_ERR_OOM; }
   pinv = prow + (m + AMG_PAD);
   fac = pinv + (m + AMG_PAD);
   const int T = AMG_THREADS;
@@ -732,9 +747,9 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
     k_gj_pivot<<<1, 1024, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac, h->eflags); count_launch();
     k_gj_eliminate<<<grid_for(mm, T), T, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac); count_launch();
   }
+  pool_free(M, st);
+  pool_free(prow, st);
   cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(M);
-  cudaFree(prow);
   if (e != cudaSuccess) return amg_cuda_status(e);
   return AMG_OK;
 }
@@ -753,6 +768,7 @@ extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, co
   cudaStream_t st = (cudaStream_t)stream;
   amg_hierarchy *h = new amg_hierarchy();
   h->prm = p;
+  h->stream = st;
   amg_status s = AMG_OK;
   do {
     if (cudaGetDevice(&h->device) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
@@ -760,7 +776,8 @@ extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, co
     if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
     s = hier_alloc(h, (void **)&h->eflags, sizeof(unsigned) * 4);
     if (s) break;
-    if (cudaMallocHost((void **)&h->eflags_host, sizeof(unsigned) * 4) != cudaSuccess) { s = AMG_ERR_OOM; break; }
+    h->eflags_host = (unsigned *)pinned_small_alloc();
+    if (!h->eflags_host) { s = AMG_ERR_OOM; break; }
     cudaMemsetAsync(h->eflags, 0, sizeof(unsigned) * 4, st);
     s = setup_impl(h, n, nnz, d_row_ptr, d_col, d_val, st);
     if (s) break;

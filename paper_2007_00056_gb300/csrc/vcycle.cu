@@ -23,9 +23,10 @@
 // ---------------------------------------------------------------------------
 // Row-kernel helpers
 // ---------------------------------------------------------------------------
-template <typename T> struct Vec;
-template <> struct Vec<double> { static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); } };
-template <> struct Vec<float> { static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); } };
+// Inverse diagonal entry; a null array means a unit diagonal (the scaled
+// D^-1/2 A D^-1/2 levels of the FP16-storage mode).
+template <typename T>
+__device__ __forceinline__ T dval(const T *__restrict__ d, int i) { return d ? __ldg(&d[i]) : T(1); }
 
 __device__ __forceinline__ double as_arith(double v, double) { return v; }
 __device__ __forceinline__ float as_arith(float v, float) { return v; }
@@ -64,7 +65,7 @@ __global__ void k_jacobi0(int n, const T *__restrict__ f, const T *__restrict__ 
                           const KState *st) {
   if (is_done(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = omega * (dinv[i] * f[i]);
+    x[i] = omega * (dval(dinv, i) * f[i]);
 }
 
 // t = f - A x
@@ -91,10 +92,10 @@ __global__ void k_residual0(int n, const int32_t *__restrict__ rp, const int32_t
   ROW_LOOP_BEGIN(TPR, n)
   int b = 0, e = 0;
   if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
-  T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub, [&](int j) { return omega * (__ldg(&dinv[j]) * __ldg(&f[j])); });
+  T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub, [&](int j) { return omega * (dval(dinv, j) * __ldg(&f[j])); });
   if (valid && _sub == 0) {
     const T fi = f[row];
-    x[row] = omega * (dinv[row] * fi);
+    x[row] = omega * (dval(dinv, row) * fi);
     t[row] = fi - ax;
   }
   ROW_LOOP_END
@@ -110,50 +111,79 @@ __global__ void k_jacobi(int n, const int32_t *__restrict__ rp, const int32_t *_
   int b = 0, e = 0;
   if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
   T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub, [&](int j) { return __ldg(&x[j]); });
-  if (valid && _sub == 0) xout[row] = x[row] + omega * (dinv[row] * (f[row] - ax));
+  if (valid && _sub == 0) xout[row] = x[row] + omega * (dval(dinv, row) * (f[row] - ax));
   ROW_LOOP_END
 }
 
+// Coarse correction of fine row i: x_c[agg_i], times isig_c[agg_i] when the
+// coarse level is scaled and times sig_i when the fine level is scaled.
+template <typename T>
+__device__ __forceinline__ T coarse_corr(const T *__restrict__ xc, const int32_t *__restrict__ agg,
+                                         const float *__restrict__ sig, const float *__restrict__ isig_c, int i) {
+  const int a = __ldg(&agg[i]);
+  T c = __ldg(&xc[a]);
+  if (isig_c) c *= (T)__ldg(&isig_c[a]);
+  if (sig) c *= (T)__ldg(&sig[i]);
+  return c;
+}
+
 // Prolongation fused into the first post-smoothing sweep:
-// xp = x + xc[agg]; xout = xp + omega D^-1 (f - A xp)
+// xp = x + P xc; xout = xp + omega D^-1 (f - A xp)
 template <int TPR, typename T, typename V>
 __global__ void k_prolong_jacobi(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const V *__restrict__ val, const T *__restrict__ dinv, T omega,
                                  const T *__restrict__ x, const int32_t *__restrict__ agg,
-                                 const T *__restrict__ xc, const T *__restrict__ f, T *__restrict__ xout,
+                                 const T *__restrict__ xc, const float *__restrict__ sig,
+                                 const float *__restrict__ isig_c, const T *__restrict__ f, T *__restrict__ xout,
                                  const KState *st) {
   if (is_done(st)) return;
   ROW_LOOP_BEGIN(TPR, n)
   int b = 0, e = 0;
   if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
   T ax = row_sum<TPR, T, V>(ci, val, b, e, _sub,
-                            [&](int j) { return __ldg(&x[j]) + __ldg(&xc[__ldg(&agg[j])]); });
+                            [&](int j) { return __ldg(&x[j]) + coarse_corr(xc, agg, sig, isig_c, j); });
   if (valid && _sub == 0) {
-    T xp = x[row] + xc[agg[row]];
-    xout[row] = xp + omega * (dinv[row] * (f[row] - ax));
+    T xp = x[row] + coarse_corr(xc, agg, sig, isig_c, row);
+    xout[row] = xp + omega * (dval(dinv, row) * (f[row] - ax));
   }
   ROW_LOOP_END
 }
 
 template <typename T>
 __global__ void k_prolong(int n, const T *__restrict__ x, const int32_t *__restrict__ agg, const T *__restrict__ xc,
-                          T *__restrict__ xout, const KState *st) {
+                          const float *__restrict__ sig, const float *__restrict__ isig_c, T *__restrict__ xout,
+                          const KState *st) {
   if (is_done(st)) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    xout[i] = x[i] + xc[agg[i]];
+    xout[i] = x[i] + coarse_corr(xc, agg, sig, isig_c, i);
 }
 
-// f_c[I] = sum of t over the members of I, members ascending.
+// f_c[I] = sum of t over the members of I, members ascending (each term times
+// sig_i on a scaled fine level; the sum times isig_c[I] on a scaled coarse level).
 template <typename T>
 __global__ void k_restrict(int nc, const int32_t *__restrict__ mrp, const int32_t *__restrict__ mem,
-                           const T *__restrict__ t, T *__restrict__ fc, const KState *st) {
+                           const T *__restrict__ t, const float *__restrict__ sig, const float *__restrict__ isig_c,
+                           T *__restrict__ fc, const KState *st) {
   if (is_done(st)) return;
   for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     int b = mrp[I], e = mrp[I + 1];
-    T s = t[mem[b]];
-    for (int k = b + 1; k < e; ++k) s += t[mem[k]];
-    fc[I] = s;
+    int i = mem[b];
+    T s = sig ? t[i] * (T)sig[i] : t[i];
+    for (int k = b + 1; k < e; ++k) {
+      i = mem[k];
+      s += sig ? t[i] * (T)sig[i] : t[i];
+    }
+    fc[I] = isig_c ? s * (T)isig_c[I] : s;
   }
+}
+
+// b = (B)(a * scale) with an optional per-entry scale
+template <typename A, typename B>
+__global__ void k_cast_scale(int n, const A *__restrict__ a, const float *__restrict__ scale, B *__restrict__ b,
+                             const KState *st) {
+  if (is_done(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    b[i] = scale ? (B)(a[i] * (A)scale[i]) : (B)a[i];
 }
 
 template <typename A, typename B>
@@ -193,6 +223,7 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
 // ---------------------------------------------------------------------------
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
+#define CG_CHUNK 4  // neighbours whose gathers are in flight together
 #define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -297,9 +328,19 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     const double ui = __dmul_rn(fi, di);
     double wi = 0.0;
     const int b = row_begin(i), e = row_begin(i + 1);
-    for (int k = b; k < e; ++k) {
-      const int j = lci[k];
-      wi += lval[k] * __dmul_rn((double)f[j], __ldg(&dinv[j]));
+    for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
+      double fj[CG_CHUNK], dj[CG_CHUNK], vv[CG_CHUNK];
+#pragma unroll
+      for (int u = 0; u < CG_CHUNK; ++u) {
+        const bool in = k0 + u < e;
+        const int j = in ? lci[k0 + u] : i;
+        vv[u] = in ? lval[k0 + u] : 0.0;
+        fj[u] = (double)f[j];
+        dj[u] = __ldg(&dinv[j]);
+      }
+#pragma unroll
+      for (int u = 0; u < CG_CHUNK; ++u)
+        if (k0 + u < e) wi += vv[u] * __dmul_rn(fj[u], dj[u]);
     }
     cg.r[0][i] = fi;
     cg.w[0][i] = wi;
@@ -340,11 +381,29 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
         const double unew = __dmul_rn(rnew, di);
         x[i] = __fma_rn(alpha, pi, __ldcg(&x[i]));
         p[i] = pi;
+        // gathers of a chunk of neighbours are issued together (the SpMV is
+        // bound by L2 latency, not bandwidth); the sum keeps the stored order
         double wi = 0.0;
         const int b = row_begin(i), e = row_begin(i + 1);
-        for (int k = b; k < e; ++k) {
-          const int j = lci[k];
-          wi += lval[k] * cg_unext(__ldcg(&ro[j]), __ldcg(&wo[j]), __ldcg(&so[j]), __ldg(&dinv[j]), alpha, beta);
+        for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
+          int jj[CG_CHUNK];
+          double vv[CG_CHUNK], rj[CG_CHUNK], wj[CG_CHUNK], sj[CG_CHUNK], dj[CG_CHUNK];
+#pragma unroll
+          for (int u = 0; u < CG_CHUNK; ++u) {
+            const bool in = k0 + u < e;
+            jj[u] = in ? lci[k0 + u] : i;
+            vv[u] = in ? lval[k0 + u] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < CG_CHUNK; ++u) {
+            rj[u] = __ldcg(&ro[jj[u]]);
+            wj[u] = __ldcg(&wo[jj[u]]);
+            sj[u] = __ldcg(&so[jj[u]]);
+            dj[u] = __ldg(&dinv[jj[u]]);
+          }
+#pragma unroll
+          for (int u = 0; u < CG_CHUNK; ++u)
+            if (k0 + u < e) wi += vv[u] * cg_unext(rj[u], wj[u], sj[u], dj[u], alpha, beta);
         }
         rn[i] = rnew;
         sn[i] = snew;
@@ -385,22 +444,39 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename T> struct LevelVec;
-template <> struct LevelVec<double> {
+// Per-precision views of a level: vectors of type T, matrix values of type V,
+// inverse diagonal (null for the unit-diagonal scaled FP16 levels) and the
+// scale factors of the FP16 mode.
+template <typename T, typename V> struct Sel;
+template <> struct Sel<double, double> {
   static double *f(Level &l) { return l.f; }
   static double *x(Level &l) { return l.x; }
   static double *t(Level &l) { return l.t; }
   static double *y(Level &l) { return l.y; }
   static const double *val(const Level &l) { return l.val; }
   static const double *dinv(const Level &l) { return l.dinv; }
+  static const float *sig(const Level &) { return nullptr; }
+  static const float *isig(const Level &) { return nullptr; }
 };
-template <> struct LevelVec<float> {
+template <> struct Sel<float, float> {
   static float *f(Level &l) { return l.f32; }
   static float *x(Level &l) { return l.x32; }
   static float *t(Level &l) { return l.t32; }
   static float *y(Level &l) { return l.y32; }
   static const float *val(const Level &l) { return l.val32; }
   static const float *dinv(const Level &l) { return l.dinv32; }
+  static const float *sig(const Level &) { return nullptr; }
+  static const float *isig(const Level &) { return nullptr; }
+};
+template <> struct Sel<float, __half> {
+  static float *f(Level &l) { return l.f32; }
+  static float *x(Level &l) { return l.x32; }
+  static float *t(Level &l) { return l.t32; }
+  static float *y(Level &l) { return l.y32; }
+  static const __half *val(const Level &l) { return l.val16; }
+  static const float *dinv(const Level &) { return nullptr; }
+  static const float *sig(const Level &l) { return l.sig; }
+  static const float *isig(const Level &l) { return l.isig; }
 };
 
 inline int row_blocks(const Level &l) {
@@ -415,12 +491,12 @@ inline double bytes_A(const Level &l, int vbytes) { return (double)l.nnz * (vbyt
   do {                                                                                    \
     int _g = row_blocks(l);                                                               \
     switch ((l).tpr) {                                                                    \
-      case 1: KERNEL<1, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      case 2: KERNEL<2, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      case 4: KERNEL<4, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      case 8: KERNEL<8, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      case 16: KERNEL<16, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;           \
-      default: KERNEL<32, T, T><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;           \
+      case 1: KERNEL<1, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 2: KERNEL<2, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 4: KERNEL<4, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 8: KERNEL<8, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 16: KERNEL<16, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;           \
+      default: KERNEL<32, T, V><<<_g, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;           \
     }                                                                                     \
   } while (0)
 
@@ -450,23 +526,27 @@ void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KSta
                      (const double *)c.dinv, f, x, h->cg, st, h->eflags);
 }
 
-// Runs the V-cycle below level 0 given f0 (level-0 rhs) and writes out0.
-template <typename T>
+// Runs the V-cycle given f0 (level-0 right-hand side, in the level's own
+// scaling) and writes out0.  Levels below L are scaled in the FP16 mode; the
+// coarsest level L is never scaled.
+template <typename T, typename V>
 void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const KState *st) {
+  using S = Sel<T, V>;
   const int L = h->L;
   const T omega = (T)h->prm.omega;
   const int nu_pre = h->prm.nu_pre, nu_post = h->prm.nu_post;
-  const double sz = sizeof(T);
+  const double sz = sizeof(T), szv = sizeof(V);
   const T *fk[AMG_MAX_LEVELS];
   T *cur[AMG_MAX_LEVELS];
-  for (int k = 0; k <= L; ++k) fk[k] = (k == 0) ? f0 : LevelVec<T>::f(h->lev[k]);
+  for (int k = 0; k <= L; ++k) fk[k] = (k == 0) ? f0 : S::f(h->lev[k]);
   // down sweep
   for (int k = 0; k < L; ++k) {
     Level &l = h->lev[k];
-    T *a = LevelVec<T>::x(l), *b = LevelVec<T>::t(l);
-    const T *dinv = LevelVec<T>::dinv(l);
-    const T *val = LevelVec<T>::val(l);
-    const double BA = bytes_A(l, (int)sz);
+    Level &c = h->lev[k + 1];
+    T *a = S::x(l), *b = S::t(l);
+    const T *dinv = S::dinv(l);
+    const V *val = S::val(l);
+    const double BA = bytes_A(l, (int)szv);
     if (nu_pre == 1 && l.fuse_pre) {
       LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
       DISPATCH_TPR(l, k_residual0, l.n, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
@@ -487,42 +567,45 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
         DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, a, fk[k], b, st);
       }
     }
-    Level &c = h->lev[k + 1];
     {
+      const float *isig_c = (k + 1 < L) ? S::isig(c) : nullptr;
       LaunchScope ls(h, s, PK_RESTRICT, k, (sz + 4.0) * l.n + (sz + 4.0) * c.n + 4.0);
-      k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, LevelVec<T>::f(c), st);
+      k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, S::sig(l), isig_c,
+                                                                        S::f(c), st);
     }
   }
   // coarsest
-  T *xc = (L == 0) ? out0 : LevelVec<T>::y(h->lev[L]);
+  T *xc = (L == 0) ? out0 : S::y(h->lev[L]);
   coarse_solve<T>(h, fk[L], xc, s, st);
   // up sweep
   for (int k = L - 1; k >= 0; --k) {
     Level &l = h->lev[k];
     const int nc = h->lev[k + 1].n;
-    T *final_out = (k == 0) ? out0 : LevelVec<T>::y(l);
+    const float *sig = S::sig(l);
+    const float *isig_c = (k + 1 < L) ? S::isig(h->lev[k + 1]) : nullptr;
+    T *final_out = (k == 0) ? out0 : S::y(l);
     T *in = cur[k];
-    T *other = (in == LevelVec<T>::x(l)) ? LevelVec<T>::t(l) : LevelVec<T>::x(l);
-    const T *dinv = LevelVec<T>::dinv(l);
-    const T *val = LevelVec<T>::val(l);
-    const double BA = bytes_A(l, (int)sz);
+    T *other = (in == S::x(l)) ? S::t(l) : S::x(l);
+    const T *dinv = S::dinv(l);
+    const V *val = S::val(l);
+    const double BA = bytes_A(l, (int)szv);
     if (nu_post == 0) {
       LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
-      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, final_out, st);
+      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, final_out, st);
     } else {
-      // cur: current iterate; spare: a free buffer distinct from final_out
+      // curb: current iterate; spare: a free buffer distinct from final_out
       T *curb, *spare;
       int sweeps = nu_post;
       if (l.fuse_post) {
         T *o = (nu_post == 1) ? final_out : other;
         LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
-        DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, fk[k], o, st);
+        DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
         curb = o;
         spare = in;
         sweeps -= 1;
       } else {
         LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
-        k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, other, st);
+        k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, other, st);
         curb = other;
         spare = in;
       }
@@ -542,18 +625,22 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
 
 amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st) {
   if (h->prm.precision == AMG_FP64) {
-    vcycle_levels<double>(h, r, z, s, st);
+    vcycle_levels<double, double>(h, r, z, s, st);
   } else {
     Level &l0 = h->lev[0];
+    const bool half = h->prm.precision == AMG_FP16_STORAGE;
+    // level 0 is scaled in the FP16 mode unless it is also the coarsest level
+    const float *isig0 = (half && h->L > 0) ? l0.isig : nullptr;
     int g = grid_for(l0.n, AMG_THREADS);
     {
       LaunchScope ls(h, s, PK_CAST, 0, 12.0 * l0.n);
-      k_cast<double, float><<<g, AMG_THREADS, 0, s>>>(l0.n, r, l0.f32, st);
+      k_cast_scale<double, float><<<g, AMG_THREADS, 0, s>>>(l0.n, r, isig0, l0.f32, st);
     }
-    vcycle_levels<float>(h, l0.f32, l0.y32, s, st);
+    if (half) vcycle_levels<float, __half>(h, l0.f32, l0.y32, s, st);
+    else vcycle_levels<float, float>(h, l0.f32, l0.y32, s, st);
     {
       LaunchScope ls(h, s, PK_CAST, 0, 12.0 * l0.n);
-      k_cast<float, double><<<g, AMG_THREADS, 0, s>>>(l0.n, l0.y32, z, st);
+      k_cast_scale<float, double><<<g, AMG_THREADS, 0, s>>>(l0.n, l0.y32, isig0, z, st);
     }
   }
   return amg_cuda_status(cudaGetLastError());
@@ -589,6 +676,24 @@ amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
   return AMG_OK;
 }
 
+// FP16 storage of D^-1/2 A D^-1/2: sig_i = sqrt(a_ii), isig_i = 1/sig_i,
+// val16 = a_ij isig_i isig_j rounded to FP16 (computed in FP64).
+__global__ void k_scale_half(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                             const double *__restrict__ val, const double *__restrict__ dinv, __half *__restrict__ val16,
+                             float *__restrict__ sig, float *__restrict__ isig, unsigned *eflags) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double di = dinv[i];
+  if (!(di > 0.0)) { atomicOr(eflags, AMG_EFLAG_NONSYM); return; }
+  const double is = sqrt(di);
+  sig[i] = (float)(1.0 / is);
+  isig[i] = (float)is;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double v = val[e] * is * sqrt(dinv[ci[e]]);
+    val16[e] = __double2half(v);
+  }
+}
+
 __global__ void k_to_f32(long long n, const double *__restrict__ a, float *__restrict__ b) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];
@@ -607,7 +712,7 @@ static int choose_tpr(const Level &l) {
 
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
   const bool mixed = h->prm.precision != AMG_FP64;
-  if (h->prm.precision == AMG_FP16_STORAGE) return AMG_ERR_UNSUPPORTED;
+  const bool half = h->prm.precision == AMG_FP16_STORAGE;
   for (int k = 0; k <= h->L; ++k) {
     Level &l = h->lev[k];
     l.tpr = choose_tpr(l);
@@ -624,12 +729,27 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
       AMG_TRY(hier_alloc(h, (void **)&l.x32, vf));
       AMG_TRY(hier_alloc(h, (void **)&l.t32, vf));
       AMG_TRY(hier_alloc(h, (void **)&l.y32, vf));
-      AMG_TRY(hier_alloc(h, (void **)&l.val32, sizeof(float) * (l.nnz + AMG_PAD)));
-      AMG_TRY(hier_alloc(h, (void **)&l.dinv32, vf));
-      k_to_f32<<<grid_for(l.nnz, AMG_THREADS), AMG_THREADS, 0, s>>>(l.nnz, l.val, l.val32);
-      k_to_f32<<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, l.dinv, l.dinv32);
-      count_launch(2);
+      if (half && k < h->L) {
+        // levels below the coarsest store D^-1/2 A D^-1/2 in FP16
+        AMG_TRY(hier_alloc(h, (void **)&l.val16, sizeof(__half) * (l.nnz + AMG_PAD)));
+        AMG_TRY(hier_alloc(h, (void **)&l.sig, vf));
+        AMG_TRY(hier_alloc(h, (void **)&l.isig, vf));
+        k_scale_half<<<cdiv(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, l.rp, l.ci, l.val, l.dinv, l.val16, l.sig,
+                                                                     l.isig, h->eflags);
+        count_launch();
+      } else {
+        AMG_TRY(hier_alloc(h, (void **)&l.val32, sizeof(float) * (l.nnz + AMG_PAD)));
+        AMG_TRY(hier_alloc(h, (void **)&l.dinv32, vf));
+        k_to_f32<<<grid_for(l.nnz, AMG_THREADS), AMG_THREADS, 0, s>>>(l.nnz, l.val, l.val32);
+        k_to_f32<<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, l.dinv, l.dinv32);
+        count_launch(2);
+      }
     }
+  }
+  if (half) {
+    unsigned f = 0;
+    AMG_TRY(read_eflags(h, s, &f));
+    if (f & AMG_EFLAG_NONSYM) return AMG_ERR_UNSUPPORTED;  // FP16 storage needs a positive diagonal
   }
   apply_tuned(h);
   // Krylov work vectors at level 0 (FP64 in every precision)
@@ -641,7 +761,9 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
   AMG_TRY(hier_alloc(h, (void **)&h->counter, sizeof(unsigned) * 16));
   AMG_TRY(hier_alloc(h, (void **)&h->st, sizeof(KState)));
   AMG_CUDA(cudaMemsetAsync(h->counter, 0, sizeof(unsigned) * 16, s));
-  if (cudaMallocHost((void **)&h->st_host, sizeof(KState)) != cudaSuccess) { cudaGetLastError(); return AMG_ERR_OOM; }
+  static_assert(sizeof(KState) <= 256, "KState must fit a small pinned buffer");
+  h->st_host = (KState *)pinned_small_alloc();
+  if (!h->st_host) return AMG_ERR_OOM;
   return amg_cuda_status(cudaGetLastError());
 }
 
@@ -673,8 +795,9 @@ float time_launch(cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps, const 
   return best;
 }
 
-template <typename T>
+template <typename T, typename V>
 amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
+  using S = Sel<T, V>;
   cudaEvent_t ea, eb;
   AMG_CUDA(cudaEventCreate(&ea));
   AMG_CUDA(cudaEventCreate(&eb));
@@ -682,10 +805,12 @@ amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
   const int reps = 3;
   for (int k = 0; k < h->L; ++k) {
     Level &l = h->lev[k];
-    const T *val = LevelVec<T>::val(l);
-    const T *dinv = LevelVec<T>::dinv(l);
-    T *f = LevelVec<T>::f(l), *x = LevelVec<T>::x(l), *t = LevelVec<T>::t(l), *y = LevelVec<T>::y(l);
-    const T *xc = LevelVec<T>::y(h->lev[k + 1]);
+    const V *val = S::val(l);
+    const T *dinv = S::dinv(l);
+    T *f = S::f(l), *x = S::x(l), *t = S::t(l), *y = S::y(l);
+    const T *xc = S::y(h->lev[k + 1]);
+    const float *sig = S::sig(l);
+    const float *isig_c = (k + 1 < h->L) ? S::isig(h->lev[k + 1]) : nullptr;
     const double avg = l.n ? (double)l.nnz / l.n : 0.0;
     cudaMemsetAsync(f, 0, sizeof(T) * l.n, s);
     cudaMemsetAsync(x, 0, sizeof(T) * l.n, s);
@@ -715,11 +840,11 @@ amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
     l.fuse_pre = pre_fused <= pre_split ? 1 : 0;
     // prolongation: fused into the first postsmoothing sweep, or separate
     float post_fused = time_launch<T>(s, ea, eb, reps, [&]() {
-      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, f, y,
+      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, sig, isig_c, f, y,
                    (const KState *)nullptr);
     });
     float post_split = time_launch<T>(s, ea, eb, reps, [&]() {
-      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, x, l.agg, xc, t, nullptr);
+      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, x, l.agg, xc, sig, isig_c, t, nullptr);
       DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, t, f, y, (const KState *)nullptr);
     });
     l.fuse_post = post_fused <= post_split ? 1 : 0;
@@ -752,7 +877,9 @@ extern "C" amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream) {
   if (!h) return AMG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   AMG_CUDA(cudaStreamSynchronize(s));
-  amg_status st = h->prm.precision == AMG_FP64 ? tune_levels<double>(h, s) : tune_levels<float>(h, s);
+  amg_status st = h->prm.precision == AMG_FP64   ? tune_levels<double, double>(h, s)
+                  : h->prm.precision == AMG_FP32 ? tune_levels<float, float>(h, s)
+                                                 : tune_levels<float, __half>(h, s);
   reset_graphs(h);
   AMG_CUDA(cudaStreamSynchronize(s));
   return st;

@@ -20,6 +20,10 @@ from paper_2007_00056_gb300 import workloads as W  # noqa: E402
 from tests.gpu_util import rel_err, setup_both, to_cuda  # noqa: E402
 
 VCYCLE_TOL_FP32 = 1e-5
+# FP16 storage rounds every stored value of D^-1/2 A D^-1/2 to 11 significant
+# bits (relative 4.9e-4); the V-cycle then approximates the FP64 one to
+# roughly that size times the coarse-correction gain, bounded here by 2e-2.
+VCYCLE_TOL_FP16 = 2e-2
 
 CASES = [
     ("poisson2d_64", lambda: W.poisson2d(64), dict(coarse_max=64)),
@@ -75,3 +79,34 @@ def test_fp32_bicgstab_convdiff():
     assert info.status == amg.AMG_OK and info.rel_res_true <= 1.05e-8
     assert info.iterations <= info_o.iterations + 2
     assert rel_err(x.cpu().numpy(), x_o) < 1e-6
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_fp16_storage_vcycle_and_flexible_pcg(case):
+    _, make, kw = case
+    s = make()
+    h, oh, b = setup_both(s, precision=amg.AMG_FP16_STORAGE, **kw)
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < VCYCLE_TOL_FP16
+    x = torch.zeros_like(b)
+    info = amg.pcg_solve(h, b, x, rtol=1e-8, flexible=True)
+    x_o, info_o = oh.pcg(s.b, rtol=1e-8, flexible=True)
+    assert info.status == amg.AMG_OK and info.rel_res_true <= 1.05e-8
+    assert info.iterations <= int(1.5 * info_o.iterations) + 2
+    assert rel_err(x.cpu().numpy(), x_o) < 1e-6
+
+
+def test_fp16_storage_kernel_variants():
+    s = W.lognormal3d(18, seed=2)
+    h, oh, b = setup_both(s, precision=amg.AMG_FP16_STORAGE, coarse_max=200)
+    z_o = oh.vcycle(s.b)
+    for tpr in (1, 4):
+        for fp in (0, 1):
+            for fq in (0, 1):
+                for k in range(h.num_levels):
+                    amg.amg_level_set_config(h, k, tpr, fp, fq)
+                z = torch.empty_like(b)
+                amg.amg_vcycle(h, b, z)
+                assert rel_err(z.cpu().numpy(), z_o) < VCYCLE_TOL_FP16
+    amg.amg_autotune(h)
