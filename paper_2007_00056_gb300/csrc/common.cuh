@@ -57,6 +57,7 @@ struct Level {
   int32_t *agg = nullptr;    // n, into level k+1
   int32_t *mrp = nullptr;    // n_{k+1}+1
   int32_t *mem = nullptr;    // n
+  int32_t *perm = nullptr;   // row processing order grouped by length class (levels >= 1)
   double *f = nullptr, *x = nullptr, *t = nullptr, *y = nullptr;
   float *f32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
   int rounds[AMG_MAX_PASSES] = {0};

@@ -284,25 +284,34 @@ __global__ void __launch_bounds__(AMG_THREADS)
     int distinct = 0;
     const int out0 = FILL ? rpc[I] : 0;
     if (m <= 32) {
-      // each lane holds one contribution; compare through shuffles
-      int J = lane < m ? agg[ci[r.pos(lane)]] : 0x7fffffff;
-      double v = lane < m ? val[r.pos(lane)] : 0.0;
-      bool firstJ = lane < m;
-      int rank = 0;
+      // each lane holds one contribution (lanes >= m get distinct negative
+      // keys); lanes with the same coarse column form a match group, the
+      // group's lowest lane (first in stored order) sums its values in lane
+      // order -- FP64 adds only for real duplicates
+      const int J = lane < m ? agg[ci[r.pos(lane)]] : -1 - lane;
+      const double v = lane < m ? val[r.pos(lane)] : 0.0;
+      sV[wib][lane] = v;
+      const unsigned grp = __match_any_sync(0xffffffffu, J);
+      const bool firstJ = lane < m && (grp & ((1u << lane) - 1u)) == 0u;
+      __syncwarp();
       double sum = v;
-      for (int k = 0; k < m; ++k) {
-        int Jk = __shfl_sync(0xffffffffu, J, k);
-        double vk = __shfl_sync(0xffffffffu, v, k);
-        if (k < lane && Jk == J) firstJ = false;
-        if (k > lane && Jk == J) sum = __dadd_rn(sum, vk);
+      if (firstJ) {
+        unsigned rest = grp & ~((2u << lane) - 1u);  // later lanes of the group, ascending
+        while (rest) {
+          const int q = __ffs(rest) - 1;
+          sum = __dadd_rn(sum, sV[wib][q]);
+          rest &= rest - 1u;
+        }
       }
-      unsigned fm = __ballot_sync(0xffffffffu, firstJ);
+      const unsigned fm = __ballot_sync(0xffffffffu, firstJ);
+      int rank = 0;
       for (int k = 0; k < m; ++k) {
-        int Jk = __shfl_sync(0xffffffffu, J, k);
+        const int Jk = __shfl_sync(0xffffffffu, J, k);
         if (((fm >> k) & 1u) && Jk < J) ++rank;
       }
       distinct = __popc(fm);
       if (FILL && firstJ) { cic[out0 + rank] = J; valc[out0 + rank] = sum; }
+      __syncwarp();
     } else if (m <= GAL_CAP) {
       // stage the contributions of this coarse row in the warp's shared slice
       int *J = sJ[wib];

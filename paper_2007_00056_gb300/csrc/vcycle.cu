@@ -53,9 +53,71 @@ __device__ __forceinline__ T row_sum(const int32_t *__restrict__ ci, const V *__
   const long long _nwarps = ((long long)gridDim.x * blockDim.x) >> 5;                   \
   for (long long _base = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * _rows_per_warp; \
        _base < (n); _base += _nwarps * _rows_per_warp) {                                \
-    const int row = (int)(_base + _lane / (TPR));                                       \
-    const bool valid = row < (n);
+    const int _slot = (int)(_base + _lane / (TPR));                                     \
+    const bool valid = _slot < (n);                                                     \
+    const int row = (valid && perm) ? __ldg(&perm[_slot]) : _slot;
 #define ROW_LOOP_END }
+
+
+// ---------------------------------------------------------------------------
+// Row ordering by length class.  A warp issues every FP64 instruction for all
+// 32 lanes, so with one thread per row a warp pays for its longest row; on
+// irregular (coarse) levels that inflates the FP64 work several times.  Rows
+// are therefore processed grouped by length class (class limits grow by 1.5x
+// or less), each class in index order: a fixed, deterministic order.
+// ---------------------------------------------------------------------------
+#define ROW_CLASSES 11
+__device__ __forceinline__ int row_class(int len) {
+  return len <= 4 ? 0 : len <= 6 ? 1 : len <= 8 ? 2 : len <= 12 ? 3 : len <= 16 ? 4 : len <= 24 ? 5
+       : len <= 32 ? 6 : len <= 48 ? 7 : len <= 64 ? 8 : len <= 96 ? 9 : 10;
+}
+
+// Exclusive block scan of 0/1 flags; *total receives the block total.
+__device__ __forceinline__ int block_scan01(int flag, int *sh, int *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  const int in_warp = __popc(m & ((1u << lane) - 1u));
+  if (lane == 0) sh[wid] = __popc(m);
+  __syncthreads();
+  int off = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int c = sh[w];
+    if (w < wid) off += c;
+    tot += c;
+  }
+  __syncthreads();
+  *total = tot;
+  return off + in_warp;
+}
+
+// ord[0..nr) = local indices 0..nr-1 grouped by length class, stable.
+// len_of(k) gives the length of local row k.  All threads of the block call it.
+template <typename LenF>
+__device__ void block_class_order(int nr, int *ord, int *sh, LenF len_of) {
+  int base_pos = 0;
+  for (int c = 0; c < ROW_CLASSES; ++c) {
+    for (int b0 = 0; b0 < nr; b0 += blockDim.x) {
+      const int k = b0 + threadIdx.x;
+      const int flag = (k < nr && row_class(len_of(k)) == c) ? 1 : 0;
+      int total;
+      const int pos = block_scan01(flag, sh, &total);
+      if (flag) ord[base_pos + pos] = k;
+      base_pos += total;
+    }
+  }
+  __syncthreads();
+}
+
+// Setup: perm[w*ORDER_WINDOW + j] = rows of window w grouped by length class.
+#define ORDER_WINDOW 4096
+__global__ void k_level_order(int n, const int32_t *__restrict__ rp, int32_t *__restrict__ perm) {
+  __shared__ int sh[32];
+  const int r0 = blockIdx.x * ORDER_WINDOW;
+  const int nr = min(ORDER_WINDOW, n - r0);
+  if (nr <= 0) return;
+  block_class_order(nr, perm + r0, sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; });
+  for (int k = threadIdx.x; k < nr; k += blockDim.x) perm[r0 + k] += r0;
+}
 
 // ---------------------------------------------------------------------------
 // V-cycle kernels
@@ -70,7 +132,7 @@ __global__ void k_jacobi0(int n, const T *__restrict__ f, const T *__restrict__ 
 
 // t = f - A x
 template <int TPR, typename T, typename V>
-__global__ void k_residual(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_residual(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                            const V *__restrict__ val, const T *__restrict__ x, const T *__restrict__ f,
                            T *__restrict__ t, const KState *st) {
   if (is_done(st)) return;
@@ -85,7 +147,7 @@ __global__ void k_residual(int n, const int32_t *__restrict__ rp, const int32_t 
 // First presmoothing sweep from the zero guess fused with the residual:
 // x = omega D^-1 f (stored) and t = f - A x, neighbours' x formed on the fly.
 template <int TPR, typename T, typename V>
-__global__ void k_residual0(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_residual0(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                             const V *__restrict__ val, const T *__restrict__ dinv, T omega, const T *__restrict__ f,
                             T *__restrict__ x, T *__restrict__ t, const KState *st) {
   if (is_done(st)) return;
@@ -103,7 +165,7 @@ __global__ void k_residual0(int n, const int32_t *__restrict__ rp, const int32_t
 
 // xout = x + omega D^-1 (f - A x)
 template <int TPR, typename T, typename V>
-__global__ void k_jacobi(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_jacobi(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                          const V *__restrict__ val, const T *__restrict__ dinv, T omega, const T *__restrict__ x,
                          const T *__restrict__ f, T *__restrict__ xout, const KState *st) {
   if (is_done(st)) return;
@@ -130,7 +192,7 @@ __device__ __forceinline__ T coarse_corr(const T *__restrict__ xc, const int32_t
 // Prolongation fused into the first post-smoothing sweep:
 // xp = x + P xc; xout = xp + omega D^-1 (f - A xp)
 template <int TPR, typename T, typename V>
-__global__ void k_prolong_jacobi(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_prolong_jacobi(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                  const V *__restrict__ val, const T *__restrict__ dinv, T omega,
                                  const T *__restrict__ x, const int32_t *__restrict__ agg,
                                  const T *__restrict__ xc, const float *__restrict__ sig,
@@ -277,16 +339,28 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   const int R = (n + (int)G - 1) / (int)G;
   const int r0 = min(n, (int)blockIdx.x * R), r1 = min(n, r0 + R), nr = r1 - r0;
   const int e0 = rp[r0], e1 = rp[r1], ne = e1 - e0;
-  const bool staged = (size_t)ne * 12 + (size_t)(nr + 1) * 4 <= cg.smem;
-  double *s_val = (double *)cg_smem;
-  int *s_ci = (int *)(s_val + ne);
-  int *s_rp = s_ci + ne;
+  // dynamic shared memory: [row order: nr][row pointers: nr+1][cols: ne][values: ne]
+  const size_t ord_bytes = (size_t)nr * 4;
+  const size_t rp_off = ord_bytes, ci_off = rp_off + (size_t)(nr + 1) * 4;
+  const size_t val_off = (ci_off + (size_t)ne * 4 + 7) / 8 * 8;
+  const bool ordered = ord_bytes <= cg.smem;
+  const bool staged = val_off + (size_t)ne * 8 <= cg.smem;
+  int *s_ord = (int *)cg_smem;
+  int *s_rp = (int *)(cg_smem + rp_off);
+  int *s_ci = (int *)(cg_smem + ci_off);
+  double *s_val = (double *)(cg_smem + val_off);
   if (threadIdx.x == 0) fail_sh = 0;
   if (staged) {
     for (int k = threadIdx.x; k < ne; k += blockDim.x) { s_val[k] = val[e0 + k]; s_ci[k] = ci[e0 + k]; }
     for (int k = threadIdx.x; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k] - e0;
   }
   __syncthreads();
+  if (ordered) {
+    __shared__ int ord_sh[32];
+    block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; });
+  }
+  // thread t handles the block's rows at order positions t, t + blockDim, ...
+  auto row_at = [&](int t) { return r0 + (ordered ? s_ord[t] : t); };
   const double *lval = staged ? s_val : val + e0;
   const int *lci = staged ? s_ci : ci + e0;
   GridBarrier gb{cg.bar, 0u};
@@ -323,7 +397,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   __shared__ double sc[3];
   // initial phase: r0 = f, u0 = D^-1 f, w0 = A u0, s = p = x = 0
   double v[3] = {0.0, 0.0, 0.0};
-  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const int i = row_at(t);
     const double fi = (double)f[i], di = __ldg(&dinv[i]);
     const double ui = __dmul_rn(fi, di);
     double wi = 0.0;
@@ -371,7 +446,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       const double *ro = cg.r[cur], *wo = cg.w[cur], *so = cg.s[cur];
       double *rn = cg.r[cur ^ 1], *wn = cg.w[cur ^ 1], *sn = cg.s[cur ^ 1];
       double acc[3] = {0.0, 0.0, 0.0};
-      for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const int i = row_at(t);
         const double di = __ldg(&dinv[i]);
         const double rold = __ldcg(&ro[i]), wold = __ldcg(&wo[i]), sold = __ldcg(&so[i]);
         const double uold = __dmul_rn(rold, di);
@@ -549,7 +625,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
     const double BA = bytes_A(l, (int)szv);
     if (nu_pre == 1 && l.fuse_pre) {
       LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
-      DISPATCH_TPR(l, k_residual0, l.n, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
+      DISPATCH_TPR(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
       cur[k] = a;
     } else {
       {
@@ -558,13 +634,13 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       }
       for (int sw = 1; sw < nu_pre; ++sw) {
         LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, a, fk[k], b, st);
+        DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, a, fk[k], b, st);
         std::swap(a, b);
       }
       cur[k] = a;
       {
         LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
-        DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, a, fk[k], b, st);
+        DISPATCH_TPR(l, k_residual, l.n, l.perm, l.rp, l.ci, val, a, fk[k], b, st);
       }
     }
     {
@@ -599,7 +675,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       if (l.fuse_post) {
         T *o = (nu_post == 1) ? final_out : other;
         LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
-        DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
+        DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
         curb = o;
         spare = in;
         sweeps -= 1;
@@ -612,7 +688,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       for (int sw = 0; sw < sweeps; ++sw) {
         T *dst = (sw == sweeps - 1) ? final_out : spare;
         LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, curb, fk[k], dst, st);
+        DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, curb, fk[k], dst, st);
         spare = curb;
         curb = dst;
       }
@@ -751,6 +827,13 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
     AMG_TRY(read_eflags(h, s, &f));
     if (f & AMG_EFLAG_NONSYM) return AMG_ERR_UNSUPPORTED;  // FP16 storage needs a positive diagonal
   }
+  // coarse levels are irregular: their row kernels visit rows by length class
+  for (int k = 1; k < h->L; ++k) {
+    Level &l = h->lev[k];
+    AMG_TRY(hier_alloc(h, (void **)&l.perm, sizeof(int32_t) * (l.n + AMG_PAD)));
+    k_level_order<<<cdiv(l.n, ORDER_WINDOW), 512, 0, s>>>(l.n, l.rp, l.perm);
+    count_launch();
+  }
   apply_tuned(h);
   // Krylov work vectors at level 0 (FP64 in every precision)
   const int n = h->lev[0].n;
@@ -824,28 +907,28 @@ amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
       Level lt = l;
       lt.tpr = tpr;
       float ms = time_launch<T>(s, ea, eb, reps, [&]() {
-        DISPATCH_TPR(lt, k_residual, lt.n, lt.rp, lt.ci, val, x, f, t, (const KState *)nullptr);
+        DISPATCH_TPR(lt, k_residual, lt.n, lt.perm, lt.rp, lt.ci, val, x, f, t, (const KState *)nullptr);
       });
       if (ms < best) { best = ms; best_tpr = tpr; }
     }
     l.tpr = best_tpr;
     // first presmoothing sweep: fused with the residual, or separate
     float pre_fused = time_launch<T>(s, ea, eb, reps, [&]() {
-      DISPATCH_TPR(l, k_residual0, l.n, l.rp, l.ci, val, dinv, omega, f, x, t, (const KState *)nullptr);
+      DISPATCH_TPR(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, f, x, t, (const KState *)nullptr);
     });
     float pre_split = time_launch<T>(s, ea, eb, reps, [&]() {
       k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, f, dinv, omega, x, nullptr);
-      DISPATCH_TPR(l, k_residual, l.n, l.rp, l.ci, val, x, f, t, (const KState *)nullptr);
+      DISPATCH_TPR(l, k_residual, l.n, l.perm, l.rp, l.ci, val, x, f, t, (const KState *)nullptr);
     });
     l.fuse_pre = pre_fused <= pre_split ? 1 : 0;
     // prolongation: fused into the first postsmoothing sweep, or separate
     float post_fused = time_launch<T>(s, ea, eb, reps, [&]() {
-      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, sig, isig_c, f, y,
+      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, sig, isig_c, f, y,
                    (const KState *)nullptr);
     });
     float post_split = time_launch<T>(s, ea, eb, reps, [&]() {
       k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, x, l.agg, xc, sig, isig_c, t, nullptr);
-      DISPATCH_TPR(l, k_jacobi, l.n, l.rp, l.ci, val, dinv, omega, t, f, y, (const KState *)nullptr);
+      DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, t, f, y, (const KState *)nullptr);
     });
     l.fuse_post = post_fused <= post_split ? 1 : 0;
     count_launch(0);

@@ -1,0 +1,57 @@
+"""Continuous-batching server: every request converges, each result is the same
+(bitwise) alone and in the mix, admission respects the memory budget, and the
+hierarchy cache is reused."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2007_00056_gb300 import amg  # noqa: E402
+from paper_2007_00056_gb300 import serving as S  # noqa: E402
+from paper_2007_00056_gb300 import workloads as W  # noqa: E402
+
+
+def _stream(count=24, n_hi=6e4):
+    reqs = W.request_stream(count=count, rate_hz=2000.0, n_lo=1e3, n_hi=n_hi, seed=11)
+    return reqs, [r.system() for r in reqs]
+
+
+def test_server_mix_equals_alone_and_converges():
+    reqs, systems = _stream()
+    srv = S.SolveServer(workers=4, small_max_n=20000)
+    mixed, wall = S.serve_stream(srv, reqs, systems)
+    srv.close()
+    assert {r.path for r in mixed} == {"batch", "single"}, "the stream should exercise both paths"
+    for r in mixed:
+        assert r.status == amg.AMG_OK and r.rel_res_true <= 1.05e-8, r
+    # each request alone, through a fresh server
+    alone = S.SolveServer(workers=1, small_max_n=20000)
+    for req, s, r in zip(reqs, systems, mixed):
+        alone.submit(req.rid, s.rp, s.ci, s.val, s.b, arrival=0.0)
+        a = alone.wait([req.rid])[0]
+        assert a.path == r.path
+        assert np.array_equal(a.x.view(np.int64), r.x.view(np.int64)), f"request {req.rid} differs alone vs mixed"
+    alone.close()
+    summ = S.latency_summary(mixed)
+    assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_admission_budget_and_cache():
+    reqs, systems = _stream(count=6, n_hi=8e3)
+    need = max(S.estimate_bytes(s.n, s.nnz, amg.AMG_FP32) for s in systems)
+    srv = S.SolveServer(workers=3, memory_budget=int(1.5 * need), cache_entries=2)
+    res, _ = S.serve_stream(srv, reqs, systems)
+    assert all(r.status == amg.AMG_OK for r in res)
+    assert srv.stats["evicted"] >= 1  # the small budget forced evictions
+    # the same matrix again hits the cache and gives the same solution
+    s = systems[-1]
+    srv.submit(1000, s.rp, s.ci, s.val, s.b, arrival=0.0)
+    again = srv.wait([1000])[0]
+    assert srv.stats["cache_hit"] >= 1
+    assert np.array_equal(again.x, res[-1].x)
+    with pytest.raises(MemoryError):
+        big = W.poisson2d(300)
+        srv.submit(2000, big.rp, big.ci, big.val, big.b, arrival=0.0)
+    srv.close()
