@@ -44,6 +44,10 @@ def parse_args():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=192,
+                    help="requests of the serving stream sample added to the line (0: none)")
+    ap.add_argument("--workload", choices=["solve", "serving"], default="solve",
+                    help="serving: run the full 2048-request stream and print only its line")
     return ap.parse_args()
 
 
@@ -219,6 +223,71 @@ def run_reference(args, sys_):
 
 
 # ---------------------------------------------------------------------------
+# serving stream (continuous batching)
+# ---------------------------------------------------------------------------
+def _gen_request(req):
+    s = req.system()
+    return req.rid, s.rp, s.ci, s.val, s.b
+
+
+def generate_requests(count: int):
+    """The first `count` requests of the 2048-request stream (Poisson arrivals at
+    200/s, N log-uniform in [1e3, 1e6]) and their systems, generated on the host
+    by a spawn-context process pool (safe after CUDA initialisation)."""
+    import multiprocessing as mp
+
+    from paper_2007_00056_gb300 import workloads as W
+
+    reqs = W.request_stream(count=2048)[:count]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        out = pool.map(_gen_request, reqs, chunksize=1)
+    systems = {rid: W.System(f"req{rid}", rp, ci, val, b) for rid, rp, ci, val, b in out}
+    return reqs, [systems[r.rid] for r in reqs]
+
+
+def run_serving(reqs, systems):
+    """Serves the stream at its arrival times (latency), then all at once
+    (capacity), then the plain FP64 method one request at a time (context)."""
+    import numpy as np
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import serving as S
+
+    total_n = sum(s.n for s in systems)
+    srv = S.SolveServer()
+    res, wall = S.serve_stream(srv, reqs, systems)
+    stats = dict(srv.stats)
+    srv.close()
+    srv = S.SolveServer()
+    res_cap, wall_cap = S.serve_stream(srv, reqs, systems, time_scale=0.0)
+    srv.close()
+    ok = sum(r.status == amg.AMG_OK and r.rel_res_true <= 1.05e-8 for r in res)
+    # plain FP64 method: setup + pcg_solve per request, sequential, same device
+    dev = torch.device("cuda", torch.cuda.current_device())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in systems:
+        rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
+        h = amg.amg_setup(rp, ci, val, amg.amg_default_params())
+        x = torch.zeros_like(b)
+        amg.pcg_solve(h, b, x, rtol=RTOL, flexible=not h.sizes()[-1] <= 4096)
+        x.cpu()
+        h.close()
+    plain = time.perf_counter() - t0
+    lat = S.latency_summary(res)
+    return {
+        "requests": len(reqs), "unknowns_total": int(total_n), "converged_1e-8": int(ok),
+        "arrival_rate_hz": 200.0, "solves_per_s": len(reqs) / wall, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+        "capacity_solves_per_s": len(reqs) / wall_cap,
+        "capacity_p50_ms": S.latency_summary(res_cap)["p50_ms"],
+        "plain_fp64_sequential_solves_per_s": len(reqs) / plain,
+        "batched_requests": int(stats.get("batched", 0)), "batches": int(stats.get("batches", 0)),
+        "precision": "fp32 V-cycle, fp64 flexible PCG",
+    }
+
+
+# ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
 def main():
@@ -229,6 +298,17 @@ def main():
         if int(os.environ.get("RANK", "0")) != 0:
             return
         run_reference(args, W.lognormal3d(args.grid, seed=1))
+        return
+    if args.workload == "serving":
+        reqs, systems = generate_requests(2048)
+        from paper_2007_00056_gb300 import amg
+
+        amg.lib(build_if_missing=True)
+        out = run_serving(reqs, systems)
+        out.update({"metric": METRIC, "unit": "solves/s", "value": out["solves_per_s"], "n_gpus": 1,
+                    "higher_is_better": True, "data": "synthetic", "dtype": "f32/f64",
+                    "config": {"workload": "serving stream, 2048 requests, Poisson arrivals 200/s"}})
+        print(json.dumps(out), flush=True)
         return
 
     rank, world, local = dist_setup(args)
@@ -377,6 +457,11 @@ def main():
                           f"samples ({statistics.mean(ts):.3f} s each), extrapolated to {it_gpu} iterations"),
                "time_to_solution_s": t_solve}
 
+    serving = None
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        reqs, systems = generate_requests(args.serving_requests)
+        serving = run_serving(reqs, systems)
+
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -394,6 +479,7 @@ def main():
             "roofline": roofline, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -275,13 +275,13 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
 // ---------------------------------------------------------------------------
 // Coarsest solve: Jacobi-PCG to ||r|| <= 1e-12 ||f|| (max 1000 iterations) in
 // the Chronopoulos-Gear arrangement, so the three inner products of an
-// iteration come from one grid reduction: one persistent cooperative kernel,
-// one bounded software grid barrier per iteration.  Block b owns a contiguous
-// row range and stages its matrix slice in shared memory.  A row's next
-// preconditioned residual u_j = D^-1 (r_j - alpha (w_j + beta s_j)) is formed
-// by its owner and, identically, by every block that gathers it, from the
-// previous iteration's copies of r, w, s (double-buffered), so the SpMV of
-// iteration k+1 needs no barrier after the updates of iteration k.
+// iteration come from one grid reduction: one persistent cooperative kernel
+// per solve, two bounded software grid barriers per iteration (after the new
+// preconditioned residual u = D^-1 r is published, and in the reduction).
+// Block b owns a contiguous row range: it stages its matrix slice and keeps
+// the state of its rows (r, s, p, x, w, u) in shared memory, so the only
+// global traffic of an iteration is u: written by owners, gathered once per
+// nonzero by the SpMV.
 // ---------------------------------------------------------------------------
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
@@ -321,9 +321,6 @@ struct GridBarrier {
   }
 };
 
-__device__ __forceinline__ double cg_unext(double r, double w, double s, double d, double alpha, double beta) {
-  return __dmul_rn(__fma_rn(-alpha, __fma_rn(beta, s, w), r), d);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS, 1)
@@ -333,19 +330,24 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   if (is_done(st)) return;
   extern __shared__ __align__(16) unsigned char cg_smem[];
   __shared__ double red_sh[3 * 32];
-  __shared__ double red[3];
   __shared__ int fail_sh;
+  __shared__ int ord_sh[32];
   const unsigned G = gridDim.x;
   const int R = (n + (int)G - 1) / (int)G;
   const int r0 = min(n, (int)blockIdx.x * R), r1 = min(n, r0 + R), nr = r1 - r0;
   const int e0 = rp[r0], e1 = rp[r1], ne = e1 - e0;
-  // dynamic shared memory: [row order: nr][row pointers: nr+1][cols: ne][values: ne]
+  // dynamic shared memory, in order of priority:
+  //   [row order: nr ints][row state r,s,p,x,w,u: 6 nr doubles][row pointers: nr+1][cols: ne][values: ne]
   const size_t ord_bytes = (size_t)nr * 4;
-  const size_t rp_off = ord_bytes, ci_off = rp_off + (size_t)(nr + 1) * 4;
+  const size_t st_off = (ord_bytes + 7) / 8 * 8;
+  const size_t rp_off = st_off + (size_t)nr * 48;
+  const size_t ci_off = rp_off + (size_t)(nr + 1) * 4;
   const size_t val_off = (ci_off + (size_t)ne * 4 + 7) / 8 * 8;
   const bool ordered = ord_bytes <= cg.smem;
+  const bool local_state = rp_off <= cg.smem;
   const bool staged = val_off + (size_t)ne * 8 <= cg.smem;
   int *s_ord = (int *)cg_smem;
+  double *s_st = (double *)(cg_smem + st_off);
   int *s_rp = (int *)(cg_smem + rp_off);
   int *s_ci = (int *)(cg_smem + ci_off);
   double *s_val = (double *)(cg_smem + val_off);
@@ -355,18 +357,24 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     for (int k = threadIdx.x; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k] - e0;
   }
   __syncthreads();
-  if (ordered) {
-    __shared__ int ord_sh[32];
-    block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; });
-  }
-  // thread t handles the block's rows at order positions t, t + blockDim, ...
-  auto row_at = [&](int t) { return r0 + (ordered ? s_ord[t] : t); };
+  if (ordered) block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; });
+  // local row k of this block: state in shared memory, or in the global work arrays
+  double *vr = local_state ? s_st : cg.r[1] + r0;
+  double *vs = local_state ? s_st + nr : cg.s[0] + r0;
+  double *vp = local_state ? s_st + 2 * nr : cg.p + r0;
+  double *vx = local_state ? s_st + 3 * nr : cg.x + r0;
+  double *vw = local_state ? s_st + 4 * nr : cg.w[0] + r0;
+  double *vu = local_state ? s_st + 5 * nr : cg.s[1] + r0;
+  double *u = cg.r[0];  // published preconditioned residual, read by every block's SpMV
   const double *lval = staged ? s_val : val + e0;
   const int *lci = staged ? s_ci : ci + e0;
+  auto row_begin = [&](int i) { return staged ? s_rp[i - r0] : __ldg(&rp[i]) - e0; };
+  // thread t handles the block's local rows at order positions t, t + blockDim, ...
+  auto local_at = [&](int t) { return ordered ? s_ord[t] : t; };
   GridBarrier gb{cg.bar, 0u};
   int slot = 0;
   // block partial sums -> barrier -> warp 0 sums the G partials in index order;
-  // the totals are valid in thread 0 only (it alone evaluates the scalars)
+  // the totals are valid in warp 0 (thread 0 evaluates the scalars)
   auto reduce3 = [&](double (&v)[3]) -> bool {
     block_sum<3>(v, red_sh);
     double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
@@ -390,44 +398,50 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     slot ^= 1;
     return ok;
   };
-  auto row_begin = [&](int i) { return staged ? s_rp[i - r0] : __ldg(&rp[i]) - e0; };
-
-  double *x = cg.x, *p = cg.p;
-  // scalars broadcast from thread 0: [0] alpha, [1] beta, [2] stop flag
-  __shared__ double sc[3];
-  // initial phase: r0 = f, u0 = D^-1 f, w0 = A u0, s = p = x = 0
-  double v[3] = {0.0, 0.0, 0.0};
-  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    const int i = row_at(t);
-    const double fi = (double)f[i], di = __ldg(&dinv[i]);
-    const double ui = __dmul_rn(fi, di);
-    double wi = 0.0;
-    const int b = row_begin(i), e = row_begin(i + 1);
-    for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
-      double fj[CG_CHUNK], dj[CG_CHUNK], vv[CG_CHUNK];
+  // w = A u for the thread's rows (one gather per nonzero, a chunk in flight at once);
+  // accumulates (r,u), (w,u), (r,r) into acc
+  auto spmv_dots = [&](double (&acc)[3]) {
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int k = local_at(t), i = r0 + k;
+      double wi = 0.0;
+      const int b = row_begin(i), e = row_begin(i + 1);
+      for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
+        double uu[CG_CHUNK], vv[CG_CHUNK];
 #pragma unroll
-      for (int u = 0; u < CG_CHUNK; ++u) {
-        const bool in = k0 + u < e;
-        const int j = in ? lci[k0 + u] : i;
-        vv[u] = in ? lval[k0 + u] : 0.0;
-        fj[u] = (double)f[j];
-        dj[u] = __ldg(&dinv[j]);
+        for (int q = 0; q < CG_CHUNK; ++q) {
+          const bool in = k0 + q < e;
+          vv[q] = in ? lval[k0 + q] : 0.0;
+          uu[q] = __ldcg(&u[in ? lci[k0 + q] : i]);
+        }
+#pragma unroll
+        for (int q = 0; q < CG_CHUNK; ++q)
+          if (k0 + q < e) wi += vv[q] * uu[q];
       }
-#pragma unroll
-      for (int u = 0; u < CG_CHUNK; ++u)
-        if (k0 + u < e) wi += vv[u] * __dmul_rn(fj[u], dj[u]);
+      vw[k] = wi;
+      const double ri = vr[k], ui = vu[k];
+      acc[0] += ri * ui;
+      acc[1] += wi * ui;
+      acc[2] += ri * ri;
     }
-    cg.r[0][i] = fi;
-    cg.w[0][i] = wi;
-    cg.s[0][i] = 0.0;
-    x[i] = 0.0;
-    p[i] = 0.0;
-    v[0] += fi * ui;
-    v[1] += wi * ui;
-    v[2] += fi * fi;
+  };
+
+  __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
+  // initial phase: r0 = f, u0 = D^-1 f (published), s = p = x = 0; then w0 = A u0
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const int k = local_at(t), i = r0 + k;
+    const double fi = (double)f[i];
+    const double ui = __dmul_rn(fi, __ldg(&dinv[i]));
+    vr[k] = fi;
+    vu[k] = ui;
+    u[i] = ui;
+    vs[k] = 0.0;
+    vp[k] = 0.0;
+    vx[k] = 0.0;
   }
-  bool ok = reduce3(v);
-  // thread 0 keeps the recurrence scalars
+  bool ok = gb.sync(G, eflags, &fail_sh);
+  double v[3] = {0.0, 0.0, 0.0};
+  if (ok) spmv_dots(v);
+  ok = reduce3(v) && ok;
   double fnorm = 0.0, gamma = 0.0, alpha_t = 0.0, beta_t = 0.0;
   if (threadIdx.x == 0) {
     fnorm = sqrt(v[2]);
@@ -440,56 +454,27 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   __syncthreads();
   int it = 0;
   if (sc[2] == 0.0) {
-    int cur = 0;
     for (it = 1; it <= CG_MAXIT; ++it) {
       const double alpha = sc[0], beta = sc[1];
-      const double *ro = cg.r[cur], *wo = cg.w[cur], *so = cg.s[cur];
-      double *rn = cg.r[cur ^ 1], *wn = cg.w[cur ^ 1], *sn = cg.s[cur ^ 1];
-      double acc[3] = {0.0, 0.0, 0.0};
+      // phase A (own rows): p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
       for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    const int i = row_at(t);
-        const double di = __ldg(&dinv[i]);
-        const double rold = __ldcg(&ro[i]), wold = __ldcg(&wo[i]), sold = __ldcg(&so[i]);
-        const double uold = __dmul_rn(rold, di);
-        const double pi = __fma_rn(beta, __ldcg(&p[i]), uold);
-        const double snew = __fma_rn(beta, sold, wold);
-        const double rnew = __fma_rn(-alpha, snew, rold);
-        const double unew = __dmul_rn(rnew, di);
-        x[i] = __fma_rn(alpha, pi, __ldcg(&x[i]));
-        p[i] = pi;
-        // gathers of a chunk of neighbours are issued together (the SpMV is
-        // bound by L2 latency, not bandwidth); the sum keeps the stored order
-        double wi = 0.0;
-        const int b = row_begin(i), e = row_begin(i + 1);
-        for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
-          int jj[CG_CHUNK];
-          double vv[CG_CHUNK], rj[CG_CHUNK], wj[CG_CHUNK], sj[CG_CHUNK], dj[CG_CHUNK];
-#pragma unroll
-          for (int u = 0; u < CG_CHUNK; ++u) {
-            const bool in = k0 + u < e;
-            jj[u] = in ? lci[k0 + u] : i;
-            vv[u] = in ? lval[k0 + u] : 0.0;
-          }
-#pragma unroll
-          for (int u = 0; u < CG_CHUNK; ++u) {
-            rj[u] = __ldcg(&ro[jj[u]]);
-            wj[u] = __ldcg(&wo[jj[u]]);
-            sj[u] = __ldcg(&so[jj[u]]);
-            dj[u] = __ldg(&dinv[jj[u]]);
-          }
-#pragma unroll
-          for (int u = 0; u < CG_CHUNK; ++u)
-            if (k0 + u < e) wi += vv[u] * cg_unext(rj[u], wj[u], sj[u], dj[u], alpha, beta);
-        }
-        rn[i] = rnew;
-        sn[i] = snew;
-        wn[i] = wi;
-        acc[0] += rnew * unew;
-        acc[1] += wi * unew;
-        acc[2] += rnew * rnew;
+        const int k = local_at(t), i = r0 + k;
+        const double pi = __fma_rn(beta, vp[k], vu[k]);
+        const double si = __fma_rn(beta, vs[k], vw[k]);
+        vx[k] = __fma_rn(alpha, pi, vx[k]);
+        const double ri = __fma_rn(-alpha, si, vr[k]);
+        const double ui = __dmul_rn(ri, __ldg(&dinv[i]));
+        vp[k] = pi;
+        vs[k] = si;
+        vr[k] = ri;
+        vu[k] = ui;
+        u[i] = ui;
       }
-      ok = reduce3(acc);
-      cur ^= 1;
+      ok = gb.sync(G, eflags, &fail_sh);
+      // phase B: w = A u and the three inner products, one reduction
+      double acc[3] = {0.0, 0.0, 0.0};
+      if (ok) spmv_dots(acc);
+      ok = reduce3(acc) && ok;
       if (threadIdx.x == 0) {
         bool stop = !ok || fail_sh != 0 || sqrt(acc[2]) <= CG_RTOL * fnorm;
         if (!stop) {
@@ -508,7 +493,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     }
     if (it > CG_MAXIT) it = CG_MAXIT;
   }
-  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) xout[i] = (T)__ldcg(&x[i]);
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const int k = local_at(t);
+    xout[r0 + k] = (T)vx[k];
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *cg.iters = it;
     atomicAdd(cg.iters_total, (unsigned long long)it);
