@@ -194,6 +194,14 @@ amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_p
 
 /* ---- Instrumentation (no counterpart in the paper; used for measurement) ---- */
 
+/* Self-test of the library's bounded device waits: `blocks` (1..64) blocks
+ * wait at the grid barrier used by the coarse solver for one arrival that
+ * never comes; each must give up after about 2 ms of clock cycles.  Returns
+ * AMG_ERR_TIMEOUT when every block reported the timeout (the expected
+ * outcome), AMG_OK if any block passed the barrier (a defect), or a CUDA
+ * error.  The device stays usable afterwards.  Synchronises the stream. */
+amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream);
+
 /* Kernel kinds reported by the per-kernel profiler.  Each kind is tracked per
  * level (0 = finest); Krylov kinds are reported at level 0. */
 typedef enum {

@@ -34,6 +34,7 @@ EXPORTS = (
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
+    "amg_selftest_wait_timeout",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -109,6 +110,7 @@ def lib(build_if_missing: bool = False):
             l.amg_profile_reset.argtypes = [vp]
             l.amg_profile_read.argtypes = [vp, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_longlong)]
             l.amg_autotune.argtypes = [vp, vp]
+            l.amg_selftest_wait_timeout.argtypes = [i32, vp]
             l.amg_batch_pcg.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, i32, i32, vp,
                                         C.POINTER(amg_solve_info)]
             l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]
@@ -361,3 +363,8 @@ def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible
     if st not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN):
         raise AmgError(st, "amg_batch_pcg")
     return list(infos)
+
+
+def amg_selftest_wait_timeout(blocks: int = 8, stream=None) -> int:
+    """Runs the bounded-wait self-test; returns the status (AMG_ERR_TIMEOUT expected)."""
+    return lib().amg_selftest_wait_timeout(int(blocks), _stream(stream))

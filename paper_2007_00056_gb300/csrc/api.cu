@@ -201,13 +201,17 @@ extern "C" amg_status amg_export_level(const amg_hierarchy *h, int level, int32_
 
 extern "C" void amg_destroy(amg_hierarchy *h) {
   if (!h) return;
-  cudaDeviceSynchronize();
+  // wait for the latest work that used the hierarchy (its calls are otherwise
+  // synchronous), not for the whole device: other streams keep running
+  cudaStreamSynchronize(h->last_stream ? h->last_stream : h->stream);
+  cudaGetLastError();
   if (h->g_vcycle) cudaGraphExecDestroy(h->g_vcycle);
   if (h->g_pcg) cudaGraphExecDestroy(h->g_pcg);
   if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
   prof_flush(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
-  for (void *p : h->allocs) pool_free(p, nullptr);
+  // stream-ordered frees back into the library pool, on the hierarchy's own stream
+  for (void *p : h->allocs) pool_free(p, h->cap_stream);
   pinned_small_free(h->st_host);
   pinned_small_free(h->eflags_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

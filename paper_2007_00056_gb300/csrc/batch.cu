@@ -327,6 +327,7 @@ extern "C" amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const do
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return AMG_ERR_INVALID_ARG;  // a hierarchy's work vectors serve one solve
     AMG_TRY(batch_descriptor(hs[i], s, &jobs[i].sys));
+    hs[i]->last_stream = s;
     jobs[i].b = d_b[i];
     jobs[i].x = d_x[i];
   }

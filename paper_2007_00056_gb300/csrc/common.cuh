@@ -119,6 +119,7 @@ struct amg_hierarchy {
   unsigned *eflags_host = nullptr;
   std::vector<void *> allocs;
   cudaStream_t stream = nullptr;       // stream of amg_setup (stream-ordered allocations)
+  cudaStream_t last_stream = nullptr;  // stream of the latest call that used the hierarchy
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr;
   long long g_pcg_nodes = 0, g_bicg_nodes = 0;

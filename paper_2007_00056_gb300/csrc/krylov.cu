@@ -527,6 +527,7 @@ extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, doub
   if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
   const int n = h->lev[0].n;
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, flexible ? 1 : 0, s));
   AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
@@ -547,6 +548,7 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
   if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
   const int n = h->lev[0].n;
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, 0, s));
   {

@@ -778,6 +778,7 @@ extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, co
   amg_hierarchy *h = new amg_hierarchy();
   h->prm = p;
   h->stream = st;
+  h->last_stream = st;
   amg_status s = AMG_OK;
   do {
     if (cudaGetDevice(&h->device) != cudaSuccess) { s = AMG_ERR_CUDA; break; }

@@ -16,6 +16,7 @@
 #include <map>
 #include <mutex>
 #include <functional>
+#include <type_traits>
 #include <tuple>
 
 #include "common.cuh"
@@ -93,9 +94,10 @@ __device__ __forceinline__ int block_scan01(int flag, int *sh, int *total) {
 // ord[0..nr) = local indices 0..nr-1 grouped by length class, stable.
 // len_of(k) gives the length of local row k.  All threads of the block call it.
 template <typename LenF>
-__device__ void block_class_order(int nr, int *ord, int *sh, LenF len_of) {
+__device__ void block_class_order(int nr, int *ord, int *sh, LenF len_of, int *class_start = nullptr) {
   int base_pos = 0;
   for (int c = 0; c < ROW_CLASSES; ++c) {
+    if (class_start && threadIdx.x == 0) class_start[c] = base_pos;
     for (int b0 = 0; b0 < nr; b0 += blockDim.x) {
       const int k = b0 + threadIdx.x;
       const int flag = (k < nr && row_class(len_of(k)) == c) ? 1 : 0;
@@ -105,6 +107,7 @@ __device__ void block_class_order(int nr, int *ord, int *sh, LenF len_of) {
       base_pos += total;
     }
   }
+  if (class_start && threadIdx.x == 0) class_start[ROW_CLASSES] = base_pos;
   __syncthreads();
 }
 
@@ -300,6 +303,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
 struct GridBarrier {
   unsigned *count;
   unsigned target;
+  long long limit = BARRIER_SPIN_LIMIT;
   __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
     __syncthreads();
     target += G;
@@ -309,7 +313,7 @@ struct GridBarrier {
       long long t0 = clock64();
       while (ld_acquire_u32(count) < target) {
         __nanosleep(20);
-        if (clock64() - t0 > BARRIER_SPIN_LIMIT) {
+        if (clock64() - t0 > limit) {
           atomicOr(eflags, AMG_EFLAG_TIMEOUT);
           *fail_sh = 1;
           break;
@@ -332,9 +336,21 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   __shared__ double red_sh[3 * 32];
   __shared__ int fail_sh;
   __shared__ int ord_sh[32];
+  __shared__ int cls_start[ROW_CLASSES + 1];
   const unsigned G = gridDim.x;
-  const int R = (n + (int)G - 1) / (int)G;
-  const int r0 = min(n, (int)blockIdx.x * R), r1 = min(n, r0 + R), nr = r1 - r0;
+  // rows split so that every block holds about the same number of nonzeros
+  auto first_row_with = [&](long long target) {  // smallest r with rp[r] >= target
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if ((long long)rp[mid] >= target) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  };
+  const long long nnz_all = rp[n];
+  const int r0 = blockIdx.x == 0 ? 0 : first_row_with(nnz_all * blockIdx.x / G);
+  const int r1 = blockIdx.x + 1 == G ? n : first_row_with(nnz_all * (blockIdx.x + 1) / G);
+  const int nr = r1 - r0;
   const int e0 = rp[r0], e1 = rp[r1], ne = e1 - e0;
   // dynamic shared memory, in order of priority:
   //   [row order: nr ints][row state r,s,p,x,w,u: 6 nr doubles][row pointers: nr+1][cols: ne][values: ne]
@@ -357,7 +373,12 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     for (int k = threadIdx.x; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k] - e0;
   }
   __syncthreads();
-  if (ordered) block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; });
+  if (ordered) {
+    block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; }, cls_start);
+  } else if (threadIdx.x == 0) {
+    for (int c = 0; c <= ROW_CLASSES; ++c) cls_start[c] = 0;  // unordered: every row takes one lane
+  }
+  __syncthreads();
   // local row k of this block: state in shared memory, or in the global work arrays
   double *vr = local_state ? s_st : cg.r[1] + r0;
   double *vs = local_state ? s_st + nr : cg.s[0] + r0;
@@ -398,31 +419,56 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     slot ^= 1;
     return ok;
   };
-  // w = A u for the thread's rows (one gather per nonzero, a chunk in flight at once);
-  // accumulates (r,u), (w,u), (r,r) into acc
-  auto spmv_dots = [&](double (&acc)[3]) {
-    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-      const int k = local_at(t), i = r0 + k;
+  // w = A u for the block's rows and the three inner products (r,u), (w,u),
+  // (r,r).  Rows up to 16 entries take one lane each, 17-48 entries four
+  // lanes, longer rows a whole warp, so no lane walks a long chain of
+  // dependent gathers; a group's partial sums meet in a fixed shuffle tree.
+  auto spmv_group = [&](int pa, int pb, auto lanes_tag, double (&acc)[3]) {
+    constexpr int LN = decltype(lanes_tag)::value;
+    const int slots = (pb - pa) * LN;
+    const int warp_base = (threadIdx.x & ~31);
+    for (int s0 = 0; s0 + warp_base < slots; s0 += blockDim.x) {
+      const int slot = s0 + threadIdx.x;
+      const bool valid = slot < slots;
+      const int sub = slot % LN;
+      const int pos = pa + slot / LN;
+      const int k = valid ? local_at(pos) : 0;
+      const int i = r0 + k;
       double wi = 0.0;
-      const int b = row_begin(i), e = row_begin(i + 1);
-      for (int k0 = b; k0 < e; k0 += CG_CHUNK) {
-        double uu[CG_CHUNK], vv[CG_CHUNK];
+      if (valid) {
+        const int b = row_begin(i), e = row_begin(i + 1);
+        for (int k0 = b + sub * CG_CHUNK; k0 < e; k0 += LN * CG_CHUNK) {
+          double uu[CG_CHUNK], vv[CG_CHUNK];
 #pragma unroll
-        for (int q = 0; q < CG_CHUNK; ++q) {
-          const bool in = k0 + q < e;
-          vv[q] = in ? lval[k0 + q] : 0.0;
-          uu[q] = __ldcg(&u[in ? lci[k0 + q] : i]);
+          for (int q = 0; q < CG_CHUNK; ++q) {
+            const bool in = k0 + q < e;
+            vv[q] = in ? lval[k0 + q] : 0.0;
+            uu[q] = __ldcg(&u[in ? lci[k0 + q] : i]);
+          }
+#pragma unroll
+          for (int q = 0; q < CG_CHUNK; ++q)
+            if (k0 + q < e) wi += vv[q] * uu[q];
         }
-#pragma unroll
-        for (int q = 0; q < CG_CHUNK; ++q)
-          if (k0 + q < e) wi += vv[q] * uu[q];
       }
-      vw[k] = wi;
-      const double ri = vr[k], ui = vu[k];
-      acc[0] += ri * ui;
-      acc[1] += wi * ui;
-      acc[2] += ri * ri;
+      if (LN > 1) {
+#pragma unroll
+        for (int o = LN / 2; o > 0; o >>= 1) wi += __shfl_xor_sync(0xffffffffu, wi, o);
+      }
+      if (valid && sub == 0) {
+        vw[k] = wi;
+        const double ri = vr[k], ui = vu[k];
+        acc[0] += ri * ui;
+        acc[1] += wi * ui;
+        acc[2] += ri * ri;
+      }
     }
+  };
+  auto spmv_dots = [&](double (&acc)[3]) {
+    const int p1 = ordered ? cls_start[5] : nr;  // classes 0-4: up to 16 entries
+    const int p2 = ordered ? cls_start[8] : nr;  // classes 5-7: up to 48 entries
+    spmv_group(0, p1, std::integral_constant<int, 1>{}, acc);
+    spmv_group(p1, p2, std::integral_constant<int, 4>{}, acc);
+    spmv_group(p2, nr, std::integral_constant<int, 32>{}, acc);
   };
 
   __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
@@ -1019,10 +1065,51 @@ amg_status coarse_cg_launch(int n, const int32_t *rp, const int32_t *ci, const d
   return AMG_OK;
 }
 
+// Self-test of the bounded wait: every block waits at the grid barrier for
+// one more arrival than there are blocks, so the wait must give up after
+// `limit` cycles and report the timeout instead of hanging.
+__global__ void k_wait_selftest(unsigned *bar, unsigned *eflags, long long limit, int *out) {
+  __shared__ int fail_sh;
+  if (threadIdx.x == 0) fail_sh = 0;
+  __syncthreads();
+  GridBarrier gb{bar, 0u};
+  gb.limit = limit;
+  const bool ok = gb.sync(gridDim.x + 1, eflags, &fail_sh);
+  if (threadIdx.x == 0) atomicAdd(out, ok ? 0 : 1);
+}
+
+extern "C" amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream) {
+  if (blocks < 1 || blocks > 64) return AMG_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned *buf = nullptr;
+  AMG_TRY(pool_alloc((void **)&buf, 64, s));
+  AMG_CUDA(cudaMemsetAsync(buf, 0, 64, s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(64);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // all blocks resident: only the phantom is missing
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_wait_selftest, buf, buf + 4, (long long)(1 << 22), (int *)(buf + 8));
+  unsigned host[12] = {0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, buf, 48, cudaMemcpyDeviceToHost, s);
+  pool_free(buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return amg_cuda_status(e);
+  // every block must have given up and raised the timeout flag
+  if ((host[4] & AMG_EFLAG_TIMEOUT) && (int)host[8] == blocks) return AMG_ERR_TIMEOUT;
+  return AMG_OK;
+}
+
 extern "C" amg_status amg_vcycle(const amg_hierarchy *hc, const double *d_r, double *d_z, amg_stream_t stream) {
   if (!hc || !d_r || !d_z || d_r == d_z) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
   AMG_TRY(vcycle_run(h, d_r, d_z, s, nullptr));
   if (h->prof.on) prof_flush(h);
   unsigned f = 0;

@@ -11,10 +11,11 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    ``amg_setup`` (or a hit in the device hierarchy cache, keyed by a
    fingerprint of the matrix);
 3. solve: a request whose hierarchy fits the batched kernel (dense coarsest
-   level, at most ``small_max_n`` rows) joins the batch queue; a batcher
-   thread launches ``amg_batch_pcg`` on everything ready, again and again, so
-   requests that become ready while a batch runs join the next one (their
-   work overlaps with the large solves on the other streams).  Larger
+   level, at most ``small_max_n`` rows) joins the batch queue; batcher
+   threads (each with its own stream) launch ``amg_batch_pcg`` on whatever
+   became ready within a short window, again and again, so requests that
+   become ready while a batch runs join the next one, and batches overlap
+   with each other and with the large solves on the worker streams.  Larger
    requests run ``pcg_solve`` on their worker's stream;
 4. completion: the solution is copied to host memory; the latency is
    completion time minus arrival time.
@@ -84,9 +85,9 @@ class _Entry:
 
 class SolveServer:
     def __init__(self, device: int = 0, memory_budget: int | None = None, precision: int = amg.AMG_FP32,
-                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 6, small_max_n: int = 60000,
+                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 12, small_max_n: int = 60000,
                  batch_coarse_max: int = 256, big_coarse_max: int = 4096, max_batch: int = 256,
-                 cache_entries: int = 64):
+                 cache_entries: int = 64, batchers: int = 2, batch_window_s: float = 0.001):
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         amg.lib()
@@ -102,6 +103,7 @@ class SolveServer:
         self.big_coarse_max = big_coarse_max
         self.max_batch = max_batch
         self.cache_entries = cache_entries
+        self.batch_window_s = batch_window_s
         self._lock = threading.Condition()
         self._in_use = 0                      # bytes of admitted requests (inputs + work)
         self._cache: "collections.OrderedDict[str, _Entry]" = collections.OrderedDict()
@@ -112,10 +114,9 @@ class SolveServer:
         self._stop = False
         self.stats = collections.Counter()
         self._workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
-        self._batcher = threading.Thread(target=self._batch_loop, daemon=True)
-        for t in self._workers:
+        self._batchers = [threading.Thread(target=self._batch_loop, daemon=True) for _ in range(batchers)]
+        for t in self._workers + self._batchers:
             t.start()
-        self._batcher.start()
 
     # ------------------------------------------------------------------ admission
     def _params_for(self, n: int):
@@ -256,10 +257,13 @@ class SolveServer:
                 if self._stop:
                     return
                 continue
+            # gather what becomes ready within a short window after the first request
             group = [first]
+            deadline = time.perf_counter() + self.batch_window_s
             while len(group) < self.max_batch:
+                left = deadline - time.perf_counter()
                 try:
-                    group.append(self._batchq.get_nowait())
+                    group.append(self._batchq.get(timeout=left) if left > 0 else self._batchq.get_nowait())
                 except queue.Empty:
                     break
             try:
@@ -287,9 +291,8 @@ class SolveServer:
         with self._lock:
             self._stop = True
             self._lock.notify_all()
-        for t in self._workers:
+        for t in self._workers + self._batchers:
             t.join(timeout=10)
-        self._batcher.join(timeout=10)
         with self._lock:
             for e in self._cache.values():
                 e.h.close()
