@@ -279,6 +279,8 @@ def run_serving(reqs, systems):
     return {
         "requests": len(reqs), "unknowns_total": int(total_n), "converged_1e-8": int(ok),
         "arrival_rate_hz": 200.0, "solves_per_s": len(reqs) / wall, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+        "mean_queue_ms": lat.get("mean_queue_ms"), "mean_setup_ms": lat.get("mean_setup_ms"),
+        "mean_solve_ms": lat.get("mean_solve_ms"),
         "capacity_solves_per_s": len(reqs) / wall_cap,
         "capacity_p50_ms": S.latency_summary(res_cap)["p50_ms"],
         "plain_fp64_sequential_solves_per_s": len(reqs) / plain,

@@ -174,7 +174,9 @@ int amg_setup_rounds(const amg_hierarchy *h, int level, int pass);
 
 /* ---- Kernel autotuning (no counterpart in the paper) ----
  * Times, on each level of h, the threads-per-row choices of the row kernels
- * (1, 2, 4, ... 32 lanes per row) and the fused / separate forms of the first
+ * (1, 2, 4, ... 32 lanes per row, and 0: one lane per row reading tiles of
+ * the matrix that TMA bulk copies stage in shared memory) and the fused /
+ * separate forms of the first
  * pre-smoothing sweep (with the residual) and of the prolongation (with the
  * first post-smoothing sweep), keeps the fastest for h, and remembers the
  * choice by level shape (rows, nonzeros, precision) so that every later
@@ -188,8 +190,10 @@ amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream);
  * fused prolongation.  Returns 0, or -1 for a NULL h or a bad level. */
 int amg_level_config(const amg_hierarchy *h, int level, int *tpr, int *fuse_pre, int *fuse_post);
 
-/* Sets a level's kernel configuration by hand (tpr in {1,2,4,8,16,32}).
- * AMG_ERR_INVALID_ARG for a NULL h, a bad level or a bad tpr. */
+/* Sets a level's kernel configuration by hand (tpr in {0,1,2,4,8,16,32}).
+ * AMG_ERR_INVALID_ARG for a NULL h, a bad level or a bad tpr;
+ * AMG_ERR_UNSUPPORTED for tpr 0 on a level without the staged form (a
+ * tile of 256 rows too large for shared memory). */
 amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_pre, int fuse_post);
 
 /* ---- Instrumentation (no counterpart in the paper; used for measurement) ---- */
@@ -268,6 +272,10 @@ amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, c
 /* Frees every device allocation of h (NULL is a no-op).  Synchronises the
  * device work of h first. */
 void amg_destroy(amg_hierarchy *h);
+
+/* Text of the last CUDA runtime error behind an AMG_ERR_CUDA or AMG_ERR_OOM
+ * returned to the calling thread ("no CUDA error" if none). */
+const char *amg_last_cuda_error(void);
 
 /* Static English text for a status code. */
 const char *amg_status_string(amg_status s);

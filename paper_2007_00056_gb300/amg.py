@@ -34,7 +34,7 @@ EXPORTS = (
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
-    "amg_selftest_wait_timeout",
+    "amg_selftest_wait_timeout", "amg_last_cuda_error",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -43,7 +43,13 @@ KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "
 class AmgError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({status_string(status)})")
+        detail = status_string(status)
+        if status in (8, 4):  # AMG_ERR_CUDA, AMG_ERR_OOM: name the CUDA error behind it
+            try:
+                detail += f"; {lib().amg_last_cuda_error().decode()}"
+            except Exception:
+                pass
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
 
 
 class amg_params(C.Structure):
@@ -111,6 +117,8 @@ def lib(build_if_missing: bool = False):
             l.amg_profile_read.argtypes = [vp, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_longlong)]
             l.amg_autotune.argtypes = [vp, vp]
             l.amg_selftest_wait_timeout.argtypes = [i32, vp]
+            l.amg_last_cuda_error.argtypes = []
+            l.amg_last_cuda_error.restype = C.c_char_p
             l.amg_batch_pcg.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, i32, i32, vp,
                                         C.POINTER(amg_solve_info)]
             l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]

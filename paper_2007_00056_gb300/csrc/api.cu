@@ -49,8 +49,11 @@ amg_status prof_flush(amg_hierarchy *h) {
   return AMG_OK;
 }
 
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+
 amg_status amg_cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return AMG_OK;
+  g_last_cuda_error = e;
   if (e == cudaErrorMemoryAllocation) return AMG_ERR_OOM;
   return AMG_ERR_CUDA;
 }
@@ -149,6 +152,10 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->coarse_solver = AMG_COARSE_AUTO;
   p->precision = AMG_FP64;
   return AMG_OK;
+}
+
+extern "C" const char *amg_last_cuda_error(void) {
+  return g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda_error);
 }
 
 extern "C" const char *amg_status_string(amg_status s) {

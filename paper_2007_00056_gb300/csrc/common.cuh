@@ -62,6 +62,8 @@ struct Level {
   float *f32 = nullptr, *x32 = nullptr, *t32 = nullptr, *y32 = nullptr;
   int rounds[AMG_MAX_PASSES] = {0};
   int tpr = 1;               // threads per row of this level's row kernels
+  int st_cap = 0;            // TMA-staged row kernels: entries per stage buffer (0: not offered)
+  int st_grid = 0;           // blocks of the persistent staged kernels
   int fuse_pre = 1;          // first presmoothing sweep fused into the residual kernel
   int fuse_post = 0;         // prolongation fused into the first postsmoothing sweep
 };
@@ -124,6 +126,7 @@ struct amg_hierarchy {
   cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr;
   long long g_pcg_nodes = 0, g_bicg_nodes = 0;
   int graphs_ok = 1;
+  int solves = 0;            // Krylov solves run on this hierarchy (graphs from the second one)
   Profiler prof;
   void *batch_desc = nullptr;  // device descriptor for batched solves (built on first use)
 };

@@ -446,7 +446,10 @@ amg_status get_graph(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long l
 }
 
 amg_status run_iterations(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long long *nodes, cudaStream_t s) {
-  const bool use_graph = !h->prof.on;
+  // a graph is captured once the hierarchy is reused: for a single solve the
+  // capture and instantiation cost more than the launches they save
+  const bool use_graph = !h->prof.on && (*exec != nullptr || h->solves >= 1);
+  h->solves += 1;
   if (use_graph) AMG_TRY(get_graph(h, fn, exec, nodes));
   // enqueue a few iterations between host checks; kernels after convergence are no-ops
   int chunk = 1;

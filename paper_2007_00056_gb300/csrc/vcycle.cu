@@ -180,6 +180,138 @@ __global__ void k_jacobi(int n, const int32_t *__restrict__ perm, const int32_t 
   ROW_LOOP_END
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged row kernels (lanes-per-row choice 0): each block walks tiles of
+// ST_ROWS consecutive rows; one elected thread copies a tile's values and
+// column indices into shared memory with cp.async.bulk (completion counted
+// by an mbarrier), double-buffered so the next tile streams in while the
+// current one is computed, and every thread then forms its row's sum from
+// shared memory.  This replaces the per-thread, uncoalesced row reads of the
+// one-lane kernels.  Waits are bounded: a copy that does not complete within
+// about a second sets the timeout flag and the block stops.
+// ---------------------------------------------------------------------------
+#define ST_ROWS 256
+// dynamic shared memory limit of the staged kernels (one value for every level:
+// the attribute belongs to the kernel, not to a launch)
+#define ST_SMEM_MAX (96 * 1024)
+#define ST_WAIT_LIMIT (1ll << 31)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait for a phase of the barrier; false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > ST_WAIT_LIMIT) return false;
+  return true;
+}
+
+// Byte layout of one stage buffer for a tile of at most `cap` stored entries.
+// (the aligned copy of a tile holding `cap` entries spans at most cap + 2*VA - 2
+// values and cap + 6 columns)
+template <typename V>
+__host__ __device__ __forceinline__ size_t st_val_bytes(int cap) {
+  return ((size_t)(cap + 2 * (16 / sizeof(V))) * sizeof(V) + 127) / 128 * 128;
+}
+__host__ __device__ __forceinline__ size_t st_col_bytes(int cap) { return ((size_t)(cap + 8) * 4 + 127) / 128 * 128; }
+
+// largest number of stored entries in a tile of ST_ROWS rows
+__global__ void k_tile_max(int n, const int32_t *__restrict__ rp, int *out) {
+  const int ntiles = (n + ST_ROWS - 1) / ST_ROWS;
+  int m = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x)
+    m = max(m, rp[min(n, (t + 1) * ST_ROWS)] - rp[t * ST_ROWS]);
+  atomicMax(out, m);
+}
+
+// MODE 0: out = f - A x.  MODE 1: out = x + omega D^-1 (f - A x).
+template <typename T, typename V, int MODE>
+__global__ void __launch_bounds__(ST_ROWS)
+    k_rows_staged(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const V *__restrict__ val,
+                  const T *__restrict__ dinv, T omega, const T *__restrict__ x, const T *__restrict__ f,
+                  T *__restrict__ out, int cap, unsigned *eflags, const KState *st) {
+  if (is_done(st)) return;
+  extern __shared__ __align__(128) unsigned char st_smem[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  const size_t vb = st_val_bytes<V>(cap), cb = st_col_bytes(cap);
+  V *sval[2] = {(V *)st_smem, (V *)(st_smem + vb + cb)};
+  int *scol[2] = {(int *)(st_smem + vb), (int *)(st_smem + 2 * vb + cb)};
+  constexpr int VA = 16 / sizeof(V);  // values per 16 bytes
+  const int ntiles = (n + ST_ROWS - 1) / ST_ROWS;
+  if (threadIdx.x == 0) {
+    mbar_init(&mbar[0], 1);
+    mbar_init(&mbar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  // one elected thread issues a tile's copies (16-byte aligned start and size;
+  // the arrays are padded, so rounding the end up stays inside them)
+  auto issue = [&](int tile, int b) {
+    const int r0 = tile * ST_ROWS, r1 = min(n, r0 + ST_ROWS);
+    const int e0 = rp[r0], e1 = rp[r1];
+    const int v0 = e0 & ~(VA - 1), v1 = (e1 + VA - 1) & ~(VA - 1);
+    const int c0 = e0 & ~3, c1 = (e1 + 3) & ~3;
+    const unsigned vbytes = (unsigned)(v1 - v0) * sizeof(V), cbytes = (unsigned)(c1 - c0) * 4u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&mbar[b], vbytes + cbytes);
+    if (vbytes) bulk_g2s(sval[b], val + v0, vbytes, &mbar[b]);
+    if (cbytes) bulk_g2s(scol[b], ci + c0, cbytes, &mbar[b]);
+  };
+  unsigned parity[2] = {0u, 0u};
+  int k = 0;
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++k) {
+    const int b = k & 1;
+    const int next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) issue(next, b ^ 1);
+    const bool ok = mbar_wait(&mbar[b], parity[b]);
+    parity[b] ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      // give up: flag it, wait (bounded) for the other buffer's copy, stop
+      if (threadIdx.x == 0) {
+        atomicOr(eflags, AMG_EFLAG_TIMEOUT);
+        if (next < ntiles) mbar_wait(&mbar[b ^ 1], parity[b ^ 1]);
+      }
+      return;
+    }
+    const int r0 = tile * ST_ROWS;
+    const int row = r0 + threadIdx.x;
+    if (row < n) {
+      const int e0t = rp[r0];
+      const int v0 = e0t & ~(VA - 1), c0 = e0t & ~3;
+      const int eb = rp[row], ee = rp[row + 1];
+      const V *lv = sval[b] - v0;
+      const int *lc = scol[b] - c0;
+      T ax = T(0);
+      for (int e = eb; e < ee; ++e) ax += as_arith(lv[e], T(0)) * __ldg(&x[lc[e]]);
+      if (MODE == 0) out[row] = f[row] - ax;
+      else out[row] = x[row] + omega * (dval(dinv, row) * (f[row] - ax));
+    }
+    __syncthreads();  // buffer b is refilled two tiles later
+  }
+}
+
 // Coarse correction of fine row i: x_c[agg_i], times isig_c[agg_i] when the
 // coarse level is scaled and times sig_i when the fine level is scaled.
 template <typename T>
@@ -610,6 +742,44 @@ inline double bytes_A(const Level &l, int vbytes) { return (double)l.nnz * (vbyt
     }                                                                                     \
   } while (0)
 
+// Residual t = f - A x and Jacobi sweep on a level, by its lanes-per-row
+// choice (0 = TMA-staged tiles).  Kernels without a staged form use one lane.
+template <typename T, typename V>
+void launch_residual(amg_hierarchy *h, const Level &l, const V *val, const T *x, const T *f, T *t, cudaStream_t s,
+                     const KState *st) {
+  if (l.tpr == 0 && l.st_cap > 0) {
+    const size_t smem = 2 * (st_val_bytes<V>(l.st_cap) + st_col_bytes(l.st_cap));
+    k_rows_staged<T, V, 0><<<l.st_grid, ST_ROWS, smem, s>>>(l.n, l.rp, l.ci, val, (const T *)nullptr, T(0), x, f, t,
+                                                             l.st_cap, h->eflags, st);
+    return;
+  }
+  Level lt = l;
+  if (lt.tpr == 0) lt.tpr = 1;
+  DISPATCH_TPR(lt, k_residual, lt.n, lt.perm, lt.rp, lt.ci, val, x, f, t, st);
+}
+
+template <typename T, typename V>
+void launch_jacobi(amg_hierarchy *h, const Level &l, const V *val, const T *dinv, T omega, const T *x, const T *f,
+                   T *out, cudaStream_t s, const KState *st) {
+  if (l.tpr == 0 && l.st_cap > 0) {
+    const size_t smem = 2 * (st_val_bytes<V>(l.st_cap) + st_col_bytes(l.st_cap));
+    k_rows_staged<T, V, 1><<<l.st_grid, ST_ROWS, smem, s>>>(l.n, l.rp, l.ci, val, dinv, omega, x, f, out, l.st_cap,
+                                                             h->eflags, st);
+    return;
+  }
+  Level lt = l;
+  if (lt.tpr == 0) lt.tpr = 1;
+  DISPATCH_TPR(lt, k_jacobi, lt.n, lt.perm, lt.rp, lt.ci, val, dinv, omega, x, f, out, st);
+}
+
+// Other row kernels: one lane per row when the level uses the staged form.
+#define DISPATCH_ROWS(l, KERNEL, ...)           \
+  do {                                          \
+    Level _lr = (l);                            \
+    if (_lr.tpr == 0) _lr.tpr = 1;              \
+    DISPATCH_TPR(_lr, KERNEL, __VA_ARGS__);     \
+  } while (0)
+
 template <typename T>
 void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KState *st) {
   Level &c = h->lev[h->L];
@@ -659,7 +829,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
     const double BA = bytes_A(l, (int)szv);
     if (nu_pre == 1 && l.fuse_pre) {
       LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
-      DISPATCH_TPR(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
+      DISPATCH_ROWS(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
       cur[k] = a;
     } else {
       {
@@ -668,13 +838,13 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       }
       for (int sw = 1; sw < nu_pre; ++sw) {
         LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, a, fk[k], b, st);
+        launch_jacobi<T, V>(h, l, val, dinv, omega, a, fk[k], b, s, st);
         std::swap(a, b);
       }
       cur[k] = a;
       {
         LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
-        DISPATCH_TPR(l, k_residual, l.n, l.perm, l.rp, l.ci, val, a, fk[k], b, st);
+        launch_residual<T, V>(h, l, val, a, fk[k], b, s, st);
       }
     }
     {
@@ -709,7 +879,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       if (l.fuse_post) {
         T *o = (nu_post == 1) ? final_out : other;
         LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
-        DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
+        DISPATCH_ROWS(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
         curb = o;
         spare = in;
         sweeps -= 1;
@@ -722,7 +892,7 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
       for (int sw = 0; sw < sweeps; ++sw) {
         T *dst = (sw == sweeps - 1) ? final_out : spare;
         LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, curb, fk[k], dst, st);
+        launch_jacobi<T, V>(h, l, val, dinv, omega, curb, fk[k], dst, s, st);
         spare = curb;
         curb = dst;
       }
@@ -861,6 +1031,47 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
     AMG_TRY(read_eflags(h, s, &f));
     if (f & AMG_EFLAG_NONSYM) return AMG_ERR_UNSUPPORTED;  // FP16 storage needs a positive diagonal
   }
+  // TMA-staged row kernels: stage capacity (largest tile) and persistent grid
+  {
+    int *d_max = nullptr;
+    AMG_TRY(pool_alloc((void **)&d_max, sizeof(int) * 64, s));
+    AMG_CUDA(cudaMemsetAsync(d_max, 0, sizeof(int) * 64, s));
+    for (int k = 0; k < h->L; ++k) {
+      k_tile_max<<<grid_for(cdiv(h->lev[k].n, ST_ROWS), 256, 512), 256, 0, s>>>(h->lev[k].n, h->lev[k].rp, d_max + k);
+      count_launch();
+    }
+    int hmax[64] = {0};
+    AMG_CUDA(cudaMemcpyAsync(hmax, d_max, sizeof(int) * 64, cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    pool_free(d_max, s);
+    for (int k = 0; k < h->L; ++k) {
+      Level &l = h->lev[k];
+      const bool f64 = h->prm.precision == AMG_FP64, f16 = h->prm.precision == AMG_FP16_STORAGE;
+      const void *vp = f64 ? (const void *)l.val : f16 ? (const void *)l.val16 : (const void *)l.val32;
+      const size_t vsz = f64 ? 8 : f16 ? 2 : 4;
+      const int cap = hmax[k];
+      const size_t smem = 2 * ((((size_t)cap + 2 * (16 / vsz)) * vsz + 127) / 128 * 128 + st_col_bytes(cap));
+      if (cap <= 0 || smem > ST_SMEM_MAX || ((uintptr_t)vp & 15) || ((uintptr_t)l.ci & 15)) continue;
+      int occ = 0;
+      cudaError_t e;
+      if (f64) {
+        cudaFuncSetAttribute(k_rows_staged<double, double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        cudaFuncSetAttribute(k_rows_staged<double, double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_staged<double, double, 0>, ST_ROWS, smem);
+      } else if (f16) {
+        cudaFuncSetAttribute(k_rows_staged<float, __half, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        cudaFuncSetAttribute(k_rows_staged<float, __half, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_staged<float, __half, 0>, ST_ROWS, smem);
+      } else {
+        cudaFuncSetAttribute(k_rows_staged<float, float, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        cudaFuncSetAttribute(k_rows_staged<float, float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM_MAX);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_rows_staged<float, float, 0>, ST_ROWS, smem);
+      }
+      if (e != cudaSuccess || occ < 1) { cudaGetLastError(); continue; }
+      l.st_cap = cap;
+      l.st_grid = std::max(1, std::min(cdiv(l.n, ST_ROWS), occ * h->num_sms));
+    }
+  }
   // coarse levels are irregular: their row kernels visit rows by length class
   for (int k = 1; k < h->L; ++k) {
     Level &l = h->lev[k];
@@ -935,34 +1146,33 @@ amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
     // threads per row: timed on the residual kernel
     int best_tpr = l.tpr;
     float best = 1e30f;
-    const int cands[] = {1, 2, 4, 8, 16, 32};
+    const int cands[] = {0, 1, 2, 4, 8, 16, 32};
     for (int tpr : cands) {
+      if (tpr == 0 && l.st_cap == 0) continue;
       if (tpr > 1 && tpr > 4.0 * avg) break;
       Level lt = l;
       lt.tpr = tpr;
-      float ms = time_launch<T>(s, ea, eb, reps, [&]() {
-        DISPATCH_TPR(lt, k_residual, lt.n, lt.perm, lt.rp, lt.ci, val, x, f, t, (const KState *)nullptr);
-      });
+      float ms = time_launch<T>(s, ea, eb, reps, [&]() { launch_residual<T, V>(h, lt, val, x, f, t, s, nullptr); });
       if (ms < best) { best = ms; best_tpr = tpr; }
     }
     l.tpr = best_tpr;
     // first presmoothing sweep: fused with the residual, or separate
     float pre_fused = time_launch<T>(s, ea, eb, reps, [&]() {
-      DISPATCH_TPR(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, f, x, t, (const KState *)nullptr);
+      DISPATCH_ROWS(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, f, x, t, (const KState *)nullptr);
     });
     float pre_split = time_launch<T>(s, ea, eb, reps, [&]() {
       k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, f, dinv, omega, x, nullptr);
-      DISPATCH_TPR(l, k_residual, l.n, l.perm, l.rp, l.ci, val, x, f, t, (const KState *)nullptr);
+      launch_residual<T, V>(h, l, val, x, f, t, s, nullptr);
     });
     l.fuse_pre = pre_fused <= pre_split ? 1 : 0;
     // prolongation: fused into the first postsmoothing sweep, or separate
     float post_fused = time_launch<T>(s, ea, eb, reps, [&]() {
-      DISPATCH_TPR(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, sig, isig_c, f, y,
-                   (const KState *)nullptr);
+      DISPATCH_ROWS(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, x, l.agg, xc, sig, isig_c, f, y,
+                    (const KState *)nullptr);
     });
     float post_split = time_launch<T>(s, ea, eb, reps, [&]() {
       k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, x, l.agg, xc, sig, isig_c, t, nullptr);
-      DISPATCH_TPR(l, k_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, t, f, y, (const KState *)nullptr);
+      launch_jacobi<T, V>(h, l, val, dinv, omega, t, f, y, s, nullptr);
     });
     l.fuse_post = post_fused <= post_split ? 1 : 0;
     count_launch(0);
@@ -1004,8 +1214,9 @@ extern "C" amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream) {
 
 extern "C" amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_pre, int fuse_post) {
   if (!h || level < 0 || level > h->L) return AMG_ERR_INVALID_ARG;
-  if (tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return AMG_ERR_INVALID_ARG;
+  if (tpr != 0 && tpr != 1 && tpr != 2 && tpr != 4 && tpr != 8 && tpr != 16 && tpr != 32) return AMG_ERR_INVALID_ARG;
   Level &l = h->lev[level];
+  if (tpr == 0 && l.st_cap == 0) return AMG_ERR_UNSUPPORTED;
   l.tpr = tpr;
   l.fuse_pre = fuse_pre ? 1 : 0;
   l.fuse_post = fuse_post ? 1 : 0;

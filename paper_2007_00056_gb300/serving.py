@@ -50,6 +50,8 @@ class ServeResult:
     admitted: float
     finished: float
     path: str  # "batch" or "single"
+    started: float = 0.0      # a worker picked the request up
+    setup_done: float = 0.0   # input on the device and hierarchy ready
 
     @property
     def latency(self) -> float:
@@ -178,6 +180,7 @@ class SolveServer:
 
     def _run(self, job, stream):
         rid, rp, ci, val, b, arrival, admitted, need = job
+        started = time.perf_counter()
         n = len(rp) - 1
         key = fingerprint(rp, ci, val)
         with torch.cuda.stream(stream):
@@ -207,6 +210,8 @@ class SolveServer:
                 self.stats["cache_hit"] += 1
             x = torch.zeros_like(d_b)
             h = entry.h
+            stream.synchronize()
+            setup_done = time.perf_counter()
             batchable = (n <= self.small_max_n and h.sizes()[-1] <= self.batch_coarse_max
                          and self._dense_coarse(h))
             if batchable:
@@ -228,7 +233,7 @@ class SolveServer:
             entry.users -= 1
             self._in_use -= need
             self._results[rid] = ServeResult(rid, hx.numpy(), info.iterations, info.rel_res_true, info.status,
-                                             arrival, admitted, fin, path)
+                                             arrival, admitted, fin, path, started, setup_done)
             self._lock.notify_all()
 
     def _evict_one_idle(self) -> bool:
@@ -317,5 +322,12 @@ def serve_stream(server: SolveServer, requests, systems, time_scale: float = 1.0
 
 def latency_summary(results):
     lat = np.array([r.latency for r in results])
-    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-            "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+    out = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+    done = [r for r in results if r.started > 0]
+    if done:
+        # where the time goes: waiting for a worker, setup (copy + hierarchy), solve
+        out["mean_queue_ms"] = float(np.mean([r.started - r.arrival for r in done]) * 1e3)
+        out["mean_setup_ms"] = float(np.mean([r.setup_done - r.started for r in done]) * 1e3)
+        out["mean_solve_ms"] = float(np.mean([r.finished - r.setup_done for r in done]) * 1e3)
+    return out
