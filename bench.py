@@ -31,6 +31,8 @@ METRIC = "AMG-PCG time to 1e-8 rel. residual; V-cycle HBM GB/s; batched solves/s
 UNIT = "solves/s"
 WORKLOAD = "lognormal3d_128: 3D 7-pt FV diffusion, 128^3 cells, lognormal(0,1) coefficients seed 1, FP64 CSR"
 RTOL = 1e-8
+# FP64 peak of GB300: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def parse_args():
@@ -46,6 +48,8 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=192,
                     help="requests of the serving stream sample added to the line (0: none)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (256^3 mixed precision, 2048^2 BiCGStab, 64^2 Poisson)")
     ap.add_argument("--workload", choices=["solve", "serving"], default="solve",
                     help="serving: run the full 2048-request stream and print only its line")
     return ap.parse_args()
@@ -269,7 +273,8 @@ def run_serving(reqs, systems):
     t0 = time.perf_counter()
     for s in systems:
         rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
-        h = amg.amg_setup(rp, ci, val, amg.amg_default_params())
+        # the server's hierarchy shape (coarsest size) in plain FP64
+        h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=256 if s.n <= 60000 else 1024))
         x = torch.zeros_like(b)
         amg.pcg_solve(h, b, x, rtol=RTOL, flexible=not h.sizes()[-1] <= 4096)
         x.cpu()
@@ -287,6 +292,95 @@ def run_serving(reqs, systems):
         "batched_requests": int(stats.get("batched", 0)), "batches": int(stats.get("batches", 0)),
         "precision": "fp32 V-cycle, fp64 flexible PCG",
     }
+
+
+VCYCLE_KINDS = {"jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
+                "coarse_cg", "cast"}
+
+
+def _solve_timed(sys_, params, krylov, dev, profile=False):
+    """Setup + Krylov solve of one system from device-resident inputs; CUDA
+    events on the current stream.  Returns times, the solve info, x and (with
+    profile) the V-cycle's algorithmic bytes and device time."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+
+    stream = torch.cuda.current_stream()
+    rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (sys_.rp, sys_.ci, sys_.val, sys_.b))
+    x = torch.zeros_like(b)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h = amg.amg_setup(rp, ci, val, params)
+    e1.record(stream)
+    if profile:
+        amg.amg_profile_enable(h, True)
+    solve = amg.pcg_solve if krylov == "pcg" else amg.bicgstab_solve
+    kw = {"flexible": True} if krylov == "pcg" else {}
+    info = solve(h, b, x, rtol=RTOL, max_iter=1000, **kw)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    vc_bytes = vc_ms = 0.0
+    if profile:
+        for r in amg.amg_profile_table(h):
+            if r["kind"] in VCYCLE_KINDS:
+                vc_bytes += r["bytes"]
+                vc_ms += r["ms"]
+    levels = h.sizes()
+    h.close()
+    return dict(setup_ms=e0.elapsed_time(e1), solve_ms=e1.elapsed_time(e2), info=info, x=x, levels=levels,
+                vc_bytes=vc_bytes, vc_ms=vc_ms)
+
+
+def run_configs(dev, peak):
+    """The other workloads of the method, measured on this GPU: the 256^3
+    anisotropic system in FP64 and both mixed-precision forms (flexible PCG),
+    the 2048^2 upwind convection-diffusion system with BiCGStab (FP32 V-cycle,
+    FP64 outer) at three Peclet numbers, and the 64^2 Poisson system.  Each
+    line: setup and solve time (a second solve after one untimed warm-up),
+    iterations, true relative residual, V-cycle GB/s from the library's event
+    profiler (a third, profiled solve) and, for the mixed-precision forms, the
+    relative 2-norm difference to the FP64 solution of the same system."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    out = []
+
+    def line(name, sys_, prec, krylov, x_ref=None):
+        params = amg.amg_default_params(precision=prec)
+        _solve_timed(sys_, params, krylov, dev)
+        r = _solve_timed(sys_, params, krylov, dev)
+        p = _solve_timed(sys_, params, krylov, dev, profile=True)
+        info = r["info"]
+        gbs = p["vc_bytes"] / (p["vc_ms"] * 1e-3) / 1e9 if p["vc_ms"] > 0 else None
+        d = {"config": name, "n": sys_.n, "nnz": sys_.nnz, "krylov": krylov,
+             "precision": {amg.AMG_FP64: "fp64", amg.AMG_FP32: "fp32 V-cycle / fp64 outer",
+                           amg.AMG_FP16_STORAGE: "fp16-storage V-cycle / fp64 outer"}[prec],
+             "status": amg.status_string(info.status),
+             "iterations": info.iterations, "rel_res_true": info.rel_res_true,
+             "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"],
+             "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None}
+        if x_ref is not None:
+            d["rel_diff_vs_fp64_solution"] = float(torch.linalg.vector_norm(r["x"] - x_ref) /
+                                                   torch.linalg.vector_norm(x_ref))
+        out.append(d)
+        return r["x"]
+
+    s3 = W.config_anisotropic3d_256()
+    x64 = line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP64, "pcg")
+    line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP32, "pcg", x64)
+    line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP16_STORAGE, "pcg", x64)
+    del s3, x64
+    for pe in (10.0, 100.0, 1000.0):
+        s4 = W.config_convdiff2d_2048(peclet=pe)
+        line(f"convdiff2d_2048 upwind Pe={pe:g}", s4, amg.AMG_FP32, "bicgstab")
+        del s4
+    line("poisson2d_64", W.config_poisson2d_64(), amg.AMG_FP64, "pcg")
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -361,6 +455,9 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     setup_ms, iters = [], []
+    # NVTX range "timed": lets a profiler capture exactly the timed launches
+    # (ncu --nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     last = ev0
     for _ in range(args.steps):
@@ -374,6 +471,7 @@ def main():
         h.close()
         last = ev_end
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
     launches = amg.amg_kernel_launches() - launches0
@@ -390,8 +488,10 @@ def main():
     peak, peak_kind = measured_peaks()
     table_acc = {}
     vc_bytes = vc_ms = 0.0
+    level_nnz = []
     for _ in range(args.profile_steps):
         h, info, _ = step(profile=True)
+        level_nnz = [amg.amg_level_info(h, k) for k in range(h.num_levels)]
         for r in amg.amg_profile_table(h):
             key = (r["kind"], r["level"])
             acc = table_acc.setdefault(key, dict(kind=r["kind"], level=r["level"], ms=0.0, bytes=0.0, launches=0))
@@ -408,13 +508,37 @@ def main():
             vc_ms += r["ms"]
     top = table[0] if table else None
     roofline = None
-    if top:
+    if top and top["kind"] == "coarse_cg" and level_nnz:
+        # The coarse CG keeps its rows in shared memory: per iteration it reads
+        # no matrix from HBM, and its bound is the FP64 pipe (and its two grid
+        # barriers).  FP64 flops per iteration: 2 nnz (SpMV) + 15 n (p, s, r,
+        # x updates, u = D^-1 r, three inner products); the iteration count
+        # comes from the profiler's byte total, which it charges per iteration.
+        n_l, nnz_l = level_nnz[top["level"]]
+        bytes_per_iter = nnz_l * 12 + 4 * (n_l + 1) + 80 * n_l
+        iters_per_launch = top["bytes"] / top["launches"] / bytes_per_iter
+        flops = (2.0 * nnz_l + 15.0 * n_l) * iters_per_launch
+        per_launch_ms = top["ms"] / top["launches"]
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top['kind']}@level{top['level']}",
+                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                    "flops_per_launch": flops, "iterations_per_launch": iters_per_launch,
+                    "ms_per_launch": per_launch_ms, "us_per_iteration": per_launch_ms * 1e3 / iters_per_launch}
+    elif top:
         per_launch_bytes = top["bytes"] / top["launches"]
         per_launch_ms = top["ms"] / top["launches"]
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": f"{top['kind']}@level{top['level']}", "achieved": achieved,
                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                     "peak_source": peak_kind, "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
+    # the level-0 kernels, which stream the 183 MB matrix from HBM
+    hbm_level0 = []
+    for r in table:
+        if r["level"] == 0 and r["kind"] in ("jacobi", "residual", "prolong_jacobi", "krylov_spmv") and r["ms"] > 0:
+            g = r["bytes"] / (r["ms"] * 1e-3) / 1e9
+            hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak})
     kernels = [dict(kernel=f"{r['kind']}@{r['level']}", ms_per_step=r["ms"] / args.profile_steps,
                     launches_per_step=r["launches"] / args.profile_steps,
                     gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:12]]
@@ -459,6 +583,10 @@ def main():
                           f"samples ({statistics.mean(ts):.3f} s each), extrapolated to {it_gpu} iterations"),
                "time_to_solution_s": t_solve}
 
+    configs = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        configs = run_configs(dev, peak)
+
     serving = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
         reqs, systems = generate_requests(args.serving_requests)
@@ -478,10 +606,10 @@ def main():
             "vcycle": {"gbs": vc_bytes / (vc_ms * 1e-3) / 1e9 if vc_ms > 0 else None,
                        "ms_per_step": vc_ms / max(1, args.profile_steps), "peak": peak,
                        "frac": (vc_bytes / (vc_ms * 1e-3) / 1e9) / peak if vc_ms > 0 else None},
-            "roofline": roofline, "kernels": kernels,
+            "roofline": roofline, "hbm_level0": hbm_level0, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
-            "serving": serving,
+            "configs_measured": configs, "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

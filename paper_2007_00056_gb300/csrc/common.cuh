@@ -95,8 +95,10 @@ struct CoarseCG {
   size_t smem = 0;           // dynamic shared memory per block (matrix slice staging)
   double *x = nullptr, *p = nullptr;
   double *r[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr};
-  double *part = nullptr;    // 2 slots x 3 values x AMG_MAX_BLOCKS
-  unsigned *bar = nullptr;   // [0] monotonic arrival counter
+  double *part = nullptr;    // CG_PART_DOUBLES: 2 slots x 3 values x AMG_MAX_BLOCKS, then 3 totals
+  int *ord = nullptr;        // n: rows of each block's range sorted by length (coarse_cg_prepare)
+  int *meta = nullptr;       // 5 x grid: row range and length-group bounds per block
+  unsigned *bar = nullptr;   // [0] monotonic arrival counter, [1] reduction release counter
   int *iters = nullptr;
   unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
 };
@@ -274,9 +276,11 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
 amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
 #define CG_THREADS 512
+#define CG_PART_DOUBLES (6 * AMG_MAX_BLOCKS + 32)
 #define CG_SMEM_CAP (200 * 1024)
 // Grid, block and shared-memory configuration of the coarse CG for n rows on
 // the current device (also sets the kernel's shared-memory limit).
 amg_status coarse_cg_config(int n, CoarseCG *cg);
+amg_status coarse_cg_prepare(int n, const int32_t *rp, const CoarseCG &cg, cudaStream_t s);
 amg_status coarse_cg_launch(int n, const int32_t *rp, const int32_t *ci, const double *val, const double *dinv,
                             const double *f, double *x, const CoarseCG &cg, unsigned *eflags, cudaStream_t s);

@@ -16,10 +16,10 @@
 // Largest system accepted: 262,144 rows and 2^31 - 1 stored entries.
 #define NOALLOC_MAX_N 262144
 #define NOALLOC_ALIGN 256
-#define NOALLOC_VECS 10  // dinv + the solver's work vectors, with room to spare
+#define NOALLOC_VECS 10  // dinv, the solver's eight work vectors and the row order
 #define NOALLOC_BYTES                                                                            \
-  ((size_t)NOALLOC_VECS * 8 * (NOALLOC_MAX_N + AMG_PAD) + (size_t)6 * AMG_MAX_BLOCKS * 8 + \
-   16 * NOALLOC_ALIGN)
+  ((size_t)NOALLOC_VECS * 8 * (NOALLOC_MAX_N + AMG_PAD) + (size_t)CG_PART_DOUBLES * 8 + \
+   (size_t)5 * AMG_MAX_BLOCKS * 4 + 16 * NOALLOC_ALIGN)
 
 // The scratch array: about 21 MB on every device that loads the library.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
@@ -98,7 +98,9 @@ extern "C" amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d
     cg.w[k] = (double *)take(vb);
     cg.s[k] = (double *)take(vb);
   }
-  cg.part = (double *)take(sizeof(double) * 6 * AMG_MAX_BLOCKS);
+  cg.part = (double *)take(sizeof(double) * CG_PART_DOUBLES);
+  cg.ord = (int *)take(sizeof(int) * ((size_t)n + AMG_PAD));
+  cg.meta = (int *)take(sizeof(int) * 5 * AMG_MAX_BLOCKS);
   cg.bar = (unsigned *)take(sizeof(unsigned) * 4);
   cg.iters = (int *)take(sizeof(int) * 4);
   cg.iters_total = (unsigned long long *)take(sizeof(unsigned long long));
@@ -116,6 +118,7 @@ extern "C" amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d
   AMG_CUDA(cudaStreamSynchronize(s));
   if (hflags[0] & AMG_EFLAG_BAD_CSR) return AMG_ERR_INVALID_CSR;
   if (hflags[0] & AMG_EFLAG_ZERO_DIAG) return AMG_ERR_ZERO_DIAG;
+  AMG_TRY(coarse_cg_prepare(n, d_row_ptr, cg, s));
   AMG_TRY(coarse_cg_launch(n, d_row_ptr, d_col, d_val, dinv, d_f, d_x, cg, flags, s));
   int it = 0;
   AMG_CUDA(cudaMemcpyAsync(hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));

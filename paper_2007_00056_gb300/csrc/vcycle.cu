@@ -413,14 +413,25 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
 // iteration come from one grid reduction: one persistent cooperative kernel
 // per solve, two bounded software grid barriers per iteration (after the new
 // preconditioned residual u = D^-1 r is published, and in the reduction).
-// Block b owns a contiguous row range: it stages its matrix slice and keeps
-// the state of its rows (r, s, p, x, w, u) in shared memory, so the only
-// global traffic of an iteration is u: written by owners, gathered once per
-// nonzero by the SpMV.
+//
+// Block b owns the rows of a contiguous range holding about nnz/G entries.
+// Setup sorts each block's rows by length once (stable, so the order is
+// fixed); the kernel keeps the state of its rows (r, s, p, x, w, u, 1/a_ii)
+// in shared memory, in that order, and stages its matrix slice as SELL-32
+// (slices of 32 lanes, entry q of a lane at slice offset + 32 q; Kreutzer et
+// al., SIAM J. Sci. Comput. 36(5), 2014): rows up to 16 entries take one
+// lane, up to 64 entries four lanes, up to 256 sixteen lanes; longer rows
+// take a warp and are read from global memory.  A lane gathers all of its
+// (at most 16) neighbours in one round, and a warp runs exactly as many FMAs
+// as its longest lane needs: FP64 instructions cost the full pipe time even
+// for inactive lanes, so the FMA count is chosen by a warp-uniform branch
+// rather than by predication.  The only global traffic of an iteration is u:
+// written by owners, gathered once per nonzero.
 // ---------------------------------------------------------------------------
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
-#define CG_CHUNK 4  // neighbours whose gathers are in flight together
+#define CG_KEYS 258     // sort keys: row length 0..256, 257 for longer rows
+#define CG_MAXQ 16      // neighbours a lane gathers in one round
 #define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -428,23 +439,31 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 // Monotonic-counter grid barrier: the k-th barrier completes when the counter
 // reaches k * G.  Waits are bounded; a block that gives up sets the timeout
-// flag and the caller leaves its loop.
+// flag and the caller leaves its loop.  arrive() and wait() may be split so
+// that a block does independent work while the others arrive.
 struct GridBarrier {
   unsigned *count;
   unsigned target;
   long long limit = BARRIER_SPIN_LIMIT;
-  __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
+  bool was_last = false;  // thread 0: this block's arrival completed the barrier
+  __device__ __forceinline__ void arrive(unsigned G) {
     __syncthreads();
     target += G;
     if (threadIdx.x == 0) {
       __threadfence();
-      atomicAdd(count, 1u);
+      was_last = atomicAdd(count, 1u) == target - 1;
+    }
+  }
+  __device__ __forceinline__ bool wait(unsigned *eflags, int *fail_sh) {
+    if (threadIdx.x == 0) {
       long long t0 = clock64();
       while (ld_acquire_u32(count) < target) {
-        __nanosleep(20);
         if (clock64() - t0 > limit) {
           atomicOr(eflags, AMG_EFLAG_TIMEOUT);
           *fail_sh = 1;
@@ -455,8 +474,132 @@ struct GridBarrier {
     __syncthreads();
     return *fail_sh == 0;
   }
+  __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
+    arrive(G);
+    return wait(eflags, fail_sh);
+  }
 };
 
+__device__ __forceinline__ int cg_key(int len) { return len < CG_KEYS - 1 ? len : CG_KEYS - 1; }
+
+// FP64 work of a row per CG iteration, in multiply-adds: its entries plus
+// about eight vector operations (updates, the three inner products).
+#define CG_ROW_COST 8
+
+// Smallest row r whose work prefix rp[r] + CG_ROW_COST r reaches target.
+__device__ __forceinline__ int cg_first_row_with(const int32_t *rp, int n, long long target) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if ((long long)rp[mid] + (long long)CG_ROW_COST * mid >= target) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+// One warp per block of the coarse CG grid: the block's row range (about
+// 1/G of the FP64 work) and its rows sorted by length, stable.  meta[5 b ..] =
+// first row, end of the 1-lane rows (<= 16 entries), end of the 4-lane rows
+// (<= 64), end of the 16-lane rows (<= 256), end of the range.
+__global__ void k_cg_prepare(int n, const int32_t *__restrict__ rp, int *__restrict__ ord, int *__restrict__ meta) {
+  __shared__ int cnt[CG_KEYS];
+  const int lane = threadIdx.x, b = blockIdx.x, G = gridDim.x;
+  const long long work = (long long)rp[n] + (long long)CG_ROW_COST * n;
+  const int r0 = b == 0 ? 0 : cg_first_row_with(rp, n, work * b / G);
+  const int r1 = b + 1 == G ? n : cg_first_row_with(rp, n, work * (b + 1) / G);
+  for (int k = lane; k < CG_KEYS; k += 32) cnt[k] = 0;
+  __syncwarp();
+  for (int i = r0 + lane; i < r1; i += 32) atomicAdd(&cnt[cg_key(rp[i + 1] - rp[i])], 1);
+  __syncwarp();
+  if (lane == 0) {
+    int s = 0, e1 = 0, e2 = 0, e3 = 0;
+    for (int k = 0; k < CG_KEYS; ++k) {
+      const int c = cnt[k];
+      cnt[k] = s;
+      s += c;
+      if (k == 16) e1 = s;
+      if (k == 64) e2 = s;
+      if (k == 256) e3 = s;
+    }
+    meta[5 * b + 0] = r0;
+    meta[5 * b + 1] = r0 + e1;
+    meta[5 * b + 2] = r0 + e2;
+    meta[5 * b + 3] = r0 + e3;
+    meta[5 * b + 4] = r1;
+  }
+  __syncwarp();
+  // stable scatter: rows in index order, equal keys ranked by lane
+  for (int base = r0; base < r1; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < r1;
+    const int key = valid ? cg_key(rp[i + 1] - rp[i]) : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(same & ((1u << lane) - 1u));
+    if (valid) ord[r0 + cnt[key] + rank] = i;
+    __syncwarp();
+    if (valid && rank == 0) cnt[key] += __popc(same);
+    __syncwarp();
+  }
+}
+
+// Partial row sum of one lane: entries q = 0..N-1 at cols[q * stride], of
+// which the first `cnt` exist; w continues the lane's FMA chain.  From four
+// entries on, even and odd entries form two chains (halving the dependent
+// FP64 latency) that meet at the end.
+template <int N>
+__device__ __forceinline__ double cg_lane_dot(const int *cols, const double *vals, int stride, int cnt,
+                                              const double *u, double w) {
+  double vv[N], uu[N];
+#pragma unroll
+  for (int q = 0; q < N; ++q) {
+    const bool in = q < cnt;
+    const int c = in ? cols[q * stride] : 0;
+    vv[q] = in ? vals[q * stride] : 0.0;
+    uu[q] = in ? __ldcg(&u[c]) : 0.0;
+  }
+  if (N < 4) {
+#pragma unroll
+    for (int q = 0; q < N; ++q) w = __fma_rn(vv[q], uu[q], w);
+    return w;
+  }
+  double w1 = 0.0;
+#pragma unroll
+  for (int q = 0; q < N; q += 2) {
+    w = __fma_rn(vv[q], uu[q], w);
+    if (q + 1 < N) w1 = __fma_rn(vv[q + 1], uu[q + 1], w1);
+  }
+  return __dadd_rn(w, w1);
+}
+
+// Dispatch on the warp's largest lane count (warp-uniform): exactly that many
+// FMAs per lane, or rounds of CG_MAXQ for longer rows.
+__device__ __forceinline__ double cg_row_part(const int *cols, const double *vals, int stride, int cnt, int wmax,
+                                              const double *u) {
+  switch (wmax) {
+    case 0: return 0.0;
+    case 1: return cg_lane_dot<1>(cols, vals, stride, cnt, u, 0.0);
+    case 2: return cg_lane_dot<2>(cols, vals, stride, cnt, u, 0.0);
+    case 3: return cg_lane_dot<3>(cols, vals, stride, cnt, u, 0.0);
+    case 4: return cg_lane_dot<4>(cols, vals, stride, cnt, u, 0.0);
+    case 5: return cg_lane_dot<5>(cols, vals, stride, cnt, u, 0.0);
+    case 6: return cg_lane_dot<6>(cols, vals, stride, cnt, u, 0.0);
+    case 7: return cg_lane_dot<7>(cols, vals, stride, cnt, u, 0.0);
+    case 8: return cg_lane_dot<8>(cols, vals, stride, cnt, u, 0.0);
+    case 9: return cg_lane_dot<9>(cols, vals, stride, cnt, u, 0.0);
+    case 10: return cg_lane_dot<10>(cols, vals, stride, cnt, u, 0.0);
+    case 11: return cg_lane_dot<11>(cols, vals, stride, cnt, u, 0.0);
+    case 12: return cg_lane_dot<12>(cols, vals, stride, cnt, u, 0.0);
+    case 13: return cg_lane_dot<13>(cols, vals, stride, cnt, u, 0.0);
+    case 14: return cg_lane_dot<14>(cols, vals, stride, cnt, u, 0.0);
+    case 15: return cg_lane_dot<15>(cols, vals, stride, cnt, u, 0.0);
+    case 16: return cg_lane_dot<16>(cols, vals, stride, cnt, u, 0.0);
+    default: {
+      double w = 0.0;
+      for (int q0 = 0; q0 < wmax; q0 += CG_MAXQ)
+        w = cg_lane_dot<CG_MAXQ>(cols + (size_t)q0 * stride, vals + (size_t)q0 * stride, stride, cnt - q0, u, w);
+      return w;
+    }
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(CG_THREADS, 1)
@@ -465,166 +608,300 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
                 const KState *st, unsigned *eflags) {
   if (is_done(st)) return;
   extern __shared__ __align__(16) unsigned char cg_smem[];
-  __shared__ double red_sh[3 * 32];
-  __shared__ int fail_sh;
-  __shared__ int ord_sh[32];
-  __shared__ int cls_start[ROW_CLASSES + 1];
+  __shared__ double red_w[3][CG_THREADS];  // block reduction, one row per inner product
+  __shared__ double tot_sh[3];
+  __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
+  __shared__ int fail_sh, last_sh;
+  __shared__ int gs[5], nslice_sh[4], wl_sh[CG_THREADS / 32 + 1];
+  __shared__ long long sell_total_sh;
   const unsigned G = gridDim.x;
-  // rows split so that every block holds about the same number of nonzeros
-  auto first_row_with = [&](long long target) {  // smallest r with rp[r] >= target
-    int lo = 0, hi = n;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if ((long long)rp[mid] >= target) hi = mid; else lo = mid + 1;
-    }
-    return lo;
-  };
-  const long long nnz_all = rp[n];
-  const int r0 = blockIdx.x == 0 ? 0 : first_row_with(nnz_all * blockIdx.x / G);
-  const int r1 = blockIdx.x + 1 == G ? n : first_row_with(nnz_all * (blockIdx.x + 1) / G);
-  const int nr = r1 - r0;
-  const int e0 = rp[r0], e1 = rp[r1], ne = e1 - e0;
+  const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int *meta = cg.meta + 5 * blockIdx.x;
+  const int P0 = meta[0], nr = meta[4] - P0;
+  // group g (0..3) holds positions [gs[g], gs[g+1]) with lanes_of(g) lanes per row
+  if (threadIdx.x < 5) gs[threadIdx.x] = threadIdx.x == 0 ? 0 : meta[threadIdx.x] - P0;
+  __syncthreads();
+  auto lanes_of = [](int g) { return g == 3 ? 32 : 1 << (2 * g); };
+  auto log_lanes = [](int g) { return g == 3 ? 5 : 2 * g; };
   // dynamic shared memory, in order of priority:
-  //   [row order: nr ints][row state r,s,p,x,w,u: 6 nr doubles][row pointers: nr+1][cols: ne][values: ne]
-  const size_t ord_bytes = (size_t)nr * 4;
-  const size_t st_off = (ord_bytes + 7) / 8 * 8;
-  const size_t rp_off = st_off + (size_t)nr * 48;
-  const size_t ci_off = rp_off + (size_t)(nr + 1) * 4;
-  const size_t val_off = (ci_off + (size_t)ne * 4 + 7) / 8 * 8;
-  const bool ordered = ord_bytes <= cg.smem;
-  const bool local_state = rp_off <= cg.smem;
-  const bool staged = val_off + (size_t)ne * 8 <= cg.smem;
-  int *s_ord = (int *)cg_smem;
+  //   [row ids: nr][row lengths: nr][state r,s,p,x,w,u,d: 7 nr doubles]
+  //   [slice offsets: ns + 1][warp of each slice: ns][slices by warp: ns]
+  //   [SELL columns][SELL values]
+  const size_t ids_bytes = (size_t)nr * 8;
+  const size_t st_off = (ids_bytes + 15) / 16 * 16;
+  const size_t sl_off = st_off + (size_t)nr * 56;
+  int ns_abc = 0;
+  for (int g = 0; g < 3; ++g) ns_abc += (gs[g + 1] - gs[g] + (32 / lanes_of(g)) - 1) / (32 / lanes_of(g));
+  const size_t sell_off = (sl_off + (size_t)(3 * ns_abc + 1) * 4 + 15) / 16 * 16;
+  const bool local_ids = ids_bytes <= cg.smem;
+  const bool local_state = sl_off <= cg.smem;
+  int *s_row = (int *)cg_smem;
+  int *s_len = s_row + nr;
   double *s_st = (double *)(cg_smem + st_off);
-  int *s_rp = (int *)(cg_smem + rp_off);
-  int *s_ci = (int *)(cg_smem + ci_off);
-  double *s_val = (double *)(cg_smem + val_off);
+  int *s_slice = (int *)(cg_smem + sl_off);
+  int *s_wsl = s_slice + ns_abc + 1;
+  int *s_list = s_wsl + ns_abc;  // slice indices grouped by warp: [wl_sh[w], wl_sh[w + 1])
   if (threadIdx.x == 0) fail_sh = 0;
+  if (local_ids) {
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const int i = cg.ord[P0 + t];
+      s_row[t] = i;
+      s_len[t] = rp[i + 1] - rp[i];
+    }
+  }
+  __syncthreads();
+  auto row_at = [&](int pos) { return local_ids ? s_row[pos] : cg.ord[P0 + pos]; };
+  auto len_at = [&](int pos) {
+    if (local_ids) return s_len[pos];
+    const int i = cg.ord[P0 + pos];
+    return (int)(rp[i + 1] - rp[i]);
+  };
+  // SELL slice offsets and the warp of each slice (thread 0; slices are few).
+  // A slice costs about width + log2(lanes per row) + 3 FP64 instructions
+  // (the inner products); the slices go, widest first, to the least loaded
+  // warp, and each warp's slices are listed in index order.
+  if (threadIdx.x == 0) {
+    long long off = 0;
+    int j = 0;
+    const bool room = sl_off + (size_t)(3 * ns_abc + 1) * 4 <= cg.smem;
+    for (int g = 0; g < 3; ++g) {
+      const int rs = 32 / lanes_of(g);
+      nslice_sh[g] = j;
+      for (int a = gs[g]; a < gs[g + 1]; a += rs, ++j) {
+        const int last = min(a + rs, gs[g + 1]) - 1;  // rows ascend by length within a group
+        const int width = (len_at(last) + lanes_of(g) - 1) / lanes_of(g);
+        if (room) s_slice[j] = (int)off;
+        off += 32ll * width;
+      }
+    }
+    nslice_sh[3] = j;
+    if (room) {
+      s_slice[j] = (int)off;
+      int load[CG_THREADS / 32];
+      for (int w = 0; w < nwarps; ++w) load[w] = 0;
+      for (int g = 2; g >= 0; --g)
+        for (int jj = nslice_sh[g + 1] - 1; jj >= nslice_sh[g]; --jj) {
+          int best = 0;
+          for (int w = 1; w < nwarps; ++w)
+            if (load[w] < load[best]) best = w;
+          load[best] += ((s_slice[jj + 1] - s_slice[jj]) >> 5) + log_lanes(g) + 3;
+          s_wsl[jj] = best;
+        }
+      // counts, then list starts, then the lists (load[] reused as cursors)
+      for (int w = 0; w < nwarps; ++w) load[w] = 0;
+      for (int jj = 0; jj < j; ++jj) ++load[s_wsl[jj]];
+      int acc = 0;
+      for (int w = 0; w < nwarps; ++w) {
+        wl_sh[w] = acc;
+        acc += load[w];
+        load[w] = wl_sh[w];
+      }
+      wl_sh[nwarps] = acc;
+      for (int jj = 0; jj < j; ++jj) s_list[load[s_wsl[jj]]++] = jj;
+    }
+    sell_total_sh = room ? off : -1;
+  }
+  __syncthreads();
+  const long long sell_n = sell_total_sh;
+  const size_t sell_val_off = sell_off + ((size_t)(sell_n > 0 ? sell_n : 0) * 4 + 15) / 16 * 16;
+  const bool staged = local_state && sell_n >= 0 && sell_val_off + (size_t)sell_n * 8 <= cg.smem;
+  int *sell_ci = (int *)(cg_smem + sell_off);
+  double *sell_val = (double *)(cg_smem + sell_val_off);
+  auto group_of = [&](int j) { return j < nslice_sh[1] ? 0 : j < nslice_sh[2] ? 1 : 2; };
   if (staged) {
-    for (int k = threadIdx.x; k < ne; k += blockDim.x) { s_val[k] = val[e0 + k]; s_ci[k] = ci[e0 + k]; }
-    for (int k = threadIdx.x; k <= nr; k += blockDim.x) s_rp[k] = rp[r0 + k] - e0;
+    // warp per slice: entry q of lane l is entry sub + LN q of the lane's row
+    for (int j = warp; j < nslice_sh[3]; j += nwarps) {
+      const int g = group_of(j), ln = lanes_of(g), rs = 32 / ln;
+      const int pos = gs[g] + (j - nslice_sh[g]) * rs + lane / ln, sub = lane % ln;
+      const bool valid = pos < gs[g + 1];
+      const int i = valid ? row_at(pos) : 0;
+      const int L = valid ? len_at(pos) : 0;
+      const int b = valid ? rp[i] : 0;
+      const int width = (s_slice[j + 1] - s_slice[j]) >> 5;
+      for (int q = 0; q < width; ++q) {
+        const int e = sub + ln * q;
+        if (e < L) {
+          sell_ci[s_slice[j] + 32 * q + lane] = ci[b + e];
+          sell_val[s_slice[j] + 32 * q + lane] = val[b + e];
+        }
+      }
+    }
   }
   __syncthreads();
-  if (ordered) {
-    block_class_order(nr, s_ord, ord_sh, [&](int k) { return rp[r0 + k + 1] - rp[r0 + k]; }, cls_start);
-  } else if (threadIdx.x == 0) {
-    for (int c = 0; c <= ROW_CLASSES; ++c) cls_start[c] = 0;  // unordered: every row takes one lane
-  }
-  __syncthreads();
-  // local row k of this block: state in shared memory, or in the global work arrays
-  double *vr = local_state ? s_st : cg.r[1] + r0;
-  double *vs = local_state ? s_st + nr : cg.s[0] + r0;
-  double *vp = local_state ? s_st + 2 * nr : cg.p + r0;
-  double *vx = local_state ? s_st + 3 * nr : cg.x + r0;
-  double *vw = local_state ? s_st + 4 * nr : cg.w[0] + r0;
-  double *vu = local_state ? s_st + 5 * nr : cg.s[1] + r0;
+  // row state by position: in shared memory, or in the global work arrays
+  double *vr = local_state ? s_st : cg.r[1] + P0;
+  double *vs = local_state ? s_st + nr : cg.s[0] + P0;
+  double *vp = local_state ? s_st + 2 * nr : cg.p + P0;
+  double *vx = local_state ? s_st + 3 * nr : cg.x + P0;
+  double *vw = local_state ? s_st + 4 * nr : cg.w[0] + P0;
+  double *vu = local_state ? s_st + 5 * nr : cg.s[1] + P0;
+  double *vd = local_state ? s_st + 6 * nr : cg.w[1] + P0;
   double *u = cg.r[0];  // published preconditioned residual, read by every block's SpMV
-  const double *lval = staged ? s_val : val + e0;
-  const int *lci = staged ? s_ci : ci + e0;
-  auto row_begin = [&](int i) { return staged ? s_rp[i - r0] : __ldg(&rp[i]) - e0; };
-  // thread t handles the block's local rows at order positions t, t + blockDim, ...
-  auto local_at = [&](int t) { return ordered ? s_ord[t] : t; };
   GridBarrier gb{cg.bar, 0u};
   int slot = 0;
-  // block partial sums -> barrier -> warp 0 sums the G partials in index order;
-  // the totals are valid in warp 0 (thread 0 evaluates the scalars)
+  // Inner products: block partials -> the last block to arrive sums them ->
+  // totals for all.  Every FP64 warp instruction costs the same whatever the
+  // number of active lanes, so the block step halves the values in shared
+  // memory with whole warps and the last 32 values of each product go to
+  // their own warp.  The G partials are then read and summed by the last
+  // block alone (warps 0-2 one product each: loads in flight together, then
+  // in index order per lane and a fixed shuffle tree), which publishes the
+  // totals and releases the others through a second counter: when every
+  // block read all partials, the same few cache lines were requested by all
+  // SMs at once.  Totals land in tot_sh.
+  double *tot_g = cg.part + 6 * AMG_MAX_BLOCKS;
+  unsigned seq = 0;  // reductions done (thread 0)
   auto reduce3 = [&](double (&v)[3]) -> bool {
-    block_sum<3>(v, red_sh);
-    double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
-    if (threadIdx.x == 0) {
-      part[blockIdx.x] = v[0];
-      part[AMG_MAX_BLOCKS + blockIdx.x] = v[1];
-      part[2 * AMG_MAX_BLOCKS + blockIdx.x] = v[2];
-    }
-    bool ok = gb.sync(G, eflags, &fail_sh);
-    if (threadIdx.x < 32) {
-      double a = 0.0, b = 0.0, c = 0.0;
-      for (unsigned k = threadIdx.x; k < G; k += 32) {
-        a += __ldcg(&part[k]);
-        b += __ldcg(&part[AMG_MAX_BLOCKS + k]);
-        c += __ldcg(&part[2 * AMG_MAX_BLOCKS + k]);
+    const int t = threadIdx.x;
+    red_w[0][t] = v[0];
+    red_w[1][t] = v[1];
+    red_w[2][t] = v[2];
+    __syncthreads();
+    for (int h = blockDim.x >> 1; h >= 32; h >>= 1) {
+      if (t < h) {
+        red_w[0][t] += red_w[0][t + h];
+        red_w[1][t] += red_w[1][t + h];
+        red_w[2][t] += red_w[2][t + h];
       }
-      v[0] = warp_sum(a);
-      v[1] = warp_sum(b);
-      v[2] = warp_sum(c);
+      __syncthreads();
     }
+    double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
+    if (warp < 3) {
+      const double bsum = warp_sum(red_w[warp][lane]);
+      if (lane == 0) part[warp * AMG_MAX_BLOCKS + blockIdx.x] = bsum;
+    }
+    gb.arrive(G);
+    if (t == 0) {
+      ++seq;
+      last_sh = gb.was_last;
+      if (gb.was_last) __threadfence();  // acquire: every block's partial is visible
+    }
+    __syncthreads();
+    bool ok = true;
+    if (last_sh) {
+      if (warp < 3) {
+        constexpr int PQ = 8;  // up to 256 partials per round of loads
+        const double *pk = part + warp * AMG_MAX_BLOCKS;
+        double a = 0.0;
+        for (unsigned k0 = 0; k0 < G; k0 += 32 * PQ) {
+          double pa[PQ];
+#pragma unroll
+          for (int q = 0; q < PQ; ++q) {
+            const unsigned k = k0 + lane + 32 * q;
+            pa[q] = k < G ? __ldcg(&pk[k]) : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < PQ; ++q)
+            if (k0 + lane + 32 * q < G) a += pa[q];
+        }
+        a = warp_sum(a);
+        if (lane == 0) {
+          tot_sh[warp] = a;
+          tot_g[warp] = a;
+        }
+      }
+      __syncthreads();
+      if (t == 0) {
+        __threadfence();
+        st_release_u32(cg.bar + 1, seq);
+      }
+    } else {
+      if (t == 0) {
+        long long t0 = clock64();
+        while (ld_acquire_u32(cg.bar + 1) < seq) {
+          if (clock64() - t0 > gb.limit) {
+            atomicOr(eflags, AMG_EFLAG_TIMEOUT);
+            fail_sh = 1;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      ok = fail_sh == 0;
+      if (t < 3) tot_sh[t] = __ldcg(&tot_g[t]);
+    }
+    __syncthreads();
     slot ^= 1;
     return ok;
   };
-  // w = A u for the block's rows and the three inner products (r,u), (w,u),
-  // (r,r).  Rows up to 16 entries take one lane each, 17-48 entries four
-  // lanes, longer rows a whole warp, so no lane walks a long chain of
-  // dependent gathers; a group's partial sums meet in a fixed shuffle tree.
-  auto spmv_group = [&](int pa, int pb, auto lanes_tag, double (&acc)[3]) {
-    constexpr int LN = decltype(lanes_tag)::value;
-    const int slots = (pb - pa) * LN;
-    const int warp_base = (threadIdx.x & ~31);
-    for (int s0 = 0; s0 + warp_base < slots; s0 += blockDim.x) {
-      const int slot = s0 + threadIdx.x;
-      const bool valid = slot < slots;
-      const int sub = slot % LN;
-      const int pos = pa + slot / LN;
-      const int k = valid ? local_at(pos) : 0;
-      const int i = r0 + k;
-      double wi = 0.0;
-      if (valid) {
-        const int b = row_begin(i), e = row_begin(i + 1);
-        for (int k0 = b + sub * CG_CHUNK; k0 < e; k0 += LN * CG_CHUNK) {
-          double uu[CG_CHUNK], vv[CG_CHUNK];
-#pragma unroll
-          for (int q = 0; q < CG_CHUNK; ++q) {
-            const bool in = k0 + q < e;
-            vv[q] = in ? lval[k0 + q] : 0.0;
-            uu[q] = __ldcg(&u[in ? lci[k0 + q] : i]);
-          }
-#pragma unroll
-          for (int q = 0; q < CG_CHUNK; ++q)
-            if (k0 + q < e) wi += vv[q] * uu[q];
-        }
+  // w = A u for the block's rows, each warp taking its slices, and the three
+  // inner products (r,u), (w,u), (r,r) accumulated by the lane that finishes
+  // each row
+  auto spmv_dots = [&](double (&acc)[3]) {
+    auto slice = [&](int g, int js) {
+      const int ln = lanes_of(g), rs = 32 / ln;
+      const int pos = gs[g] + js * rs + lane / ln, sub = lane % ln;
+      const bool valid = pos < gs[g + 1];
+      const int i = valid ? row_at(pos) : 0;
+      const int L = valid ? len_at(pos) : 0;
+      const int cnt = L > sub ? (L - sub + ln - 1) / ln : 0;
+      const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+      const int *cols;
+      const double *vals;
+      int stride;
+      if (staged && g < 3) {
+        const int o = s_slice[nslice_sh[g] + js] + lane;
+        cols = sell_ci + o;
+        vals = sell_val + o;
+        stride = 32;
+      } else {
+        const int b = valid ? rp[i] : 0;
+        cols = ci + b + sub;
+        vals = val + b + sub;
+        stride = ln;
       }
-      if (LN > 1) {
-#pragma unroll
-        for (int o = LN / 2; o > 0; o >>= 1) wi += __shfl_xor_sync(0xffffffffu, wi, o);
-      }
+      double wi = cg_row_part(cols, vals, stride, cnt, wmax, u);
+      for (int o = ln >> 1; o > 0; o >>= 1) wi += __shfl_xor_sync(0xffffffffu, wi, o);
       if (valid && sub == 0) {
-        vw[k] = wi;
-        const double ri = vr[k], ui = vu[k];
-        acc[0] += ri * ui;
-        acc[1] += wi * ui;
-        acc[2] += ri * ri;
+        vw[pos] = wi;
+        const double ri = vr[pos], ui = vu[pos];
+        acc[0] = __fma_rn(ri, ui, acc[0]);
+        acc[1] = __fma_rn(wi, ui, acc[1]);
+        acc[2] = __fma_rn(ri, ri, acc[2]);
+      }
+    };
+    if (staged) {
+      for (int k = wl_sh[warp]; k < wl_sh[warp + 1]; ++k) {
+        const int j = s_list[k], g = group_of(j);
+        slice(g, j - nslice_sh[g]);
+      }
+    } else {
+      for (int g = 0; g < 3; ++g) {
+        const int nsl = nslice_sh[g + 1] - nslice_sh[g];
+        for (int js = warp; js < nsl; js += nwarps) slice(g, js);
       }
     }
-  };
-  auto spmv_dots = [&](double (&acc)[3]) {
-    const int p1 = ordered ? cls_start[5] : nr;  // classes 0-4: up to 16 entries
-    const int p2 = ordered ? cls_start[8] : nr;  // classes 5-7: up to 48 entries
-    spmv_group(0, p1, std::integral_constant<int, 1>{}, acc);
-    spmv_group(p1, p2, std::integral_constant<int, 4>{}, acc);
-    spmv_group(p2, nr, std::integral_constant<int, 32>{}, acc);
+    for (int js = warp; js < gs[4] - gs[3]; js += nwarps) slice(3, js);  // rows over 256 entries
   };
 
-  __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
   // initial phase: r0 = f, u0 = D^-1 f (published), s = p = x = 0; then w0 = A u0
   for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    const int k = local_at(t), i = r0 + k;
+    const int i = row_at(t);
     const double fi = (double)f[i];
-    const double ui = __dmul_rn(fi, __ldg(&dinv[i]));
-    vr[k] = fi;
-    vu[k] = ui;
+    const double di = __ldg(&dinv[i]);
+    const double ui = __dmul_rn(fi, di);
+    vr[t] = fi;
+    vu[t] = ui;
+    vd[t] = di;
     u[i] = ui;
-    vs[k] = 0.0;
-    vp[k] = 0.0;
-    vx[k] = 0.0;
+    vs[t] = 0.0;
+    vp[t] = 0.0;
+    vx[t] = 0.0;
   }
   bool ok = gb.sync(G, eflags, &fail_sh);
   double v[3] = {0.0, 0.0, 0.0};
   if (ok) spmv_dots(v);
   ok = reduce3(v) && ok;
-  double fnorm = 0.0, gamma = 0.0, alpha_t = 0.0, beta_t = 0.0;
+  // scalars, kept by thread 0: the stop threshold on (r,r), gamma = (r,u),
+  // alpha, and the reciprocals 1/gamma and 1/(gamma alpha) of the previous
+  // iteration, computed while the next iteration's vectors are updated so
+  // that only one division stays between a reduction and the next update
+  double thresh = 0.0, gamma = 0.0, alpha_t = 0.0, beta_t = 0.0, inv_g = 0.0, inv_ga = 0.0;
   if (threadIdx.x == 0) {
-    fnorm = sqrt(v[2]);
-    gamma = v[0];
-    alpha_t = v[0] / v[1];
+    const double fnorm = sqrt(tot_sh[2]);
+    thresh = (CG_RTOL * fnorm) * (CG_RTOL * fnorm);
+    gamma = tot_sh[0];
+    alpha_t = tot_sh[0] / tot_sh[1];
     sc[0] = alpha_t;
     sc[1] = 0.0;
     sc[2] = (fnorm > 0.0 && ok && fail_sh == 0) ? 0.0 : 1.0;
@@ -634,31 +911,37 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   if (sc[2] == 0.0) {
     for (it = 1; it <= CG_MAXIT; ++it) {
       const double alpha = sc[0], beta = sc[1];
-      // phase A (own rows): p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r
-      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        const int k = local_at(t), i = r0 + k;
-        const double pi = __fma_rn(beta, vp[k], vu[k]);
-        const double si = __fma_rn(beta, vs[k], vw[k]);
-        vx[k] = __fma_rn(alpha, pi, vx[k]);
-        const double ri = __fma_rn(-alpha, si, vr[k]);
-        const double ui = __dmul_rn(ri, __ldg(&dinv[i]));
-        vp[k] = pi;
-        vs[k] = si;
-        vr[k] = ri;
-        vu[k] = ui;
-        u[i] = ui;
+      if (threadIdx.x == 0) {
+        inv_g = 1.0 / gamma;
+        inv_ga = 1.0 / (gamma * alpha_t);
       }
-      ok = gb.sync(G, eflags, &fail_sh);
+      // phase A (own rows): p = u + beta p, s = w + beta s, r -= alpha s, u = D^-1 r
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+        const double pi = __fma_rn(beta, vp[t], vu[t]);
+        const double si = __fma_rn(beta, vs[t], vw[t]);
+        const double ri = __fma_rn(-alpha, si, vr[t]);
+        const double ui = __dmul_rn(ri, vd[t]);
+        vp[t] = pi;
+        vs[t] = si;
+        vr[t] = ri;
+        vu[t] = ui;
+        u[row_at(t)] = ui;
+      }
+      gb.arrive(G);
+      // x += alpha p while the other blocks arrive (same thread, same rows)
+      for (int t = threadIdx.x; t < nr; t += blockDim.x) vx[t] = __fma_rn(alpha, vp[t], vx[t]);
+      ok = gb.wait(eflags, &fail_sh);
       // phase B: w = A u and the three inner products, one reduction
       double acc[3] = {0.0, 0.0, 0.0};
       if (ok) spmv_dots(acc);
       ok = reduce3(acc) && ok;
       if (threadIdx.x == 0) {
-        bool stop = !ok || fail_sh != 0 || sqrt(acc[2]) <= CG_RTOL * fnorm;
+        const double gamma_new = tot_sh[0];
+        bool stop = !ok || fail_sh != 0 || tot_sh[2] <= thresh;
         if (!stop) {
-          const double gamma_new = acc[0];
-          beta_t = gamma_new / gamma;
-          alpha_t = gamma_new / (acc[1] - beta_t * gamma_new / alpha_t);
+          // beta = gamma'/gamma, alpha = gamma'/(delta' - beta gamma'/alpha)
+          beta_t = gamma_new * inv_g;
+          alpha_t = gamma_new / (tot_sh[1] - gamma_new * gamma_new * inv_ga);
           gamma = gamma_new;
           stop = !isfinite(alpha_t);
         }
@@ -671,10 +954,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     }
     if (it > CG_MAXIT) it = CG_MAXIT;
   }
-  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-    const int k = local_at(t);
-    xout[r0 + k] = (T)vx[k];
-  }
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) xout[row_at(t)] = (T)vx[t];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     *cg.iters = it;
     atomicAdd(cg.iters_total, (unsigned long long)it);
@@ -947,12 +1227,15 @@ amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
     AMG_TRY(hier_alloc(h, (void **)&cg.w[b], vb));
     AMG_TRY(hier_alloc(h, (void **)&cg.s[b], vb));
   }
-  AMG_TRY(hier_alloc(h, (void **)&cg.part, sizeof(double) * 6 * AMG_MAX_BLOCKS));
+  AMG_TRY(hier_alloc(h, (void **)&cg.part, sizeof(double) * CG_PART_DOUBLES));
+  AMG_TRY(hier_alloc(h, (void **)&cg.ord, sizeof(int) * (c.n + AMG_PAD)));
+  AMG_TRY(hier_alloc(h, (void **)&cg.meta, sizeof(int) * 5 * AMG_MAX_BLOCKS));
   AMG_TRY(hier_alloc(h, (void **)&cg.bar, sizeof(unsigned) * 4));
   AMG_TRY(hier_alloc(h, (void **)&cg.iters, sizeof(int) * 4));
   AMG_TRY(hier_alloc(h, (void **)&cg.iters_total, sizeof(unsigned long long)));
   AMG_CUDA(cudaMemsetAsync(cg.iters_total, 0, sizeof(unsigned long long), s));
   AMG_TRY(coarse_cg_config(c.n, &cg));
+  AMG_TRY(coarse_cg_prepare(c.n, c.rp, cg, s));
   return AMG_OK;
 }
 
@@ -1251,6 +1534,15 @@ amg_status coarse_cg_config(int n, CoarseCG *cg) {
   cg->grid = std::max(1, std::min(std::min(occ * sms, cdiv(n, 64)), AMG_MAX_BLOCKS));
   cg->threads = CG_THREADS;
   cg->smem = CG_SMEM_CAP;
+  return AMG_OK;
+}
+
+// Row ranges and length order of the coarse CG blocks (cg.grid must be final).
+amg_status coarse_cg_prepare(int n, const int32_t *rp, const CoarseCG &cg, cudaStream_t s) {
+  if (cg.grid < 1 || cg.grid > AMG_MAX_BLOCKS || !cg.ord || !cg.meta) return AMG_ERR_INVALID_ARG;
+  k_cg_prepare<<<cg.grid, 32, 0, s>>>(n, rp, cg.ord, cg.meta);
+  count_launch();
+  AMG_CUDA(cudaGetLastError());
   return AMG_OK;
 }
 
