@@ -33,6 +33,10 @@ WORKLOAD = "lognormal3d_128: 3D 7-pt FV diffusion, 128^3 cells, lognormal(0,1) c
 RTOL = 1e-8
 # FP64 peak of GB300: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) per launch of the coarse CG kernel on this
+# workload, from one ncu capture of the current kernel
+# (profiles/coarse_cg_lognormal3d_128.md); None once the kernel changes
+COARSE_CG_DRAM_BYTES = 10583296 + 91136
 
 
 def parse_args():
@@ -522,7 +526,8 @@ def main():
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top['kind']}@level{top['level']}",
                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": COARSE_CG_DRAM_BYTES,
+                    "traffic_note": "DRAM bytes per launch (ncu); the matrix is read once per solve",
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
                     "flops_per_launch": flops, "iterations_per_launch": iters_per_launch,
                     "ms_per_launch": per_launch_ms, "us_per_iteration": per_launch_ms * 1e3 / iters_per_launch}
