@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "amg.h"
@@ -110,7 +112,10 @@ struct amg_hierarchy {
   int L = 0;                 // index of the coarsest level
   Level lev[AMG_MAX_LEVELS];
   int dense = 0;
-  double *ainv = nullptr;    // n_L x n_L, row-major
+  double *ainv = nullptr;    // n_L x n_L, row-major FP64 inverse (null when ainv32 is used)
+  float *ainv32 = nullptr;   // n_L x n_L, row-major FP32 inverse, refined in FP64 per solve
+  double *dense_r = nullptr; // 2 x n_L: refinement residual and FP64 working solution
+  int dense_refine = 0;      // refinement steps per coarse solve with ainv32
   CoarseCG cg;
   // Krylov work vectors (level 0, FP64)
   double *kb = nullptr, *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
@@ -272,6 +277,8 @@ __device__ __forceinline__ bool is_done(const KState *st) {
 amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st);
 amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s);
 amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
+template <typename T>
+amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st);
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
 amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);

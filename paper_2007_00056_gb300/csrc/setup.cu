@@ -416,93 +416,6 @@ __global__ void k_sort_members(int nc, const int32_t *__restrict__ mrp, int32_t 
 }
 
 // ---------------------------------------------------------------------------
-// Dense coarsest inverse: Gauss-Jordan with partial pivoting (pivot = largest
-// |entry| of the column at or below the diagonal, smallest row on ties).
-// The direct coarsest solve of Sec. 2 and Algorithm 1, factored once at setup;
-// each cycle then applies A_L^{-1} as a matrix-vector product.
-// ---------------------------------------------------------------------------
-__global__ void k_csr_to_dense(int m, const int32_t *rp, const int32_t *ci, const double *val, double *M,
-                               double *Inv) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long mm = (long long)m * m;
-  for (long long t = idx; t < mm; t += (long long)gridDim.x * blockDim.x) {
-    M[t] = 0.0;
-    Inv[t] = (t / m == t % m) ? 1.0 : 0.0;
-  }
-}
-__global__ void k_csr_scatter(int m, const int32_t *rp, const int32_t *ci, const double *val, double *M) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) M[(size_t)i * m + ci[e]] = val[e];
-}
-
-// one block: pivot search in column k, row swap in M and Inv, copy of the
-// pivot row and of the column factors for the elimination step
-__global__ void k_gj_pivot(int m, int k, double *M, double *Inv, double *prow, double *pinv, double *fac,
-                           unsigned *eflags) {
-  __shared__ double bv[1024];
-  __shared__ int bi[1024];
-  double best = -1.0;
-  int bidx = m;
-  for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
-    double a = fabs(M[(size_t)i * m + k]);
-    if (a > best || (a == best && i < bidx)) { best = a; bidx = i; }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      double a = bv[threadIdx.x + s];
-      int ia = bi[threadIdx.x + s];
-      if (a > bv[threadIdx.x] || (a == bv[threadIdx.x] && ia < bi[threadIdx.x])) {
-        bv[threadIdx.x] = a;
-        bi[threadIdx.x] = ia;
-      }
-    }
-    __syncthreads();
-  }
-  int p = bi[0];
-  if (!(bv[0] > 0.0) || p >= m) {
-    if (threadIdx.x == 0) atomicOr(eflags, AMG_EFLAG_BREAKDOWN);
-    p = k;
-  }
-  if (p != k) {
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-      double t = M[(size_t)k * m + j]; M[(size_t)k * m + j] = M[(size_t)p * m + j]; M[(size_t)p * m + j] = t;
-      t = Inv[(size_t)k * m + j]; Inv[(size_t)k * m + j] = Inv[(size_t)p * m + j]; Inv[(size_t)p * m + j] = t;
-    }
-  }
-  __syncthreads();
-  double piv = M[(size_t)k * m + k];
-  double rpiv = piv != 0.0 ? 1.0 / piv : 0.0;
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    prow[j] = M[(size_t)k * m + j] * rpiv;
-    pinv[j] = Inv[(size_t)k * m + j] * rpiv;
-    fac[j] = M[(size_t)j * m + k];
-  }
-}
-
-// rows i != k: row_i -= fac_i * (pivot row / pivot); row k = pivot row / pivot
-__global__ void k_gj_eliminate(int m, int k, double *M, double *Inv, const double *__restrict__ prow,
-                               const double *__restrict__ pinv, const double *__restrict__ fac) {
-  long long mm = (long long)m * m;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < mm;
-       t += (long long)gridDim.x * blockDim.x) {
-    int i = (int)(t / m), j = (int)(t % m);
-    if (i == k) {
-      if (j >= k) M[t] = prow[j];
-      Inv[t] = pinv[j];
-    } else {
-      double f = fac[i];
-      if (j > k) M[t] = M[t] - f * prow[j];
-      else if (j == k) M[t] = 0.0;
-      Inv[t] = Inv[t] - f * pinv[j];
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -737,31 +650,6 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
 }
 
 }  // namespace
-
-// Dense inverse of the coarsest matrix (Gauss-Jordan, partial pivoting).
-amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
-  const Level &c = h->lev[h->L];
-  const int m = c.n;
-  double *M = nullptr, *prow = nullptr, *pinv = nullptr, *fac = nullptr;
-  AMG_TRY(hier_alloc(h, (void **)&h->ainv, sizeof(double) * ((size_t)m * m + AMG_PAD)));
-  if (pool_alloc((void **)&M, sizeof(double) * (size_t)m * m, st) != AMG_OK) return AMG_ERR_OOM;
-  if (pool_alloc((void **)&prow, sizeof(double) * 3 * (m + AMG_PAD), st) != AMG_OK) { pool_free(M, st); return AMG_ERR_OOM; }
-  pinv = prow + (m + AMG_PAD);
-  fac = pinv + (m + AMG_PAD);
-  const int T = AMG_THREADS;
-  long long mm = (long long)m * m;
-  k_csr_to_dense<<<grid_for(mm, T), T, 0, st>>>(m, c.rp, c.ci, c.val, M, h->ainv); count_launch();
-  k_csr_scatter<<<cdiv(m, T), T, 0, st>>>(m, c.rp, c.ci, c.val, M); count_launch();
-  for (int k = 0; k < m; ++k) {
-    k_gj_pivot<<<1, 1024, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac, h->eflags); count_launch();
-    k_gj_eliminate<<<grid_for(mm, T), T, 0, st>>>(m, k, M, h->ainv, prow, pinv, fac); count_launch();
-  }
-  pool_free(M, st);
-  pool_free(prow, st);
-  cudaError_t e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return amg_cuda_status(e);
-  return AMG_OK;
-}
 
 extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                                 const double *d_val, const amg_params *params, amg_stream_t stream,

@@ -407,6 +407,63 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
   }
 }
 
+// Coarsest solve with the FP32 inverse X: xw = (add ? xw : 0) + X v, with FP32
+// products and sums (X itself holds only FP32 accuracy), warp per row; the
+// last step also writes x = xw in the vector type T.
+template <typename V, typename T>
+__global__ void k_gemv32(int m, const float *__restrict__ X, const V *__restrict__ v, double *__restrict__ xw,
+                         int add, T *__restrict__ xout, const KState *st) {
+  if (is_done(st)) return;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
+    const float *row = X + (size_t)i * m;
+    float s = 0.0f;
+    for (int j = lane; j < m; j += 32) s = fmaf(__ldg(&row[j]), (float)v[j], s);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const double xi = (add ? xw[i] : 0.0) + (double)s;
+      xw[i] = xi;
+      if (xout) xout[i] = (T)xi;
+    }
+  }
+}
+
+// r = f - A_L xw in FP64 (the refinement residual).
+template <typename T>
+__global__ void k_dense_resid(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                              const double *__restrict__ val, const T *__restrict__ f, const double *__restrict__ xw,
+                              double *__restrict__ r, const KState *st) {
+  if (is_done(st)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = (double)f[i];
+  for (int e = rp[i]; e < rp[i + 1]; ++e) s = __fma_rn(-val[e], xw[ci[e]], s);
+  r[i] = s;
+}
+
+// x = X f refined `steps` times: xw += X (f - A_L xw).
+template <typename T>
+amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st) {
+  const Level &c = h->lev[h->L];
+  const int m = c.n;
+  double *r = h->dense_r, *xw = h->dense_r + (m + AMG_PAD);
+  const int grid = grid_for((long long)m * 32, AMG_THREADS);
+  k_gemv32<T, T><<<grid, AMG_THREADS, 0, s>>>(m, h->ainv32, f, xw, 0, steps == 0 ? x : nullptr, st);
+  count_launch();
+  for (int k = 1; k <= steps; ++k) {
+    k_dense_resid<T><<<cdiv(m, AMG_THREADS), AMG_THREADS, 0, s>>>(m, c.rp, c.ci, c.val, f, xw, r, st);
+    count_launch();
+    k_gemv32<double, T><<<grid, AMG_THREADS, 0, s>>>(m, h->ainv32, r, xw, 1, k == steps ? x : nullptr, st);
+    count_launch();
+  }
+  return amg_cuda_status(cudaGetLastError());
+}
+template amg_status dense_refined_solve<double>(amg_hierarchy *, const double *, double *, int, cudaStream_t,
+                                                const KState *);
+template amg_status dense_refined_solve<float>(amg_hierarchy *, const float *, float *, int, cudaStream_t,
+                                               const KState *);
+
 // ---------------------------------------------------------------------------
 // Coarsest solve: Jacobi-PCG to ||r|| <= 1e-12 ||f|| (max 1000 iterations) in
 // the Chronopoulos-Gear arrangement, so the three inner products of an
@@ -1064,6 +1121,13 @@ template <typename T>
 void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KState *st) {
   Level &c = h->lev[h->L];
   const double sz = sizeof(T);
+  if (h->dense && h->ainv32) {
+    const double steps = h->dense_refine;
+    LaunchScope ls(h, s, PK_COARSE_DENSE, h->L,
+                   (1.0 + steps) * (4.0 * c.n * (double)c.n + 16.0 * c.n) + steps * (bytes_A(c, 8) + 24.0 * c.n));
+    dense_refined_solve<T>(h, f, x, h->dense_refine, s, st);
+    return;
+  }
   if (h->dense) {
     LaunchScope ls(h, s, PK_COARSE_DENSE, h->L, 8.0 * c.n * (double)c.n + 2.0 * sz * c.n);
     k_gemv_dense<T><<<grid_for((long long)c.n * 32, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, h->ainv, f, x, st);

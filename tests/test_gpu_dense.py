@@ -1,0 +1,70 @@
+"""Dense coarsest solve on the GPU against the oracle's dense LU (Algorithm 1,
+coarsest level solved exactly).
+
+The library inverts the coarsest matrix by blocked Gauss-Jordan elimination:
+in FP64 up to 1024 rows, above that in FP32 with FP64 refinement in every
+coarse solve.  Either way the coarse solve must reach FP64 accuracy, so a
+one-level hierarchy's V-cycle equals the dense solve to 1e-12.
+"""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import rel_err, setup_both, to_cuda
+from paper_2007_00056_gb300 import amg
+from paper_2007_00056_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (name, system, parameters): sizes chosen to hit both inversion paths
+    ("poisson2d_32_fp64_m1024", lambda: W.poisson2d(32), dict(coarse_max=1024)),
+    ("poisson2d_64_fp32_m4096", lambda: W.poisson2d(64), dict(coarse_max=4096)),
+    ("random_spd_m1031_ragged_panels", lambda: W.random_spd(1031, 0.01, 5), dict(coarse_max=1031)),
+    ("convdiff2d_45_nonsymmetric_m2025", lambda: W.convdiff2d(45, peclet=300.0), dict(coarse_max=4096)),
+    ("lognormal3d_14_m2744", lambda: W.lognormal3d(14, seed=3), dict(coarse_max=4096)),
+    ("aniso3d_20_two_levels", lambda: W.anisotropic3d(20), dict(coarse_max=2100)),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", CASES, ids=[c[0] for c in CASES])
+def test_dense_coarse_vcycle_matches_oracle(name, make, kw):
+    s = make()
+    h, oh, b = setup_both(s, **kw)
+    assert h.sizes() == oh.sizes()
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    z_o = oh.vcycle(s.b)
+    assert rel_err(z.cpu().numpy(), z_o) < 1e-12
+    if h.num_levels == 1:
+        # one level: the V-cycle is the exact solve
+        x = np.linalg.solve(s.dense(), s.b)
+        assert rel_err(z.cpu().numpy(), x) < 1e-11
+
+
+def test_dense_coarse_exact_preconditioner_converges_in_one_iteration():
+    s = W.poisson2d(64)
+    h, _, b = setup_both(s, coarse_max=4096)
+    assert h.num_levels == 1
+    x = torch.zeros_like(b)
+    info = amg.pcg_solve(h, b, x, rtol=1e-8)
+    assert info.status == amg.AMG_OK and info.iterations == 1
+    assert info.rel_res_true < 1e-12
+
+
+def test_dense_coarse_fp32_vcycle():
+    s = W.poisson2d(64)
+    h, oh, b = setup_both(s, coarse_max=4096, precision=amg.AMG_FP32)
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    # FP32 storage of the right-hand side and the result bounds the accuracy
+    assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < 1e-6
+
+
+def test_batched_solver_requires_fp64_inverse():
+    s = W.poisson2d(40)  # 1600 rows, one level: FP32 inverse
+    rp, ci, val, b = to_cuda(s)
+    h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=2000))
+    x = torch.zeros_like(b)
+    with pytest.raises(amg.AmgError):
+        amg.amg_batch_pcg([h], [b], [x], rtol=1e-8)
