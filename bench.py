@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the coarse CG kernel on this
 # workload, from one ncu capture of the current kernel
 # (profiles/coarse_cg_lognormal3d_128.md); None once the kernel changes
-COARSE_CG_DRAM_BYTES = 10583296 + 91136
+COARSE_CG_DRAM_BYTES = None
 
 
 def parse_args():
@@ -514,14 +514,15 @@ def main():
     roofline = None
     if top and top["kind"] == "coarse_cg" and level_nnz:
         # The coarse CG keeps its rows in shared memory: per iteration it reads
-        # no matrix from HBM, and its bound is the FP64 pipe (and its two grid
-        # barriers).  FP64 flops per iteration: 2 nnz (SpMV) + 15 n (p, s, r,
-        # x updates, u = D^-1 r, three inner products); the iteration count
-        # comes from the profiler's byte total, which it charges per iteration.
+        # no matrix from HBM, and its bound is the FP64 pipe (and its grid
+        # barrier).  FP64 flops per iteration of the pipelined form: 2 nnz
+        # (SpMV) + 23 n (eight vector updates, m = D^-1 w, three inner
+        # products); the iteration count comes from the profiler's byte total,
+        # which it charges per iteration.
         n_l, nnz_l = level_nnz[top["level"]]
         bytes_per_iter = nnz_l * 12 + 4 * (n_l + 1) + 80 * n_l
         iters_per_launch = top["bytes"] / top["launches"] / bytes_per_iter
-        flops = (2.0 * nnz_l + 15.0 * n_l) * iters_per_launch
+        flops = (2.0 * nnz_l + 23.0 * n_l) * iters_per_launch
         per_launch_ms = top["ms"] / top["launches"]
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
         roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top['kind']}@level{top['level']}",

@@ -251,7 +251,7 @@ amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, d
  * that cannot afford cudaMalloc's implicit device-wide synchronisation, and
  * plugins whose host framework owns every device allocation.
  *
- * All work vectors live in one fixed array inside the library (about 21 MB,
+ * All work vectors live in one fixed array inside the library (about 29 MB,
  * held on every GPU that loads the library until the process exits), so:
  *   - n must be at most 262144 (AMG_ERR_INVALID_ARG beyond that, before any
  *     device work); nnz < 2^31;

@@ -89,18 +89,20 @@ struct Profiler {
   long long launches[AMG_PROF_IDS] = {0};
 };
 
-// Work memory of the persistent coarse CG: own-row x and p, double-buffered
-// r, w, s (neighbours read the previous iteration's copy while owners write
-// the next), reduction partials, barrier counter and iteration counters.
+// Work memory of the persistent coarse CG: the published halo vector (double
+// buffered by iteration parity), the row state when it does not fit in shared
+// memory (CG_STATE vectors of n + AMG_PAD, by position), reduction partials,
+// barrier counter and iteration counters.
+#define CG_STATE 10                 // r, u, w, m, n, z, q, s, p, x
 struct CoarseCG {
   int n = 0, grid = 0, threads = 0;
   size_t smem = 0;           // dynamic shared memory per block (matrix slice staging)
-  double *x = nullptr, *p = nullptr;
-  double *r[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr};
-  double *part = nullptr;    // CG_PART_DOUBLES: 2 slots x 3 values x AMG_MAX_BLOCKS, then 3 totals
+  double *halo[2] = {nullptr, nullptr};
+  double *state = nullptr;
+  double *part = nullptr;    // CG_PART_DOUBLES: 2 slots x 3 values x AMG_MAX_BLOCKS
   int *ord = nullptr;        // n: rows of each block's range sorted by length (coarse_cg_prepare)
   int *meta = nullptr;       // 5 x grid: row range and length-group bounds per block
-  unsigned *bar = nullptr;   // [0] monotonic arrival counter, [1] reduction release counter
+  unsigned *bar = nullptr;   // [0] monotonic arrival counter
   int *iters = nullptr;
   unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
 };

@@ -16,12 +16,12 @@
 // Largest system accepted: 262,144 rows and 2^31 - 1 stored entries.
 #define NOALLOC_MAX_N 262144
 #define NOALLOC_ALIGN 256
-#define NOALLOC_VECS 10  // dinv, the solver's eight work vectors and the row order
+#define NOALLOC_VECS 14  // dinv, the solver's twelve work vectors and the row order
 #define NOALLOC_BYTES                                                                            \
   ((size_t)NOALLOC_VECS * 8 * (NOALLOC_MAX_N + AMG_PAD) + (size_t)CG_PART_DOUBLES * 8 + \
    (size_t)5 * AMG_MAX_BLOCKS * 4 + 16 * NOALLOC_ALIGN)
 
-// The scratch array: about 21 MB on every device that loads the library.
+// The scratch array: about 29 MB on every device that loads the library.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 namespace {
@@ -91,13 +91,9 @@ extern "C" amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d
   double *dinv = (double *)take(vb);
   CoarseCG cg;
   cg.n = n;
-  cg.x = (double *)take(vb);
-  cg.p = (double *)take(vb);
-  for (int k = 0; k < 2; ++k) {
-    cg.r[k] = (double *)take(vb);
-    cg.w[k] = (double *)take(vb);
-    cg.s[k] = (double *)take(vb);
-  }
+  cg.halo[0] = (double *)take(vb);
+  cg.halo[1] = (double *)take(vb);
+  cg.state = (double *)take(vb * CG_STATE);
   cg.part = (double *)take(sizeof(double) * CG_PART_DOUBLES);
   cg.ord = (int *)take(sizeof(int) * ((size_t)n + AMG_PAD));
   cg.meta = (int *)take(sizeof(int) * 5 * AMG_MAX_BLOCKS);

@@ -466,14 +466,14 @@ template amg_status dense_refined_solve<float>(amg_hierarchy *, const float *, f
 
 // ---------------------------------------------------------------------------
 // Coarsest solve: Jacobi-PCG to ||r|| <= 1e-12 ||f|| (max 1000 iterations) in
-// the Chronopoulos-Gear arrangement, so the three inner products of an
-// iteration come from one grid reduction: one persistent cooperative kernel
-// per solve, two bounded software grid barriers per iteration (after the new
-// preconditioned residual u = D^-1 r is published, and in the reduction).
+// the pipelined arrangement, so the three inner products of an iteration
+// come from vectors known before its matrix product: one persistent
+// cooperative kernel per solve, one bounded software grid barrier per
+// iteration.
 //
 // Block b owns the rows of a contiguous range holding about nnz/G entries.
 // Setup sorts each block's rows by length once (stable, so the order is
-// fixed); the kernel keeps the state of its rows (r, s, p, x, w, u, 1/a_ii)
+// fixed); the kernel keeps the state of its rows (ten vectors and 1/a_ii)
 // in shared memory, in that order, and stages its matrix slice as SELL-32
 // (slices of 32 lanes, entry q of a lane at slice offset + 32 q; Kreutzer et
 // al., SIAM J. Sci. Comput. 36(5), 2014): rows up to 16 entries take one
@@ -482,8 +482,8 @@ template amg_status dense_refined_solve<float>(amg_hierarchy *, const float *, f
 // (at most 16) neighbours in one round, and a warp runs exactly as many FMAs
 // as its longest lane needs: FP64 instructions cost the full pipe time even
 // for inactive lanes, so the FMA count is chosen by a warp-uniform branch
-// rather than by predication.  The only global traffic of an iteration is u:
-// written by owners, gathered once per nonzero.
+// rather than by predication.  The only global traffic of an iteration is the
+// halo vector m: written by owners, gathered once per nonzero.
 // ---------------------------------------------------------------------------
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
@@ -496,9 +496,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+
 
 // Monotonic-counter grid barrier: the k-th barrier completes when the counter
 // reaches k * G.  Waits are bounded; a block that gives up sets the timeout
@@ -508,13 +506,12 @@ struct GridBarrier {
   unsigned *count;
   unsigned target;
   long long limit = BARRIER_SPIN_LIMIT;
-  bool was_last = false;  // thread 0: this block's arrival completed the barrier
   __device__ __forceinline__ void arrive(unsigned G) {
     __syncthreads();
     target += G;
     if (threadIdx.x == 0) {
       __threadfence();
-      was_last = atomicAdd(count, 1u) == target - 1;
+      atomicAdd(count, 1u);
     }
   }
   __device__ __forceinline__ bool wait(unsigned *eflags, int *fail_sh) {
@@ -667,8 +664,7 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   extern __shared__ __align__(16) unsigned char cg_smem[];
   __shared__ double red_w[3][CG_THREADS];  // block reduction, one row per inner product
   __shared__ double tot_sh[3];
-  __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
-  __shared__ int fail_sh, last_sh;
+  __shared__ int fail_sh;
   __shared__ int gs[5], nslice_sh[4], wl_sh[CG_THREADS / 32 + 1];
   __shared__ long long sell_total_sh;
   const unsigned G = gridDim.x;
@@ -681,12 +677,12 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
   auto lanes_of = [](int g) { return g == 3 ? 32 : 1 << (2 * g); };
   auto log_lanes = [](int g) { return g == 3 ? 5 : 2 * g; };
   // dynamic shared memory, in order of priority:
-  //   [row ids: nr][row lengths: nr][state r,s,p,x,w,u,d: 7 nr doubles]
+  //   [row ids: nr][row lengths: nr][state r,u,w,m,n,z,q,s,p,x,d: 11 nr doubles]
   //   [slice offsets: ns + 1][warp of each slice: ns][slices by warp: ns]
   //   [SELL columns][SELL values]
   const size_t ids_bytes = (size_t)nr * 8;
   const size_t st_off = (ids_bytes + 15) / 16 * 16;
-  const size_t sl_off = st_off + (size_t)nr * 56;
+  const size_t sl_off = st_off + (size_t)nr * 8 * (CG_STATE + 1);
   int ns_abc = 0;
   for (int g = 0; g < 3; ++g) ns_abc += (gs[g + 1] - gs[g] + (32 / lanes_of(g)) - 1) / (32 / lanes_of(g));
   const size_t sell_off = (sl_off + (size_t)(3 * ns_abc + 1) * 4 + 15) / 16 * 16;
@@ -785,30 +781,25 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     }
   }
   __syncthreads();
-  // row state by position: in shared memory, or in the global work arrays
-  double *vr = local_state ? s_st : cg.r[1] + P0;
-  double *vs = local_state ? s_st + nr : cg.s[0] + P0;
-  double *vp = local_state ? s_st + 2 * nr : cg.p + P0;
-  double *vx = local_state ? s_st + 3 * nr : cg.x + P0;
-  double *vw = local_state ? s_st + 4 * nr : cg.w[0] + P0;
-  double *vu = local_state ? s_st + 5 * nr : cg.s[1] + P0;
-  double *vd = local_state ? s_st + 6 * nr : cg.w[1] + P0;
-  double *u = cg.r[0];  // published preconditioned residual, read by every block's SpMV
+  // row state by position: in shared memory, or in the global work vectors
+  // (vector k of the row at position t at sbase[k * sstride + t])
+  double *const sbase = local_state ? s_st : cg.state + P0;
+  const size_t sstride = local_state ? (size_t)nr : (size_t)n + AMG_PAD;
+#define CGV(k) (sbase + (size_t)(k) * sstride)
+  double *vr = CGV(0), *vu = CGV(1), *vw = CGV(2), *vm = CGV(3), *vn = CGV(4);
+  double *vz = CGV(5), *vq = CGV(6), *vs = CGV(7), *vp = CGV(8), *vx = CGV(9);
+#undef CGV
+  // published vector (u for the first product, then m = D^-1 w), double
+  // buffered by iteration parity: a block may publish the next one while
+  // another still reads the current one
+  double *pub[2] = {cg.halo[0], cg.halo[1]};
+  auto dinv_at = [&](int t) { return local_state ? s_st[(size_t)10 * nr + t] : __ldg(&dinv[row_at(t)]); };
   GridBarrier gb{cg.bar, 0u};
-  int slot = 0;
-  // Inner products: block partials -> the last block to arrive sums them ->
-  // totals for all.  Every FP64 warp instruction costs the same whatever the
-  // number of active lanes, so the block step halves the values in shared
-  // memory with whole warps and the last 32 values of each product go to
-  // their own warp.  The G partials are then read and summed by the last
-  // block alone (warps 0-2 one product each: loads in flight together, then
-  // in index order per lane and a fixed shuffle tree), which publishes the
-  // totals and releases the others through a second counter: when every
-  // block read all partials, the same few cache lines were requested by all
-  // SMs at once.  Totals land in tot_sh.
-  double *tot_g = cg.part + 6 * AMG_MAX_BLOCKS;
-  unsigned seq = 0;  // reductions done (thread 0)
-  auto reduce3 = [&](double (&v)[3]) -> bool {
+  // Block partials of (r,u), (w,u), (r,r): every FP64 warp instruction costs
+  // the same whatever the number of active lanes, so the values are halved in
+  // shared memory by whole warps and the last 32 of each product go to their
+  // own warp; lane 0 of warps 0-2 publishes the block's three partials.
+  auto block_partials = [&](double (&v)[3], double *part) {
     const int t = threadIdx.x;
     red_w[0][t] = v[0];
     red_w[1][t] = v[1];
@@ -822,69 +813,26 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       }
       __syncthreads();
     }
-    double *part = cg.part + slot * 3 * AMG_MAX_BLOCKS;
     if (warp < 3) {
       const double bsum = warp_sum(red_w[warp][lane]);
       if (lane == 0) part[warp * AMG_MAX_BLOCKS + blockIdx.x] = bsum;
     }
-    gb.arrive(G);
-    if (t == 0) {
-      ++seq;
-      last_sh = gb.was_last;
-      if (gb.was_last) __threadfence();  // acquire: every block's partial is visible
-    }
-    __syncthreads();
-    bool ok = true;
-    if (last_sh) {
-      if (warp < 3) {
-        constexpr int PQ = 8;  // up to 256 partials per round of loads
-        const double *pk = part + warp * AMG_MAX_BLOCKS;
-        double a = 0.0;
-        for (unsigned k0 = 0; k0 < G; k0 += 32 * PQ) {
-          double pa[PQ];
-#pragma unroll
-          for (int q = 0; q < PQ; ++q) {
-            const unsigned k = k0 + lane + 32 * q;
-            pa[q] = k < G ? __ldcg(&pk[k]) : 0.0;
-          }
-#pragma unroll
-          for (int q = 0; q < PQ; ++q)
-            if (k0 + lane + 32 * q < G) a += pa[q];
-        }
-        a = warp_sum(a);
-        if (lane == 0) {
-          tot_sh[warp] = a;
-          tot_g[warp] = a;
-        }
-      }
-      __syncthreads();
-      if (t == 0) {
-        __threadfence();
-        st_release_u32(cg.bar + 1, seq);
-      }
-    } else {
-      if (t == 0) {
-        long long t0 = clock64();
-        while (ld_acquire_u32(cg.bar + 1) < seq) {
-          if (clock64() - t0 > gb.limit) {
-            atomicOr(eflags, AMG_EFLAG_TIMEOUT);
-            fail_sh = 1;
-            break;
-          }
-        }
-      }
-      __syncthreads();
-      ok = fail_sh == 0;
-      if (t < 3) tot_sh[t] = __ldcg(&tot_g[t]);
-    }
-    __syncthreads();
-    slot ^= 1;
-    return ok;
   };
-  // w = A u for the block's rows, each warp taking its slices, and the three
-  // inner products (r,u), (w,u), (r,r) accumulated by the lane that finishes
-  // each row
-  auto spmv_dots = [&](double (&acc)[3]) {
+  // y = A v for the block's rows into vy, each warp taking its slices; warps
+  // 0-2 first issue the loads of the G partials of one inner product each
+  // (kept in registers across the product, so their latency is hidden) and
+  // afterwards sum them in index order per lane and a fixed shuffle tree.
+  constexpr int PQ = 5;  // partials per lane loaded ahead (grids up to 160 blocks)
+  auto spmv = [&](const double *v, double *vy, const double *part, bool with_totals) {
+    double pa[PQ];
+    const double *pk = part + (warp < 3 ? warp : 0) * AMG_MAX_BLOCKS;
+    if (with_totals && warp < 3) {
+#pragma unroll
+      for (int q = 0; q < PQ; ++q) {
+        const unsigned k = lane + 32 * q;
+        pa[q] = k < G ? __ldcg(&pk[k]) : 0.0;
+      }
+    }
     auto slice = [&](int g, int js) {
       const int ln = lanes_of(g), rs = 32 / ln;
       const int pos = gs[g] + js * rs + lane / ln, sub = lane % ln;
@@ -907,15 +855,9 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
         vals = val + b + sub;
         stride = ln;
       }
-      double wi = cg_row_part(cols, vals, stride, cnt, wmax, u);
-      for (int o = ln >> 1; o > 0; o >>= 1) wi += __shfl_xor_sync(0xffffffffu, wi, o);
-      if (valid && sub == 0) {
-        vw[pos] = wi;
-        const double ri = vr[pos], ui = vu[pos];
-        acc[0] = __fma_rn(ri, ui, acc[0]);
-        acc[1] = __fma_rn(wi, ui, acc[1]);
-        acc[2] = __fma_rn(ri, ri, acc[2]);
-      }
+      double yi = cg_row_part(cols, vals, stride, cnt, wmax, v);
+      for (int o = ln >> 1; o > 0; o >>= 1) yi += __shfl_xor_sync(0xffffffffu, yi, o);
+      if (valid && sub == 0) vy[pos] = yi;
     };
     if (staged) {
       for (int k = wl_sh[warp]; k < wl_sh[warp + 1]; ++k) {
@@ -929,87 +871,122 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
       }
     }
     for (int js = warp; js < gs[4] - gs[3]; js += nwarps) slice(3, js);  // rows over 256 entries
+    if (with_totals && warp < 3) {
+      double a = 0.0;
+#pragma unroll
+      for (int q = 0; q < PQ; ++q)
+        if (lane + 32 * q < G) a += pa[q];
+      for (unsigned k0 = 32 * PQ; k0 < G; k0 += 32)  // larger grids
+        if (k0 + lane < G) a += __ldcg(&pk[k0 + lane]);
+      a = warp_sum(a);
+      if (lane == 0) tot_sh[warp] = a;
+    }
+    __syncthreads();
   };
 
-  // initial phase: r0 = f, u0 = D^-1 f (published), s = p = x = 0; then w0 = A u0
+  // Pipelined Jacobi-PCG (Ghysels and Vanroose, SIAM J. Sci. Comput. 36(2),
+  // 2014): the inner products of an iteration come from vectors known before
+  // its matrix product, so one grid barrier per iteration publishes both the
+  // halo vector m = D^-1 w and the partial sums, and the sums are formed while
+  // the product n = A m runs.  Per iteration, after alpha and beta:
+  //   z = n + beta z, q = m + beta q, s = w + beta s, p = u + beta p,
+  //   x += alpha p, r -= alpha s, u -= alpha q, w -= alpha z,
+  // with u = D^-1 r and w = A u holding by the recurrences.
+  // initial phase: r = f, u = D^-1 f published, the other vectors zero
   for (int t = threadIdx.x; t < nr; t += blockDim.x) {
     const int i = row_at(t);
     const double fi = (double)f[i];
     const double di = __ldg(&dinv[i]);
     const double ui = __dmul_rn(fi, di);
+    if (local_state) s_st[(size_t)10 * nr + t] = di;
     vr[t] = fi;
     vu[t] = ui;
-    vd[t] = di;
-    u[i] = ui;
+    pub[1][i] = ui;
+    vz[t] = 0.0;
+    vq[t] = 0.0;
     vs[t] = 0.0;
     vp[t] = 0.0;
     vx[t] = 0.0;
   }
   bool ok = gb.sync(G, eflags, &fail_sh);
-  double v[3] = {0.0, 0.0, 0.0};
-  if (ok) spmv_dots(v);
-  ok = reduce3(v) && ok;
-  // scalars, kept by thread 0: the stop threshold on (r,r), gamma = (r,u),
-  // alpha, and the reciprocals 1/gamma and 1/(gamma alpha) of the previous
-  // iteration, computed while the next iteration's vectors are updated so
-  // that only one division stays between a reduction and the next update
-  double thresh = 0.0, gamma = 0.0, alpha_t = 0.0, beta_t = 0.0, inv_g = 0.0, inv_ga = 0.0;
-  if (threadIdx.x == 0) {
-    const double fnorm = sqrt(tot_sh[2]);
-    thresh = (CG_RTOL * fnorm) * (CG_RTOL * fnorm);
-    gamma = tot_sh[0];
-    alpha_t = tot_sh[0] / tot_sh[1];
-    sc[0] = alpha_t;
-    sc[1] = 0.0;
-    sc[2] = (fnorm > 0.0 && ok && fail_sh == 0) ? 0.0 : 1.0;
+  if (ok) spmv(pub[1], vw, nullptr, false);  // w = A u
+  else __syncthreads();
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+    const double ri = vr[t], ui = vu[t], wi = vw[t];
+    const double mi = __dmul_rn(wi, dinv_at(t));
+    vm[t] = mi;
+    pub[0][row_at(t)] = mi;
+    acc[0] = __fma_rn(ri, ui, acc[0]);
+    acc[1] = __fma_rn(wi, ui, acc[1]);
+    acc[2] = __fma_rn(ri, ri, acc[2]);
   }
-  __syncthreads();
+  // scalars, kept by thread 0: the stop threshold on (r,r), gamma = (r,u) and
+  // alpha of the previous iteration and the reciprocals 1/gamma and
+  // 1/(gamma alpha), computed while the vectors are updated so that only one
+  // division stays between the reduction and the next update
+  __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
+  double thresh = 0.0, gamma = 0.0, alpha_t = 0.0, inv_g = 0.0, inv_ga = 0.0;
   int it = 0;
-  if (sc[2] == 0.0) {
-    for (it = 1; it <= CG_MAXIT; ++it) {
-      const double alpha = sc[0], beta = sc[1];
-      if (threadIdx.x == 0) {
-        inv_g = 1.0 / gamma;
-        inv_ga = 1.0 / (gamma * alpha_t);
-      }
-      // phase A (own rows): p = u + beta p, s = w + beta s, r -= alpha s, u = D^-1 r
-      for (int t = threadIdx.x; t < nr; t += blockDim.x) {
-        const double pi = __fma_rn(beta, vp[t], vu[t]);
-        const double si = __fma_rn(beta, vs[t], vw[t]);
-        const double ri = __fma_rn(-alpha, si, vr[t]);
-        const double ui = __dmul_rn(ri, vd[t]);
-        vp[t] = pi;
-        vs[t] = si;
-        vr[t] = ri;
-        vu[t] = ui;
-        u[row_at(t)] = ui;
-      }
-      gb.arrive(G);
-      // x += alpha p while the other blocks arrive (same thread, same rows)
-      for (int t = threadIdx.x; t < nr; t += blockDim.x) vx[t] = __fma_rn(alpha, vp[t], vx[t]);
-      ok = gb.wait(eflags, &fail_sh);
-      // phase B: w = A u and the three inner products, one reduction
-      double acc[3] = {0.0, 0.0, 0.0};
-      if (ok) spmv_dots(acc);
-      ok = reduce3(acc) && ok;
-      if (threadIdx.x == 0) {
-        const double gamma_new = tot_sh[0];
-        bool stop = !ok || fail_sh != 0 || tot_sh[2] <= thresh;
-        if (!stop) {
-          // beta = gamma'/gamma, alpha = gamma'/(delta' - beta gamma'/alpha)
-          beta_t = gamma_new * inv_g;
-          alpha_t = gamma_new / (tot_sh[1] - gamma_new * gamma_new * inv_ga);
-          gamma = gamma_new;
-          stop = !isfinite(alpha_t);
+  for (it = 0;; ++it) {
+    double *part = cg.part + (it & 1) * 3 * AMG_MAX_BLOCKS;
+    block_partials(acc, part);
+    ok = gb.sync(G, eflags, &fail_sh) && ok;
+    if (ok) spmv(pub[it & 1], vn, part, true);  // n = A m, totals of this iteration
+    else __syncthreads();
+    if (threadIdx.x == 0) {
+      const double g_i = tot_sh[0], d_i = tot_sh[1], rr = tot_sh[2];
+      if (it == 0) thresh = (CG_RTOL * sqrt(rr)) * (CG_RTOL * sqrt(rr));
+      bool stop = !ok || fail_sh != 0 || rr <= thresh || it >= CG_MAXIT;
+      double a = 0.0, b = 0.0;
+      if (!stop) {
+        if (it == 0) {
+          a = g_i / d_i;
+        } else {
+          // beta = gamma_i/gamma_{i-1}, alpha = gamma_i/(delta_i - beta gamma_i/alpha_{i-1})
+          b = g_i * inv_g;
+          a = g_i / (d_i - g_i * g_i * inv_ga);
         }
-        sc[0] = alpha_t;
-        sc[1] = beta_t;
-        sc[2] = stop ? 1.0 : 0.0;
+        stop = !isfinite(a);
+        gamma = g_i;
+        alpha_t = a;
       }
-      __syncthreads();
-      if (sc[2] != 0.0) break;
+      sc[0] = a;
+      sc[1] = b;
+      sc[2] = stop ? 1.0 : 0.0;
     }
-    if (it > CG_MAXIT) it = CG_MAXIT;
+    __syncthreads();
+    if (sc[2] != 0.0) break;
+    const double alpha = sc[0], beta = sc[1];
+    if (threadIdx.x == 0) {
+      inv_g = 1.0 / gamma;
+      inv_ga = 1.0 / (gamma * alpha_t);
+    }
+    double *pnext = pub[(it + 1) & 1];
+    acc[0] = acc[1] = acc[2] = 0.0;
+    for (int t = threadIdx.x; t < nr; t += blockDim.x) {
+      const double zi = __fma_rn(beta, vz[t], vn[t]);
+      const double qi = __fma_rn(beta, vq[t], vm[t]);
+      const double si = __fma_rn(beta, vs[t], vw[t]);
+      const double pi = __fma_rn(beta, vp[t], vu[t]);
+      vx[t] = __fma_rn(alpha, pi, vx[t]);
+      const double ri = __fma_rn(-alpha, si, vr[t]);
+      const double ui = __fma_rn(-alpha, qi, vu[t]);
+      const double wi = __fma_rn(-alpha, zi, vw[t]);
+      const double mi = __dmul_rn(wi, dinv_at(t));
+      vz[t] = zi;
+      vq[t] = qi;
+      vs[t] = si;
+      vp[t] = pi;
+      vr[t] = ri;
+      vu[t] = ui;
+      vw[t] = wi;
+      vm[t] = mi;
+      pnext[row_at(t)] = mi;
+      acc[0] = __fma_rn(ri, ui, acc[0]);
+      acc[1] = __fma_rn(wi, ui, acc[1]);
+      acc[2] = __fma_rn(ri, ri, acc[2]);
+    }
   }
   for (int t = threadIdx.x; t < nr; t += blockDim.x) xout[row_at(t)] = (T)vx[t];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1284,13 +1261,9 @@ amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
   CoarseCG &cg = h->cg;
   cg.n = c.n;
   size_t vb = sizeof(double) * (c.n + AMG_PAD);
-  AMG_TRY(hier_alloc(h, (void **)&cg.x, vb));
-  AMG_TRY(hier_alloc(h, (void **)&cg.p, vb));
-  for (int b = 0; b < 2; ++b) {
-    AMG_TRY(hier_alloc(h, (void **)&cg.r[b], vb));
-    AMG_TRY(hier_alloc(h, (void **)&cg.w[b], vb));
-    AMG_TRY(hier_alloc(h, (void **)&cg.s[b], vb));
-  }
+  AMG_TRY(hier_alloc(h, (void **)&cg.halo[0], vb));
+  AMG_TRY(hier_alloc(h, (void **)&cg.halo[1], vb));
+  AMG_TRY(hier_alloc(h, (void **)&cg.state, vb * CG_STATE));
   AMG_TRY(hier_alloc(h, (void **)&cg.part, sizeof(double) * CG_PART_DOUBLES));
   AMG_TRY(hier_alloc(h, (void **)&cg.ord, sizeof(int) * (c.n + AMG_PAD)));
   AMG_TRY(hier_alloc(h, (void **)&cg.meta, sizeof(int) * 5 * AMG_MAX_BLOCKS));
