@@ -10,7 +10,11 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 #define HEM_FREE (-2)
 
@@ -80,58 +84,194 @@ __global__ void k_weights(int n, const int32_t *__restrict__ rp, const int32_t *
 // ---------------------------------------------------------------------------
 // Handshake rounds
 // ---------------------------------------------------------------------------
-__global__ void k_hem_init(int n, int32_t *mate, int32_t *frontier) {
+__global__ void k_hem_init(int n, int32_t *mate, int32_t *dirty, int *stamp) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) { mate[i] = HEM_FREE; frontier[i] = i; }
+  if (i < n) {
+    mate[i] = HEM_FREE;
+    dirty[i] = i;
+    stamp[i] = 0;
+  }
 }
 
-// Rounds run in batches between host checks: a round reads the frontier size
-// left by the previous round (nf_dev) and does nothing once a previous round
-// has paired nobody (prev_pairs == 0), i.e. after the fixed point.
-__device__ __forceinline__ int round_frontier(int nf_host, const int *nf_dev, const int *prev_pairs) {
-  if (prev_pairs && *prev_pairs == 0) return 0;
-  return nf_dev ? *nf_dev : nf_host;
+// Incremental rounds.  A free node's set of free neighbours only shrinks, so
+// its pick (heaviest free neighbour, smaller index on equal weight) can change
+// only when the node it picked was matched.  Round r therefore recomputes the
+// picks of the nodes in its dirty list D_r only (D_0 = every node), pairs the
+// mutual picks found from D_r, lists the newly matched nodes, and puts every
+// free neighbour that had picked one of them into D_{r+1}.  The picks, pairs
+// and round count equal those of recomputing every free node each round.
+// Rounds run in batches between host checks: a round reads the sizes left by
+// the previous round and does nothing once a previous round has paired
+// nobody (the fixed point).  Lists are walked with grid-stride loops.
+#define HEM_BLOCK_CAP 2048     // largest dirty list handled by the one-block rounds
+#define HEM_BLOCK_ROUNDS 4096  // rounds per launch of the one-block rounds
+
+// Slot for one appended list entry: the lanes of the warp that append at the
+// same time share one atomic on the counter.
+__device__ __forceinline__ int warp_append(int *counter) {
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (int)g.size());
+  return g.shfl(base, 0) + (int)g.thread_rank();
 }
 
-// Each free node of the frontier picks its heaviest free neighbour (equal
-// weights: smaller index); -1 if it has none.
-__global__ void k_hem_pick(int nf_host, const int *nf_dev, const int *prev_pairs, const int32_t *__restrict__ frontier,
+__device__ __forceinline__ int round_count(int n_host, const int *n_dev, const int *prev_matched) {
+  if (prev_matched && *prev_matched == 0) return 0;
+  return n_dev ? *n_dev : n_host;
+}
+
+// Picks of the dirty nodes; -1 when a node has no free neighbour left.
+__global__ void k_hem_pick(int nd_host, const int *nd_dev, const int *prev_matched, const int32_t *__restrict__ D,
                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
                            const int32_t *__restrict__ mate, int32_t *__restrict__ pick) {
-  const int nf = round_frontier(nf_host, nf_dev, prev_pairs);
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nf) return;
-  int i = frontier[t];
-  int best = -1;
-  double bw = 0.0;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) {
-    double we = w[e];
-    if (we <= 0.0) continue;
-    int j = ci[e];
-    if (mate[j] != HEM_FREE) continue;
-    // columns ascend, so on equal weight the first one met is the smaller index
-    if (best < 0 || we > bw) { best = j; bw = we; }
+  const int nd = round_count(nd_host, nd_dev, prev_matched);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nd; t += gridDim.x * blockDim.x) {
+    const int i = D[t];
+    int best = -1;
+    double bw = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e) {
+      const double we = w[e];
+      if (we <= 0.0) continue;
+      const int j = ci[e];
+      if (mate[j] != HEM_FREE) continue;
+      // columns ascend, so on equal weight the first one met is the smaller index
+      if (best < 0 || we > bw) { best = j; bw = we; }
+    }
+    pick[i] = best;
   }
-  pick[i] = best;
 }
 
-// Mutual picks become pairs; nodes that still had a free neighbour stay in the
-// frontier.  cnt[0] += pairs formed, cnt[1] = size of the next frontier.
-__global__ void k_hem_match(int nf_host, const int *nf_dev, const int *prev_pairs,
-                            const int32_t *__restrict__ frontier, const int32_t *__restrict__ pick,
-                            int32_t *__restrict__ mate, int32_t *__restrict__ next, int *cnt) {
-  const int nf = round_frontier(nf_host, nf_dev, prev_pairs);
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nf) return;
-  int i = frontier[t];
-  int j = pick[i];
-  if (j < 0) return;
-  if (pick[j] == i) {
+// Mutual picks seen from D_r become pairs (both ends written; the partner of a
+// dirty node may be clean, its pick still valid).  Matched nodes are listed in
+// M, each once: a partner that is itself dirty lists itself.  cnt[0] =
+// matched nodes this round.
+// Frontier rounds (full != 0) skip the dirty pass instead: D_r then holds
+// every free node with a free neighbour (so both ends of a pair are in it),
+// and D_{r+1} (cnt[1], stamp r + 1) is every node of D_r that picked but was
+// not matched -- a superset of the dirty set, so incremental rounds may
+// follow.  Cheaper than the dirty pass in the first rounds, where most pairs
+// form; the host keeps them while a round pairs at least a quarter of its
+// list and switches to incremental rounds for good after the first one that
+// does not (a narrow front advancing through a uniform grid).
+__global__ void k_hem_match(int nd_host, const int *nd_dev, const int *prev_matched, const int32_t *__restrict__ D,
+                            int *__restrict__ stamp, int r, int full, const int32_t *__restrict__ pick,
+                            int32_t *__restrict__ mate, int32_t *__restrict__ M, int32_t *__restrict__ Dn, int *cnt) {
+  const int nd = round_count(nd_host, nd_dev, prev_matched);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nd; t += gridDim.x * blockDim.x) {
+    const int i = D[t];
+    const int j = pick[i];
+    if (j < 0) continue;
+    if (pick[j] != i) {
+      if (full) {
+        stamp[i] = r + 1;
+        Dn[warp_append(&cnt[1])] = i;
+      }
+      continue;
+    }
     mate[i] = j;
-    if (i < j) atomicAdd(&cnt[0], 1);
-  } else {
-    int slot = atomicAdd(&cnt[1], 1);
-    next[slot] = i;
+    if (full) {  // both ends are in D_r: each counts itself
+      warp_append(&cnt[0]);
+      continue;
+    }
+    mate[j] = i;
+    M[warp_append(&cnt[0])] = i;
+    if (stamp[j] != r) M[warp_append(&cnt[0])] = j;
+  }
+}
+
+// D_{r+1}: free neighbours of this round's matched nodes whose pick was one of
+// them, each listed once (stamp = r + 1).  cnt[1] = size of D_{r+1}.
+__global__ void k_hem_dirty(const int *__restrict__ matched, const int32_t *__restrict__ M,
+                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ mate, const int32_t *__restrict__ pick, int *__restrict__ stamp,
+                            int r1, int32_t *__restrict__ Dn, int *cnt) {
+  const int nm = *matched;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += gridDim.x * blockDim.x) {
+    const int m = M[t];
+    for (int e = rp[m]; e < rp[m + 1]; ++e) {
+      const int k = ci[e];
+      if (k == m || mate[k] != HEM_FREE || pick[k] != m) continue;
+      if (atomicExch(&stamp[k], r1) != r1) Dn[warp_append(&cnt[1])] = k;
+    }
+  }
+}
+
+// Incremental rounds while the dirty list is small run inside one thread block
+// (the three steps of a round separated by block barriers, the list counters
+// in shared memory): launches, not work, dominate such rounds on uniform
+// grids, where thousands of them advance a narrow front.  The block leaves at
+// the fixed point, when a next list exceeds `cap`, or after max_rounds.
+// out[0] = rounds run (the last one pairing nobody counts), out[1] = 1 at the
+// fixed point, out[2] = size of the list in D[out[3]].
+__global__ void __launch_bounds__(1024)
+    k_hem_rounds_block(int r0, int max_rounds, int cap, int nd, int32_t *__restrict__ Da, int32_t *__restrict__ Db,
+                       int *__restrict__ stamp, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ w, int32_t *__restrict__ mate, int32_t *__restrict__ pick,
+                       int32_t *__restrict__ M, int *out) {
+  __shared__ int s_nm, s_nn;
+  int32_t *D = Da, *Dn = Db;
+  int k = 0, finished = 0, which = 0;
+  for (; k < max_rounds; ++k) {
+    const int r = r0 + k;
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+      const int i = D[t];
+      int best = -1;
+      double bw = 0.0;
+      for (int e = rp[i]; e < rp[i + 1]; ++e) {
+        const double we = w[e];
+        if (we <= 0.0) continue;
+        const int j = ci[e];
+        if (mate[j] != HEM_FREE) continue;
+        if (best < 0 || we > bw) { best = j; bw = we; }
+      }
+      pick[i] = best;
+    }
+    if (threadIdx.x == 0) {
+      s_nm = 0;
+      s_nn = 0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nd; t += blockDim.x) {
+      const int i = D[t];
+      const int j = pick[i];
+      if (j < 0 || pick[j] != i) continue;
+      mate[i] = j;
+      mate[j] = i;
+      M[atomicAdd(&s_nm, 1)] = i;
+      if (stamp[j] != r) M[atomicAdd(&s_nm, 1)] = j;
+    }
+    __syncthreads();
+    const int nm = s_nm;
+    if (nm == 0) {
+      finished = 1;
+      ++k;
+      break;
+    }
+    for (int t = threadIdx.x; t < nm; t += blockDim.x) {
+      const int m = M[t];
+      for (int e = rp[m]; e < rp[m + 1]; ++e) {
+        const int q = ci[e];
+        if (q == m || mate[q] != HEM_FREE || pick[q] != m) continue;
+        if (atomicExch(&stamp[q], r + 1) != r + 1) Dn[atomicAdd(&s_nn, 1)] = q;
+      }
+    }
+    __syncthreads();
+    nd = s_nn;
+    int32_t *tmp = D;
+    D = Dn;
+    Dn = tmp;
+    which ^= 1;
+    __syncthreads();  // every thread has read s_nn before the next round resets it
+    if (nd > cap) {
+      ++k;
+      break;
+    }
+  }
+  if (threadIdx.x == 0) {
+    out[0] = k;
+    out[1] = finished;
+    out[2] = nd;
+    out[3] = which;
   }
 }
 
@@ -488,22 +628,46 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   const int T = AMG_THREADS;
   k_weights<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, in.val, S.w, h->eflags); count_launch();
   AMG_TRY(check_flags(h, st));
-  k_hem_init<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.fa); count_launch();
-  int nf = n, r = 0;
+  // S.flag holds the round stamps and S.first the matched list while the
+  // rounds run; the numbering below overwrites both
+  k_hem_init<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.fa, S.flag); count_launch();
+  int nd = n, r = 0;
   int32_t *fa = S.fa, *fb = S.fb;
   const int round_cap = 4 * n + 16;  // each productive round pairs >= 1 node
   int batch = 4;                     // rounds per host check: 4, 8, then 16
-  bool finished = false;
+  bool finished = false, frontier_rounds = true;
+  const int grid = std::min(cdiv(std::max(n, 1), T), 8 * h->num_sms);
   while (!finished) {
     if (r > round_cap) return AMG_ERR_TIMEOUT;
+    if (!frontier_rounds && nd <= HEM_BLOCK_CAP) {
+      // small list: rounds inside one block until it grows or the matching ends
+      k_hem_rounds_block<<<1, 1024, 0, st>>>(r, HEM_BLOCK_ROUNDS, HEM_BLOCK_CAP, nd, fa, fb, S.flag, in.rp, in.ci,
+                                             S.w, S.mate, S.pick, S.first, S.cnt + 36);
+      count_launch();
+      AMG_CUDA(cudaMemcpyAsync(S.host, S.cnt + 36, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+      AMG_CUDA(cudaStreamSynchronize(st));
+      r += S.host[0];
+      finished = S.host[1] != 0;
+      nd = S.host[2];
+      if (S.host[3]) std::swap(fa, fb);
+      continue;
+    }
     AMG_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(int) * 2 * batch, st));
-    const int grid = cdiv(std::max(nf, 1), T);
     int32_t *ba = fa, *bb = fb;
     for (int b = 0; b < batch; ++b) {
-      const int *nf_dev = b ? S.cnt + 2 * (b - 1) + 1 : nullptr;
+      const int *nd_dev = b ? S.cnt + 2 * (b - 1) + 1 : nullptr;
       const int *prev = b ? S.cnt + 2 * (b - 1) : nullptr;
-      k_hem_pick<<<grid, T, 0, st>>>(nf, nf_dev, prev, ba, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
-      k_hem_match<<<grid, T, 0, st>>>(nf, nf_dev, prev, ba, S.pick, S.mate, bb, S.cnt + 2 * b); count_launch();
+      const int rr = r + b;
+      k_hem_pick<<<grid, T, 0, st>>>(nd, nd_dev, prev, ba, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
+      const int full = frontier_rounds ? 1 : 0;
+      k_hem_match<<<grid, T, 0, st>>>(nd, nd_dev, prev, ba, S.flag, rr, full, S.pick, S.mate, S.first, bb,
+                                       S.cnt + 2 * b);
+      count_launch();
+      if (!full) {
+        k_hem_dirty<<<grid, T, 0, st>>>(S.cnt + 2 * b, S.first, in.rp, in.ci, S.mate, S.pick, S.flag, rr + 1, bb,
+                                         S.cnt + 2 * b);
+        count_launch();
+      }
       std::swap(ba, bb);
     }
     AMG_CUDA(cudaMemcpyAsync(S.host, S.cnt, sizeof(int) * 2 * batch, cudaMemcpyDeviceToHost, st));
@@ -511,7 +675,8 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
     for (int b = 0; b < batch; ++b) {
       ++r;
       if (S.host[2 * b] == 0) { finished = true; break; }
-      nf = S.host[2 * b + 1];
+      if (frontier_rounds && 4ll * S.host[2 * b] < (long long)nd) frontier_rounds = false;
+      nd = S.host[2 * b + 1];
     }
     fa = ba;
     fb = bb;

@@ -536,9 +536,10 @@ struct GridBarrier {
 
 __device__ __forceinline__ int cg_key(int len) { return len < CG_KEYS - 1 ? len : CG_KEYS - 1; }
 
-// FP64 work of a row per CG iteration, in multiply-adds: its entries plus
-// about eight vector operations (updates, the three inner products).
-#define CG_ROW_COST 8
+// Time of a row per CG iteration relative to one of its entries: measured
+// per block on GB300, an iteration costs about 2.6 clocks per entry (the
+// SpMV) and 8 per row (vector updates and inner products).
+#define CG_ROW_COST 3
 
 // Smallest row r whose work prefix rp[r] + CG_ROW_COST r reaches target.
 __device__ __forceinline__ int cg_first_row_with(const int32_t *rp, int n, long long target) {
@@ -731,7 +732,8 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     if (room) {
       s_slice[j] = (int)off;
       int load[CG_THREADS / 32];
-      for (int w = 0; w < nwarps; ++w) load[w] = 0;
+      // warps 0-2 also sum the partials of one inner product each
+      for (int w = 0; w < nwarps; ++w) load[w] = w < 3 ? 12 : 0;
       for (int g = 2; g >= 0; --g)
         for (int jj = nslice_sh[g + 1] - 1; jj >= nslice_sh[g]; --jj) {
           int best = 0;
@@ -921,12 +923,14 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     acc[1] = __fma_rn(wi, ui, acc[1]);
     acc[2] = __fma_rn(ri, ri, acc[2]);
   }
-  // scalars, kept by thread 0: the stop threshold on (r,r), gamma = (r,u) and
-  // alpha of the previous iteration and the reciprocals 1/gamma and
-  // 1/(gamma alpha), computed while the vectors are updated so that only one
-  // division stays between the reduction and the next update
+  // scalars: thread 0 keeps the stop threshold on (r,r) and evaluates alpha
+  // and beta from the totals and the reciprocals 1/gamma and 1/(gamma alpha)
+  // of the previous iteration, which two other warps form while the vectors
+  // are updated, so that one division stays between a reduction and the next
+  // update
   __shared__ double sc[3];  // alpha, beta, stop flag (from thread 0)
-  double thresh = 0.0, gamma = 0.0, alpha_t = 0.0, inv_g = 0.0, inv_ga = 0.0;
+  __shared__ double rcp_sh[2];  // 1/gamma and 1/(gamma alpha) of the previous iteration
+  double thresh = 0.0;
   int it = 0;
   for (it = 0;; ++it) {
     double *part = cg.part + (it & 1) * 3 * AMG_MAX_BLOCKS;
@@ -944,12 +948,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
           a = g_i / d_i;
         } else {
           // beta = gamma_i/gamma_{i-1}, alpha = gamma_i/(delta_i - beta gamma_i/alpha_{i-1})
-          b = g_i * inv_g;
-          a = g_i / (d_i - g_i * g_i * inv_ga);
+          b = g_i * rcp_sh[0];
+          a = g_i / (d_i - g_i * g_i * rcp_sh[1]);
         }
         stop = !isfinite(a);
-        gamma = g_i;
-        alpha_t = a;
       }
       sc[0] = a;
       sc[1] = b;
@@ -958,10 +960,10 @@ __global__ void __launch_bounds__(CG_THREADS, 1)
     __syncthreads();
     if (sc[2] != 0.0) break;
     const double alpha = sc[0], beta = sc[1];
-    if (threadIdx.x == 0) {
-      inv_g = 1.0 / gamma;
-      inv_ga = 1.0 / (gamma * alpha_t);
-    }
+    // the next iteration's 1/gamma and 1/(gamma alpha), on two other warps
+    // (each division is a chain of FP64 instructions on its warp's pipe)
+    if (threadIdx.x == 32) rcp_sh[0] = 1.0 / tot_sh[0];
+    if (threadIdx.x == 64) rcp_sh[1] = 1.0 / (tot_sh[0] * alpha);
     double *pnext = pub[(it + 1) & 1];
     acc[0] = acc[1] = acc[2] = 0.0;
     for (int t = threadIdx.x; t < nr; t += blockDim.x) {
