@@ -326,15 +326,20 @@ def _solve_timed(sys_, params, krylov, dev, profile=False):
     e2.record(stream)
     torch.cuda.synchronize()
     vc_bytes = vc_ms = 0.0
+    top = []
     if profile:
-        for r in amg.amg_profile_table(h):
+        table = amg.amg_profile_table(h)
+        for r in table:
             if r["kind"] in VCYCLE_KINDS:
                 vc_bytes += r["bytes"]
                 vc_ms += r["ms"]
+        for r in sorted(table, key=lambda r: -r["ms"])[:5]:
+            top.append({"kernel": f"{r['kind']}@{r['level']}", "ms": r["ms"],
+                        "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None})
     levels = h.sizes()
     h.close()
     return dict(setup_ms=e0.elapsed_time(e1), solve_ms=e1.elapsed_time(e2), info=info, x=x, levels=levels,
-                vc_bytes=vc_bytes, vc_ms=vc_ms)
+                vc_bytes=vc_bytes, vc_ms=vc_ms, top=top)
 
 
 def run_configs(dev, peak):
@@ -366,7 +371,8 @@ def run_configs(dev, peak):
              "status": amg.status_string(info.status),
              "iterations": info.iterations, "rel_res_true": info.rel_res_true,
              "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"],
-             "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None}
+             "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None,
+             "top_kernels_profiled_solve": p["top"]}
         if x_ref is not None:
             d["rel_diff_vs_fp64_solution"] = float(torch.linalg.vector_norm(r["x"] - x_ref) /
                                                    torch.linalg.vector_norm(x_ref))

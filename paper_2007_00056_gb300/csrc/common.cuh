@@ -284,7 +284,9 @@ amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cu
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
 amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
+#ifndef CG_THREADS
 #define CG_THREADS 512
+#endif
 #define CG_PART_DOUBLES (6 * AMG_MAX_BLOCKS + 32)
 #define CG_SMEM_CAP (200 * 1024)
 // Grid, block and shared-memory configuration of the coarse CG for n rows on

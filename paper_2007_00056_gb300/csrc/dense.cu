@@ -18,8 +18,9 @@
 //      row interchanges in reverse.
 //
 // The elimination costs 2 m^3 flops.  This GPU issues FP64 at about 1/66 of
-// its FP32 rate, so coarsest levels above GJ_FP64_MAX rows are inverted in
-// FP32 and each coarse solve refines in FP64 (r = f - A_L x, x += X r) a
+// its FP32 rate, so coarsest levels above GJ_FP64_MAX rows (where the FP64
+// inverse would take over about 25 ms) are inverted in FP32 and each coarse
+// solve refines in FP64 (r = f - A_L x, x += X r) a
 // number of times fixed here at setup by measuring the convergence on a test
 // vector; when the refinement does not reach FP64 accuracy the inverse is
 // recomputed in FP64.
@@ -27,7 +28,7 @@
 
 #define GJ_THREADS 1024
 #define GJ_SMEM_MAX 231000       // dynamic shared memory of the panel kernel
-#define GJ_FP64_MAX 1024         // largest coarsest level inverted in FP64 directly
+#define GJ_FP64_MAX 2048         // largest coarsest level inverted in FP64 directly
 #define GJ_TJ 256                // update kernel: columns per block (one per thread)
 #define GJ_TI 32                 // update kernel: rows per block
 #define GJ_REFINE_MAX 12         // refinement steps tried at setup

@@ -488,7 +488,9 @@ template amg_status dense_refined_solve<float>(amg_hierarchy *, const float *, f
 #define CG_RTOL 1e-12
 #define CG_MAXIT 1000
 #define CG_KEYS 258     // sort keys: row length 0..256, 257 for longer rows
+#ifndef CG_MAXQ
 #define CG_MAXQ 16      // neighbours a lane gathers in one round
+#endif
 #define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -639,6 +641,7 @@ __device__ __forceinline__ double cg_row_part(const int *cols, const double *val
     case 6: return cg_lane_dot<6>(cols, vals, stride, cnt, u, 0.0);
     case 7: return cg_lane_dot<7>(cols, vals, stride, cnt, u, 0.0);
     case 8: return cg_lane_dot<8>(cols, vals, stride, cnt, u, 0.0);
+#if CG_MAXQ >= 16
     case 9: return cg_lane_dot<9>(cols, vals, stride, cnt, u, 0.0);
     case 10: return cg_lane_dot<10>(cols, vals, stride, cnt, u, 0.0);
     case 11: return cg_lane_dot<11>(cols, vals, stride, cnt, u, 0.0);
@@ -647,6 +650,7 @@ __device__ __forceinline__ double cg_row_part(const int *cols, const double *val
     case 14: return cg_lane_dot<14>(cols, vals, stride, cnt, u, 0.0);
     case 15: return cg_lane_dot<15>(cols, vals, stride, cnt, u, 0.0);
     case 16: return cg_lane_dot<16>(cols, vals, stride, cnt, u, 0.0);
+#endif
     default: {
       double w = 0.0;
       for (int q0 = 0; q0 < wmax; q0 += CG_MAXQ)
@@ -1318,7 +1322,7 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
   for (int k = 0; k <= h->L; ++k) {
     Level &l = h->lev[k];
     l.tpr = choose_tpr(l);
-    l.fuse_pre = 1;
+    l.fuse_pre = 0;  // split first sweep and residual: the faster form at level 0 in every precision measured
     l.fuse_post = 0;
     size_t vd = sizeof(double) * (l.n + AMG_PAD), vf = sizeof(float) * (l.n + AMG_PAD);
     if (!mixed) {

@@ -2,7 +2,7 @@
 coarsest level solved exactly).
 
 The library inverts the coarsest matrix by blocked Gauss-Jordan elimination:
-in FP64 up to 1024 rows, above that in FP32 with FP64 refinement in every
+in FP64 up to 2048 rows, above that in FP32 with FP64 refinement in every
 coarse solve.  Either way the coarse solve must reach FP64 accuracy, so a
 one-level hierarchy's V-cycle equals the dense solve to 1e-12.
 """
@@ -19,10 +19,12 @@ pytestmark = pytest.mark.gpu
 CASES = [
     # (name, system, parameters): sizes chosen to hit both inversion paths
     ("poisson2d_32_fp64_m1024", lambda: W.poisson2d(32), dict(coarse_max=1024)),
+    ("random_spd_m1031_fp64_ragged_panels", lambda: W.random_spd(1031, 0.01, 5), dict(coarse_max=1031)),
+    ("convdiff2d_45_nonsymmetric_fp64_m2025", lambda: W.convdiff2d(45, peclet=300.0), dict(coarse_max=4096)),
     ("poisson2d_64_fp32_m4096", lambda: W.poisson2d(64), dict(coarse_max=4096)),
-    ("random_spd_m1031_ragged_panels", lambda: W.random_spd(1031, 0.01, 5), dict(coarse_max=1031)),
-    ("convdiff2d_45_nonsymmetric_m2025", lambda: W.convdiff2d(45, peclet=300.0), dict(coarse_max=4096)),
-    ("lognormal3d_14_m2744", lambda: W.lognormal3d(14, seed=3), dict(coarse_max=4096)),
+    ("random_spd_m2083_fp32_ragged_panels", lambda: W.random_spd(2083, 0.004, 6), dict(coarse_max=2083)),
+    ("convdiff2d_48_nonsymmetric_fp32_m2304", lambda: W.convdiff2d(48, peclet=300.0), dict(coarse_max=4096)),
+    ("lognormal3d_14_fp32_m2744", lambda: W.lognormal3d(14, seed=3), dict(coarse_max=4096)),
     ("aniso3d_20_two_levels", lambda: W.anisotropic3d(20), dict(coarse_max=2100)),
 ]
 
@@ -62,9 +64,9 @@ def test_dense_coarse_fp32_vcycle():
 
 
 def test_batched_solver_requires_fp64_inverse():
-    s = W.poisson2d(40)  # 1600 rows, one level: FP32 inverse
+    s = W.poisson2d(48)  # 2304 rows, one level: FP32 inverse
     rp, ci, val, b = to_cuda(s)
-    h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=2000))
+    h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=2400))
     x = torch.zeros_like(b)
     with pytest.raises(amg.AmgError):
         amg.amg_batch_pcg([h], [b], [x], rtol=1e-8)
