@@ -206,6 +206,15 @@ amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_p
  * error.  The device stays usable afterwards.  Synchronises the stream. */
 amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream);
 
+/* Self-test of the library's FP64 <-> FP32 conversions (the precision casts
+ * of the mixed-precision V-cycle compute them on the integer pipe): for the
+ * n doubles at d_in (device), writes d_f32[i] = d_in[i] rounded to FP32
+ * (round to nearest even) and d_f64[i] = d_f32[i] widened back to FP64, both
+ * by the library's conversion routines; the caller compares them with the
+ * hardware conversions.  Device pointers, n >= 0; AMG_ERR_INVALID_ARG for a
+ * null pointer with n > 0.  Asynchronous on `stream`. */
+amg_status amg_selftest_convert(int64_t n, const double *d_in, float *d_f32, double *d_f64, amg_stream_t stream);
+
 /* Kernel kinds reported by the per-kernel profiler.  Each kind is tracked per
  * level (0 = finest); Krylov kinds are reported at level 0. */
 typedef enum {

@@ -34,7 +34,7 @@ EXPORTS = (
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
-    "amg_selftest_wait_timeout", "amg_last_cuda_error",
+    "amg_selftest_wait_timeout", "amg_selftest_convert", "amg_last_cuda_error",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -117,6 +117,7 @@ def lib(build_if_missing: bool = False):
             l.amg_profile_read.argtypes = [vp, i32, i32, C.POINTER(d), C.POINTER(d), C.POINTER(C.c_longlong)]
             l.amg_autotune.argtypes = [vp, vp]
             l.amg_selftest_wait_timeout.argtypes = [i32, vp]
+            l.amg_selftest_convert.argtypes = [i64, vp, vp, vp, vp]
             l.amg_last_cuda_error.argtypes = []
             l.amg_last_cuda_error.restype = C.c_char_p
             l.amg_batch_pcg.argtypes = [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), d, i32, i32, vp,
@@ -371,6 +372,20 @@ def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible
     if st not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN):
         raise AmgError(st, "amg_batch_pcg")
     return list(infos)
+
+
+def amg_selftest_convert(x: torch.Tensor, stream=None):
+    """The library's FP64 -> FP32 -> FP64 conversions of a CUDA float64 tensor:
+    returns (x rounded to FP32, that widened back to FP64)."""
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise ValueError("x must be a CUDA float64 tensor")
+    x = x.contiguous()
+    f32 = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    f64 = torch.empty_like(x)
+    st = lib().amg_selftest_convert(x.numel(), x.data_ptr(), f32.data_ptr(), f64.data_ptr(), _stream(stream))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_selftest_convert")
+    return f32, f64
 
 
 def amg_selftest_wait_timeout(blocks: int = 8, stream=None) -> int:

@@ -125,12 +125,32 @@ __global__ void k_level_order(int n, const int32_t *__restrict__ rp, int32_t *__
 // ---------------------------------------------------------------------------
 // V-cycle kernels
 // ---------------------------------------------------------------------------
+// Streaming kernels walk the vectors in rounds of STREAM_U elements per thread
+// (i, i + S, i + 2S, ... for S threads in all): every load of a round is in
+// flight before the first store, and each load instruction stays coalesced.
+#define STREAM_U 4
+
 template <typename T>
 __global__ void k_jacobi0(int n, const T *__restrict__ f, const T *__restrict__ dinv, T omega, T *__restrict__ x,
                           const KState *st) {
   if (is_done(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    x[i] = omega * (dval(dinv, i) * f[i]);
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
+    T fv[STREAM_U], dv[STREAM_U];
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) {
+        fv[u] = f[i];
+        dv[u] = dval(dinv, (int)i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) x[i] = omega * (dv[u] * fv[u]);
+    }
+  }
 }
 
 // t = f - A x
@@ -351,8 +371,23 @@ __global__ void k_prolong(int n, const T *__restrict__ x, const int32_t *__restr
                           const float *__restrict__ sig, const float *__restrict__ isig_c, T *__restrict__ xout,
                           const KState *st) {
   if (is_done(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    xout[i] = x[i] + coarse_corr(xc, agg, sig, isig_c, i);
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
+    T xv[STREAM_U], cv[STREAM_U];
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) {
+        xv[u] = x[i];
+        cv[u] = coarse_corr(xc, agg, sig, isig_c, (int)i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) xout[i] = xv[u] + cv[u];
+    }
+  }
 }
 
 // f_c[I] = sum of t over the members of I, members ascending (each term times
@@ -375,18 +410,76 @@ __global__ void k_restrict(int nc, const int32_t *__restrict__ mrp, const int32_
 }
 
 // b = (B)(a * scale) with an optional per-entry scale
+// FP64 <-> FP32 conversions on the integer pipe.  The conversion instructions
+// issue on GB300's FP64 pipe (about one per clock per SM), which made the
+// precision casts of the V-cycle FP64-bound; these compute the same IEEE
+// results from the bit patterns for normal numbers (round to nearest even
+// for FP64 -> FP32) and leave zeros, subnormals, infinities and NaNs to the
+// instruction.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;  // FP32 biased exponent
+  if (e < 1 || e > 254) return (float)x;                 // outside the FP32 normal range
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  unsigned m = (unsigned)(mant >> 29);
+  const unsigned long long rem = mant & 0x1fffffffull, half = 0x10000000ull;
+  unsigned r = ((unsigned)e << 23) + m;  // exponent and mantissa, a carry moves into the exponent
+  if (rem > half || (rem == half && (m & 1u))) ++r;
+  if ((r >> 23) >= 255u) return (float)x;  // rounded up into the infinity range
+  return __uint_as_float(r | ((unsigned)(b >> 63) << 31));
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 255u) return (double)x;  // zero, subnormal, infinity, NaN
+  const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                               ((unsigned long long)(e - 127u + 1023u) << 52) |
+                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ float to_f32(double x) { return f64_to_f32(x); }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+
+// b = a (times scale in FP32 when given), converted to B.
 template <typename A, typename B>
 __global__ void k_cast_scale(int n, const A *__restrict__ a, const float *__restrict__ scale, B *__restrict__ b,
                              const KState *st) {
   if (is_done(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    b[i] = scale ? (B)(a[i] * (A)scale[i]) : (B)a[i];
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
+    float av[STREAM_U];
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) av[u] = scale ? to_f32(a[i]) * scale[i] : to_f32(a[i]);
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) b[i] = std::is_same<B, double>::value ? (B)to_f64(av[u]) : (B)av[u];
+    }
+  }
 }
 
 template <typename A, typename B>
 __global__ void k_cast(int n, const A *__restrict__ a, B *__restrict__ b, const KState *st) {
   if (is_done(st)) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (B)a[i];
+  const long long S = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
+    A av[STREAM_U];
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) av[u] = a[i];
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      if (i < n) b[i] = (B)av[u];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -398,10 +491,25 @@ __global__ void k_gemv_dense(int m, const double *__restrict__ ainv, const T *__
   if (is_done(st)) return;
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  // rows read as double2 when every row starts on 16 bytes (two partial sums
+  // per lane), else one element at a time
+  const bool vec = (m % 2) == 0 && ((uintptr_t)ainv & 15) == 0;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
     const double *row = ainv + (size_t)i * m;
     double s = 0.0;
-    for (int j = lane; j < m; j += 32) s += __ldg(&row[j]) * (double)__ldg(&f[j]);
+    if (vec) {
+      const double2 *row2 = (const double2 *)row;
+      double s1 = 0.0;
+#pragma unroll 4
+      for (int q = lane; q < m / 2; q += 32) {
+        const double2 a = __ldg(&row2[q]);
+        s = __fma_rn(a.x, (double)__ldg(&f[2 * q]), s);
+        s1 = __fma_rn(a.y, (double)__ldg(&f[2 * q + 1]), s1);
+      }
+      s += s1;
+    } else {
+      for (int j = lane; j < m; j += 32) s += __ldg(&row[j]) * (double)__ldg(&f[j]);
+    }
     s = warp_sum(s);
     if (lane == 0) x[i] = (T)s;
   }
@@ -416,30 +524,49 @@ __global__ void k_gemv32(int m, const float *__restrict__ X, const V *__restrict
   if (is_done(st)) return;
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
+  // rows read as float4 when every row starts on 16 bytes (four partial sums
+  // per lane), else one element at a time
+  const bool vec = (m % 4) == 0 && ((uintptr_t)X & 15) == 0;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
     const float *row = X + (size_t)i * m;
     float s = 0.0f;
-    for (int j = lane; j < m; j += 32) s = fmaf(__ldg(&row[j]), (float)v[j], s);
+    if (vec) {
+      const float4 *row4 = (const float4 *)row;
+      float s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll 4
+      for (int q = lane; q < m / 4; q += 32) {
+        const float4 a = __ldg(&row4[q]);
+        s = fmaf(a.x, (float)v[4 * q], s);
+        s1 = fmaf(a.y, (float)v[4 * q + 1], s1);
+        s2 = fmaf(a.z, (float)v[4 * q + 2], s2);
+        s3 = fmaf(a.w, (float)v[4 * q + 3], s3);
+      }
+      s = (s + s1) + (s2 + s3);
+    } else {
+      for (int j = lane; j < m; j += 32) s = fmaf(__ldg(&row[j]), (float)v[j], s);
+    }
     s = warp_sum(s);
     if (lane == 0) {
-      const double xi = (add ? xw[i] : 0.0) + (double)s;
+      const double xi = (add ? xw[i] : 0.0) + to_f64(s);
       xw[i] = xi;
       if (xout) xout[i] = (T)xi;
     }
   }
 }
 
-// r = f - A_L xw in FP64 (the refinement residual).
+// r = f - A_L xw, summed in FP64 and stored in FP32 for the product with X
+// (xw = null: r = f); one conversion per row instead of one per product.
 template <typename T>
 __global__ void k_dense_resid(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                               const double *__restrict__ val, const T *__restrict__ f, const double *__restrict__ xw,
-                              double *__restrict__ r, const KState *st) {
+                              float *__restrict__ r, const KState *st) {
   if (is_done(st)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
-  double s = (double)f[i];
-  for (int e = rp[i]; e < rp[i + 1]; ++e) s = __fma_rn(-val[e], xw[ci[e]], s);
-  r[i] = s;
+  double s = to_f64(f[i]);
+  if (xw)
+    for (int e = rp[i]; e < rp[i + 1]; ++e) s = __fma_rn(-val[e], xw[ci[e]], s);
+  r[i] = f64_to_f32(s);
 }
 
 // x = X f refined `steps` times: xw += X (f - A_L xw).
@@ -447,14 +574,14 @@ template <typename T>
 amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st) {
   const Level &c = h->lev[h->L];
   const int m = c.n;
-  double *r = h->dense_r, *xw = h->dense_r + (m + AMG_PAD);
+  float *r = (float *)h->dense_r;
+  double *xw = h->dense_r + (m + AMG_PAD);
   const int grid = grid_for((long long)m * 32, AMG_THREADS);
-  k_gemv32<T, T><<<grid, AMG_THREADS, 0, s>>>(m, h->ainv32, f, xw, 0, steps == 0 ? x : nullptr, st);
-  count_launch();
-  for (int k = 1; k <= steps; ++k) {
-    k_dense_resid<T><<<cdiv(m, AMG_THREADS), AMG_THREADS, 0, s>>>(m, c.rp, c.ci, c.val, f, xw, r, st);
+  for (int k = 0; k <= steps; ++k) {
+    k_dense_resid<T><<<cdiv(m, AMG_THREADS), AMG_THREADS, 0, s>>>(m, c.rp, c.ci, c.val, f, k ? xw : nullptr, r,
+                                                                 st);
     count_launch();
-    k_gemv32<double, T><<<grid, AMG_THREADS, 0, s>>>(m, h->ainv32, r, xw, 1, k == steps ? x : nullptr, st);
+    k_gemv32<float, T><<<grid, AMG_THREADS, 0, s>>>(m, h->ainv32, r, xw, k ? 1 : 0, k == steps ? x : nullptr, st);
     count_launch();
   }
   return amg_cuda_status(cudaGetLastError());
@@ -1622,6 +1749,24 @@ __global__ void k_wait_selftest(unsigned *bar, unsigned *eflags, long long limit
   gb.limit = limit;
   const bool ok = gb.sync(gridDim.x + 1, eflags, &fail_sh);
   if (threadIdx.x == 0) atomicAdd(out, ok ? 0 : 1);
+}
+
+__global__ void k_selftest_convert(long long n, const double *__restrict__ in, float *__restrict__ f32,
+                                   double *__restrict__ f64) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float f = f64_to_f32(in[i]);
+    f32[i] = f;
+    f64[i] = f32_to_f64(f);
+  }
+}
+
+extern "C" amg_status amg_selftest_convert(int64_t n, const double *d_in, float *d_f32, double *d_f64,
+                                           amg_stream_t stream) {
+  if (n < 0 || (n > 0 && (!d_in || !d_f32 || !d_f64))) return AMG_ERR_INVALID_ARG;
+  if (n == 0) return AMG_OK;
+  k_selftest_convert<<<grid_for(n, AMG_THREADS), AMG_THREADS, 0, (cudaStream_t)stream>>>(n, d_in, d_f32, d_f64);
+  count_launch();
+  return amg_cuda_status(cudaGetLastError());
 }
 
 extern "C" amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream) {
