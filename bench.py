@@ -36,7 +36,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) per launch of the coarse CG kernel on this
 # workload, from one ncu capture of the current kernel
 # (profiles/coarse_cg_lognormal3d_128.md); None once the kernel changes
-COARSE_CG_DRAM_BYTES = None
+COARSE_CG_DRAM_BYTES = 10578432 + 87040
 
 
 def parse_args():
