@@ -150,7 +150,7 @@ __global__ void k_hem_pick(int nd_host, const int *nd_dev, const int *prev_match
 // and D_{r+1} (cnt[1], stamp r + 1) is every node of D_r that picked but was
 // not matched -- a superset of the dirty set, so incremental rounds may
 // follow.  Cheaper than the dirty pass in the first rounds, where most pairs
-// form; the host keeps them while a round pairs at least a quarter of its
+// form; the host keeps them while a round pairs at least a sixteenth of its
 // list and switches to incremental rounds for good after the first one that
 // does not (a narrow front advancing through a uniform grid).
 __global__ void k_hem_match(int nd_host, const int *nd_dev, const int *prev_matched, const int32_t *__restrict__ D,
@@ -675,7 +675,7 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
     for (int b = 0; b < batch; ++b) {
       ++r;
       if (S.host[2 * b] == 0) { finished = true; break; }
-      if (frontier_rounds && 4ll * S.host[2 * b] < (long long)nd) frontier_rounds = false;
+      if (frontier_rounds && 16ll * S.host[2 * b] < (long long)nd) frontier_rounds = false;
       nd = S.host[2 * b + 1];
     }
     fa = ba;
