@@ -33,6 +33,7 @@ WORKLOAD = "lognormal3d_128: 3D 7-pt FV diffusion, 128^3 cells, lognormal(0,1) c
 RTOL = 1e-8
 # FP64 peak of GB300: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+HBM_SPEC_GBS = 7900.0  # GB300 HBM3e nominal; the measured copy bandwidth is the primary denominator
 # DRAM bytes (read + write) per launch of the coarse CG kernel on this
 # workload, from one ncu capture of the current kernel
 # (profiles/coarse_cg_lognormal3d_128.md); None once the kernel changes
@@ -275,7 +276,9 @@ def run_serving(reqs, systems):
     dev = torch.device("cuda", torch.cuda.current_device())
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    per_request = []
     for s in systems:
+        tr = time.perf_counter()
         rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
         # the server's hierarchy shape (coarsest size) in plain FP64
         h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=256 if s.n <= 60000 else 1024))
@@ -283,7 +286,13 @@ def run_serving(reqs, systems):
         amg.pcg_solve(h, b, x, rtol=RTOL, flexible=not h.sizes()[-1] <= 4096)
         x.cpu()
         h.close()
+        per_request.append(time.perf_counter() - tr)
     plain = time.perf_counter() - t0
+    # the plain method serving the same arrivals one request at a time
+    done, plain_lat = 0.0, []
+    for rq, t in zip(reqs, per_request):
+        done = max(done, rq.arrival_s) + t
+        plain_lat.append((done - rq.arrival_s) * 1e3)
     lat = S.latency_summary(res)
     return {
         "requests": len(reqs), "unknowns_total": int(total_n), "converged_1e-8": int(ok),
@@ -293,6 +302,8 @@ def run_serving(reqs, systems):
         "capacity_solves_per_s": len(reqs) / wall_cap,
         "capacity_p50_ms": S.latency_summary(res_cap)["p50_ms"],
         "plain_fp64_sequential_solves_per_s": len(reqs) / plain,
+        "plain_fp64_sequential_p50_ms": float(np.percentile(plain_lat, 50)),
+        "plain_fp64_sequential_p99_ms": float(np.percentile(plain_lat, 99)),
         "batched_requests": int(stats.get("batched", 0)), "batches": int(stats.get("batches", 0)),
         "precision": "fp32 V-cycle, fp64 flexible PCG",
     }
@@ -382,7 +393,7 @@ def run_configs(dev, peak):
     """The other workloads of the method, measured on this GPU: the 256^3
     anisotropic system in FP64 and both mixed-precision forms (flexible PCG),
     the 2048^2 upwind convection-diffusion system with BiCGStab (FP32 V-cycle,
-    FP64 outer) at three Peclet numbers, and the 64^2 Poisson system.  Each
+    FP64 outer) at three Peclet numbers, and the 64^2 Poisson system (coarsest level 64 rows).  Each
     line: setup and solve time (a second solve after one untimed warm-up),
     iterations, true relative residual, V-cycle GB/s from the library's event
     profiler (a third, profiled solve) and, for the mixed-precision forms, the
@@ -394,8 +405,8 @@ def run_configs(dev, peak):
 
     out = []
 
-    def line(name, sys_, prec, krylov, x_ref=None):
-        params = amg.amg_default_params(precision=prec)
+    def line(name, sys_, prec, krylov, x_ref=None, **kw):
+        params = amg.amg_default_params(precision=prec, **kw)
         _solve_timed(sys_, params, krylov, dev)
         r = _solve_timed(sys_, params, krylov, dev)
         p = _solve_timed(sys_, params, krylov, dev, profile=True)
@@ -408,6 +419,7 @@ def run_configs(dev, peak):
              "iterations": info.iterations, "rel_res_true": info.rel_res_true,
              "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"],
              "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None,
+             "vcycle_frac_of_spec": (gbs / HBM_SPEC_GBS) if gbs else None,
              "vcycle_ms": p["vc_cycle_ms"], "vcycle_coarsest_share": p["vc_coarse_share"],
              "top_kernels_profiled_solve": p["top"]}
         if x_ref is not None:
@@ -425,7 +437,9 @@ def run_configs(dev, peak):
         s4 = W.config_convdiff2d_2048(peclet=pe)
         line(f"convdiff2d_2048 upwind Pe={pe:g}", s4, amg.AMG_FP32, "bicgstab")
         del s4
-    line("poisson2d_64", W.config_poisson2d_64(), amg.AMG_FP64, "pcg")
+    # the 64^2 Poisson configuration coarsens to 64 rows (4096 -> 1024 -> 256 -> 64); with the
+    # library's default stop size (4096) it would be a single dense level, a direct solve
+    line("poisson2d_64 coarse_max=64", W.config_poisson2d_64(), amg.AMG_FP64, "pcg", coarse_max=64)
     torch.cuda.empty_cache()
     return out
 
@@ -590,7 +604,7 @@ def main():
     for r in table:
         if r["level"] == 0 and r["kind"] in ("jacobi", "residual", "prolong_jacobi", "krylov_spmv") and r["ms"] > 0:
             g = r["bytes"] / (r["ms"] * 1e-3) / 1e9
-            hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak})
+            hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak, "frac_of_spec": g / HBM_SPEC_GBS})
     kernels = [dict(kernel=f"{r['kind']}@{r['level']}", ms_per_step=r["ms"] / args.profile_steps,
                     launches_per_step=r["launches"] / args.profile_steps,
                     gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:12]]
@@ -656,7 +670,9 @@ def main():
             "time_to_solution_ms": ms_per_step, "setup_ms": setup_mean, "solve_ms": solve_mean,
             "iterations": iters[0],
             "vcycle": {"gbs": vc_rate[0], "ms_per_cycle": vc_rate[1], "peak": peak,
-                       "frac": vc_rate[0] / peak if vc_rate[0] else None, "coarsest_share": vc_rate[2],
+                       "frac": vc_rate[0] / peak if vc_rate[0] else None,
+                       "frac_of_spec": vc_rate[0] / HBM_SPEC_GBS if vc_rate[0] else None,
+                       "coarsest_share": vc_rate[2],
                        "note": "algorithmic bytes of one V-cycle over the time of ten V-cycles run with the "
                                "profiler off; the coarsest solve (CG from shared memory) is not HBM-bound"},
             "roofline": roofline, "hbm_level0": hbm_level0, "kernels": kernels,

@@ -69,7 +69,13 @@ typedef enum { AMG_COARSE_AUTO = 0, AMG_COARSE_DENSE = 1, AMG_COARSE_CG = 2 } am
  *   omega        damped-Jacobi weight of the smoother S_k (2/3)
  *   nu_pre, nu_post  pre- and post-smoothing sweeps (1, 1; Table 2 uses 6, 6)
  *   coarse_solver    AMG_COARSE_AUTO: dense if the coarsest level has <= coarse_max
- *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2)
+ *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2).
+ *                The dense solve applies the inverse formed at setup by blocked
+ *                Gauss-Jordan elimination with partial pivoting: in FP64 up to
+ *                2048 rows; above that in FP32 with a fixed number of FP64
+ *                refinement steps per solve (x += X (f - A x)), chosen at setup
+ *                so the result has FP64 accuracy (FP64 inverse if refinement
+ *                cannot reach it)
  *   precision    value storage / arithmetic of the V-cycle (outer Krylov is FP64) */
 typedef struct {
   int passes;
@@ -143,7 +149,8 @@ amg_status bicgstab_solve(const amg_hierarchy *h, const double *d_b, double *d_x
  * system, each running its whole solve (same arguments and stopping rule as
  * pcg_solve, applied per system).  hs[i] is the hierarchy of system i (each
  * hierarchy at most once per call; every hierarchy must have a dense
- * coarsest level of at most 2048 rows and the same precision, FP64 or FP32;
+ * coarsest level of at most 2048 rows (an FP64 inverse) and the same
+ * precision, FP64 or FP32;
  * AMG_ERR_UNSUPPORTED otherwise); d_b[i], d_x[i] are its device right-hand
  * side and initial guess / solution.  Block reductions only: the result of a
  * system does not depend on the rest of the batch.  infos (host, length nsys,
