@@ -263,7 +263,10 @@ def run_serving(reqs, systems):
     from paper_2007_00056_gb300 import amg
     from paper_2007_00056_gb300 import serving as S
 
+    import inspect
+
     total_n = sum(s.n for s in systems)
+    srv_defaults = {k: v.default for k, v in inspect.signature(S.SolveServer).parameters.items()}
     srv = S.SolveServer()
     res, wall = S.serve_stream(srv, reqs, systems)
     stats = dict(srv.stats)
@@ -281,7 +284,8 @@ def run_serving(reqs, systems):
         tr = time.perf_counter()
         rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
         # the server's hierarchy shape (coarsest size) in plain FP64
-        h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=256 if s.n <= 60000 else 1024))
+        cm = srv_defaults["batch_coarse_max"] if s.n <= srv_defaults["small_max_n"] else srv_defaults["big_coarse_max"]
+        h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=cm))
         x = torch.zeros_like(b)
         amg.pcg_solve(h, b, x, rtol=RTOL, flexible=not h.sizes()[-1] <= 4096)
         x.cpu()

@@ -16,7 +16,11 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    became ready within a short window, again and again, so requests that
    become ready while a batch runs join the next one, and batches overlap
    with each other and with the large solves on the worker streams.  Larger
-   requests run ``pcg_solve`` on their worker's stream.  Their hierarchies
+   requests run ``pcg_solve`` on their worker's stream, with the whole GPU:
+   one thread block per system only pays for really small systems (on the
+   200/s benchmark stream, batching systems of up to 5000 rows served 124
+   requests/s against 98/s when systems of up to 60000 rows were batched).
+   Their hierarchies
    stop at 1024 rows (``big_coarse_max``) rather than the library's 4096:
    the dense inverse of the coarsest level costs 2 N_L^3 FP64 operations,
    which at 4096 rows is over a hundred milliseconds of FP64 work on a
@@ -91,7 +95,7 @@ class _Entry:
 
 class SolveServer:
     def __init__(self, device: int = 0, memory_budget: int | None = None, precision: int = amg.AMG_FP32,
-                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 12, small_max_n: int = 60000,
+                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 12, small_max_n: int = 5000,
                  batch_coarse_max: int = 256, big_coarse_max: int = 1024, max_batch: int = 256,
                  cache_entries: int = 64, batchers: int = 2, batch_window_s: float = 0.001):
         self.dev = torch.device("cuda", device)
