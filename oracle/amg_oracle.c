@@ -31,7 +31,15 @@
  *  - the coarsest solve of Algorithm 1 is A_L^{-1} f_L by dense LU with partial
  *    pivoting, or, when A_L is too large for a dense factor, Jacobi-PCG to a
  *    relative residual of 1e-12 (the CG coarse solver of Sec. 4.2), written
- *    in the Chronopoulos-Gear arrangement of CG.
+ *    in the Chronopoulos-Gear arrangement of CG;
+ *  - the W- and F-cycles, which Sec. 2 and Sec. 3 only name, take their
+ *    textbook form: the coarse correction of level k is gamma = 2 cycles of
+ *    level k+1 (W), or one F-cycle then one V-cycle of level k+1 (F), the
+ *    first from a zero guess and the second from the first one's result; the
+ *    coarsest level is solved once per coarse correction;
+ *  - AMG as a solver (Sec. 3.1, Sec. 4.2) is the stationary iteration
+ *    x_{j+1} = x_j + M^{-1}(b - A x_j) with M^{-1} one cycle from a zero
+ *    guess, stopping once ||b - A x_j|| <= rtol ||b||.
  */
 #include <math.h>
 #include <stdint.h>
@@ -348,6 +356,7 @@ typedef struct {
   double stall_ratio, omega;
   int nu_pre, nu_post, coarse_solver; /* 0 auto, 1 dense LU, 2 CG */
   int matcher;                        /* 0 greedy EHEM order, 1 literal rounds */
+  int cycle;                          /* 0 V, 1 W, 2 F (Sec. 2 names all three) */
 } orc_params;
 
 typedef struct {
@@ -459,6 +468,7 @@ void orc_default_params(orc_params *p) {
   p->nu_post = 1;
   p->coarse_solver = 0;
   p->matcher = 0;
+  p->cycle = 0;
 }
 
 void orc_destroy(orc_hier *h) {
@@ -655,14 +665,18 @@ static void jacobi_sweep(const orc_level *l, double omega, const double *f, doub
   for (int i = 0; i < l->n; ++i) x[i] = x[i] + omega * (f[i] - t[i]) / l->diag[i];
 }
 
-/* V-cycle(k, f_k, x_k = 0, A_k) of Algorithm 1. */
-static void vcycle(orc_hier *h, int k, const double *f, double *x) {
+/* Multigrid cycle of level k on A_k x = f_k (Algorithm 1 and its W- and
+ * F-cycle variants).  zero_guess = 1 starts from x_k = 0 as Algorithm 1
+ * does; zero_guess = 0 starts from the x passed in.  kind: 0 V, 1 W, 2 F.
+ * The coarsest level is solved, not cycled, and ignores the guess. */
+static void mg_cycle(orc_hier *h, int k, const double *f, double *x, int kind, int zero_guess) {
   if (k == h->L) { coarse_solve(h, f, x); return; }
   const orc_level *l = &h->lev[k];
   const orc_params *p = &h->prm;
   double *t = h->t[k];
-  /* presmoothing from the zero initial guess */
-  for (int i = 0; i < l->n; ++i) x[i] = 0.0;
+  /* presmoothing */
+  if (zero_guess)
+    for (int i = 0; i < l->n; ++i) x[i] = 0.0;
   for (int s = 0; s < p->nu_pre; ++s) jacobi_sweep(l, p->omega, f, x, t);
   /* residual r_k = f_k - A_k x_k */
   orc_spmv(l->n, l->rp, l->ci, l->val, x, t);
@@ -677,18 +691,22 @@ static void vcycle(orc_hier *h, int k, const double *f, double *x) {
     else fc[I] = fc[I] + t[i];
   }
   free(seen);
-  /* coarse correction: recursion with zero initial guess, or the exact solve */
-  vcycle(h, k + 1, fc, xc);
+  /* coarse correction x_{k+1} ~ A_{k+1}^{-1} f_{k+1}: the exact solve at the
+   * coarsest level, else one (V), two (W) or an F- then a V- (F) cycle of
+   * level k+1, the first from zero, the second from the first one's result */
+  mg_cycle(h, k + 1, fc, xc, kind, 1);
+  if (k + 1 < h->L && kind == 1) mg_cycle(h, k + 1, fc, xc, 1, 0);
+  if (k + 1 < h->L && kind == 2) mg_cycle(h, k + 1, fc, xc, 0, 0);
   /* prolongation x_k += P_k x_{k+1} */
   for (int i = 0; i < l->n; ++i) x[i] = x[i] + xc[l->agg[i]];
   /* postsmoothing */
   for (int s = 0; s < p->nu_post; ++s) jacobi_sweep(l, p->omega, f, x, t);
 }
 
-/* z = M^{-1} r: one V-cycle from the zero guess (the preconditioner of
- * Algorithms 4 and 5). */
+/* z = M^{-1} r: one cycle of the configured kind from the zero guess (the
+ * preconditioner of Algorithms 4 and 5; a V-cycle by default). */
 int orc_vcycle(orc_hier *h, const double *r, double *z) {
-  vcycle(h, 0, r, z);
+  mg_cycle(h, 0, r, z, h->prm.cycle, 1);
   return ORC_OK;
 }
 
@@ -772,6 +790,49 @@ int orc_pcg(orc_hier *h, const double *b, double *x, double rtol, int max_iter, 
   info->rel_res_true = true_rel_res(l, b, x, bn);
   info->status = st;
   free(r); free(rold); free(z); free(p); free(q);
+  return st;
+}
+
+/* AMG as a solver (Sec. 3.1, Sec. 4.2): the stationary iteration
+ * x_{j+1} = x_j + M^{-1}(b - A x_j), M^{-1} one cycle of the configured kind
+ * from the zero guess.  x holds x_0 on entry.  Stops once
+ * ||b - A x_j|| <= rtol ||b|| (the residual recomputed from x_j after every
+ * cycle) or after max_iter cycles. */
+int orc_amg_solve(orc_hier *h, const double *b, double *x, double rtol, int max_iter, orc_info *info) {
+  const orc_level *l = &h->lev[0];
+  int n = l->n;
+  double *r = (double *)malloc((size_t)n * sizeof(double));
+  double *z = (double *)malloc((size_t)n * sizeof(double));
+  double bn = norm2(n, b);
+  info->iterations = 0;
+  info->status = ORC_OK;
+  if (bn == 0.0) {
+    for (int i = 0; i < n; ++i) x[i] = 0.0;
+    info->rel_res_recurrence = info->rel_res_true = 0.0;
+    free(r); free(z);
+    return ORC_OK;
+  }
+  orc_spmv(n, l->rp, l->ci, l->val, x, r);
+  for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+  double rel = norm2(n, r) / bn;
+  int st = rel <= rtol ? ORC_OK : ORC_ERR_NOT_CONVERGED;
+  int it = 0;
+  while (st != ORC_OK && it < max_iter) {
+    orc_vcycle(h, r, z);
+    for (int i = 0; i < n; ++i) x[i] = x[i] + z[i];
+    orc_spmv(n, l->rp, l->ci, l->val, x, r);
+    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];
+    ++it;
+    rel = norm2(n, r) / bn;
+    if (rel <= rtol) st = ORC_OK;
+    else if (!isfinite(rel)) st = ORC_ERR_BREAKDOWN;
+    if (st == ORC_ERR_BREAKDOWN) break;
+  }
+  info->iterations = it;
+  info->rel_res_recurrence = rel;
+  info->rel_res_true = rel;
+  info->status = st;
+  free(r); free(z);
   return st;
 }
 

@@ -38,7 +38,8 @@ def build(force: bool = False) -> str:
 
 class Params(C.Structure):
     """Oracle parameters; defaults follow the method's configuration (2 pairwise
-    passes, damped Jacobi omega = 2/3 with one pre and one post sweep)."""
+    passes, damped Jacobi omega = 2/3 with one pre and one post sweep, V-cycle;
+    cycle = 1 selects the W-cycle, 2 the F-cycle)."""
 
     _fields_ = [
         ("passes", C.c_int),
@@ -50,6 +51,7 @@ class Params(C.Structure):
         ("nu_post", C.c_int),
         ("coarse_solver", C.c_int),
         ("matcher", C.c_int),
+        ("cycle", C.c_int),
     ]
 
     def __init__(self, **kw):
@@ -98,6 +100,7 @@ def lib():
             l.orc_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
             l.orc_pcg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.c_int, C.POINTER(_Info)]
             l.orc_bicgstab.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.POINTER(_Info)]
+            l.orc_amg_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.POINTER(_Info)]
             _lib = l
     return _lib
 
@@ -193,7 +196,8 @@ class SolveInfo:
 
 
 class Hierarchy:
-    """Oracle AMG hierarchy (setup phase) with V-cycle, PCG and BiCGStab."""
+    """Oracle AMG hierarchy (setup phase) with its cycle (V, W or F), AMG as a
+    solver, PCG and BiCGStab."""
 
     def __init__(self, rp, ci, val, params: Params | None = None, **kw):
         self._rp, self._ci, self._val = _csr(rp, ci, val)
@@ -247,6 +251,7 @@ class Hierarchy:
         return [self.level_info(k)[0] for k in range(self.num_levels)]
 
     def vcycle(self, r):
+        """z = M^{-1} r: one cycle of the configured kind (V, W or F) from zero."""
         z = np.empty(self.n)
         lib().orc_vcycle(self._h, np.ascontiguousarray(r, dtype=np.float64), z)
         return z
@@ -256,6 +261,14 @@ class Hierarchy:
         info = _Info()
         lib().orc_pcg(self._h, np.ascontiguousarray(b, dtype=np.float64), x, rtol, max_iter,
                       int(flexible), C.byref(info))
+        return x, SolveInfo(info)
+
+    def amg_solve(self, b, x0=None, rtol=1e-8, max_iter=1000):
+        """AMG as a solver: x_{j+1} = x_j + M^{-1}(b - A x_j) until the tolerance."""
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64)
+        info = _Info()
+        lib().orc_amg_solve(self._h, np.ascontiguousarray(b, dtype=np.float64), x, rtol, max_iter,
+                            C.byref(info))
         return x, SolveInfo(info)
 
     def bicgstab(self, b, x0=None, rtol=1e-8, max_iter=1000):

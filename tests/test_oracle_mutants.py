@@ -36,6 +36,16 @@ MUTANTS = [
      "alpha = gamma_new / delta;", "test_coarse_cg_finite_termination_two_eigenvalues"),
     ("lu_no_pivoting", "if (fabs(a[(size_t)i * n + k]) > best)", "if (0 && fabs(a[(size_t)i * n + k]) > best)",
      "test_dense_lu_matches_numpy"),
+    ("w_second_cycle_from_zero", "kind == 1) mg_cycle(h, k + 1, fc, xc, 1, 0);",
+     "kind == 1) mg_cycle(h, k + 1, fc, xc, 1, 1);", "test_cycles_match_error_propagation_recursion"),
+    ("w_single_coarse_cycle", "if (k + 1 < h->L && kind == 1)", "if (0 && k + 1 < h->L && kind == 1)",
+     "test_cycles_match_error_propagation_recursion"),
+    ("f_second_cycle_is_f", "kind == 2) mg_cycle(h, k + 1, fc, xc, 0, 0);",
+     "kind == 2) mg_cycle(h, k + 1, fc, xc, 2, 0);", "test_cycles_match_error_propagation_recursion"),
+    ("amg_solver_correction_sign", "x[i] = x[i] + z[i];", "x[i] = x[i] - z[i];",
+     "test_amg_solver_iterates_closed_form"),
+    ("amg_solver_stale_residual", "    orc_spmv(n, l->rp, l->ci, l->val, x, r);\n    for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];\n    ++it;",
+     "    ++it;", "test_amg_solver_iterates_closed_form"),
 ]
 
 

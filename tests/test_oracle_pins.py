@@ -441,3 +441,152 @@ def test_coarse_cg_finite_termination_two_eigenvalues():
     z = h.vcycle(s.b)
     assert h.last_coarse_cg_iters <= 2
     np.testing.assert_allclose(z, np.linalg.solve(a, s.b), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# W- and F-cycles (Sec. 2 names V, W and F) and AMG as a solver (Sec. 3.1)
+# --------------------------------------------------------------------------
+
+def _levels_dense(h):
+    """Dense A_k and P_k of an oracle hierarchy (the setup is pinned above)."""
+    As, Ps = [], []
+    for k in range(h.num_levels):
+        rp, ci, val, agg = h.level(k)
+        n = len(rp) - 1
+        As.append(_dense(rp, ci, val, n))
+        if agg is not None:
+            Ps.append(_P(agg, h.level_info(k + 1)[0]))
+    return As, Ps
+
+
+def _error_propagators(As, Ps, omega=2.0 / 3.0, nu_pre=1, nu_post=1):
+    """Textbook multigrid recursion of the error propagator of one cycle at
+    level k: E_k = S_k^nu_post (I - P_k C_{k+1} P_k^T A_k) S_k^nu_pre with
+    S_k = I - omega D_k^{-1} A_k and C_{k+1} the coarse approximate inverse:
+    A_L^{-1} at the coarsest level, else (I - E_{k+1}) A_{k+1}^{-1} (V),
+    (I - E_{k+1}^2) A_{k+1}^{-1} (W: two cycles, the second from the first's
+    result) or (I - E^V_{k+1} E^F_{k+1}) A_{k+1}^{-1} (F: an F-cycle, then a
+    V-cycle).  Returns {kind: E_0} for kind 0 (V), 1 (W), 2 (F)."""
+    L = len(As) - 1
+    E = {0: [None] * (L + 1), 1: [None] * (L + 1), 2: [None] * (L + 1)}
+    for k in range(L - 1, -1, -1):
+        A = As[k]
+        n = A.shape[0]
+        S = np.eye(n) - omega * A / np.diag(A)[:, None]
+        Ac_inv = np.linalg.inv(As[k + 1])
+        for kind in (0, 1, 2):
+            if k + 1 == L:
+                C = Ac_inv
+            elif kind == 0:
+                C = (np.eye(len(Ac_inv)) - E[0][k + 1]) @ Ac_inv
+            elif kind == 1:
+                C = (np.eye(len(Ac_inv)) - E[1][k + 1] @ E[1][k + 1]) @ Ac_inv
+            else:
+                C = (np.eye(len(Ac_inv)) - E[0][k + 1] @ E[2][k + 1]) @ Ac_inv
+            P = Ps[k]
+            E[kind][k] = (np.linalg.matrix_power(S, nu_post) @ (np.eye(n) - P @ C @ P.T @ A)
+                          @ np.linalg.matrix_power(S, nu_pre))
+    return {kind: E[kind][0] for kind in (0, 1, 2)}
+
+
+_CYCLE_SYSTEMS = [
+    ("poisson2d_16_four_levels", lambda: W.poisson2d(16), 4),
+    ("lognormal3d_6", lambda: W.lognormal3d(6, seed=5), 8),
+    ("convdiff2d_14_nonsymmetric", lambda: W.convdiff2d(14, peclet=200.0), 6),
+]
+
+
+@pytest.mark.parametrize("name,make,coarse_max", _CYCLE_SYSTEMS, ids=[c[0] for c in _CYCLE_SYSTEMS])
+def test_cycles_match_error_propagation_recursion(name, make, coarse_max):
+    """M^{-1} of each cycle kind equals (I - E_0) A^{-1} of the textbook
+    recursion; needs at least four levels so that W and F differ."""
+    s = make()
+    A = s.dense()
+    Ms = {}
+    for kind in (0, 1, 2):
+        h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=coarse_max, cycle=kind)
+        assert h.num_levels >= 4, h.sizes()
+        Ms[kind] = np.column_stack([h.vcycle(e) for e in np.eye(s.n)])
+    As, Ps = _levels_dense(h)
+    Es = _error_propagators(As, Ps)
+    Ainv = np.linalg.inv(A)
+    for kind in (0, 1, 2):
+        want = (np.eye(s.n) - Es[kind]) @ Ainv
+        assert np.max(np.abs(Ms[kind] - want)) <= 1e-11 * np.max(np.abs(want)), kind
+    # the three kinds are different operators here
+    assert np.max(np.abs(Ms[1] - Ms[0])) > 1e-6 and np.max(np.abs(Ms[2] - Ms[1])) > 1e-6
+
+
+def test_cycle_kinds_coincide_on_two_and_three_levels():
+    """With two levels every kind is one exact coarse solve; with three the
+    level-1 cycles of W and F both end in the exact solve, so W = F (bitwise),
+    while W differs from V by the second level-1 cycle."""
+    s = W.poisson2d(16)
+    for coarse_max, levels in ((64, 2), (16, 3)):
+        z = {}
+        for kind in (0, 1, 2):
+            h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=coarse_max, cycle=kind)
+            assert h.num_levels == levels
+            z[kind] = h.vcycle(s.b)
+        assert np.array_equal(z[1], z[2])
+        if levels == 2:
+            assert np.array_equal(z[0], z[1])
+        else:
+            assert not np.array_equal(z[0], z[1])
+
+
+def test_w_cycle_symmetric_f_cycle_not():
+    """Same pre/post smoothing and an exact coarsest solve keep the W-cycle's
+    M^{-1} symmetric for symmetric A; the F-cycle's coarse correction (an F-
+    then a V-cycle) is not symmetric, which is why it needs flexible PCG."""
+    s = W.poisson2d(16)
+    M = {}
+    for kind in (1, 2):
+        h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=4, cycle=kind)
+        M[kind] = np.column_stack([h.vcycle(e) for e in np.eye(s.n)])
+    assert np.max(np.abs(M[1] - M[1].T)) < 1e-13
+    assert np.max(np.abs(M[2] - M[2].T)) > 1e-8
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_amg_solver_iterates_closed_form(kind):
+    """AMG as a solver from x_0 = 0: the error after j cycles is E^j x*, so
+    x_j = (I - E^j) A^{-1} b; the iteration count is the first j whose true
+    residual meets the tolerance."""
+    s = W.lognormal3d(6, seed=5)
+    A = s.dense()
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=8, cycle=kind)
+    E = _error_propagators(*_levels_dense(h))[kind]
+    xs = np.linalg.solve(A, s.b)
+    for j in (1, 2, 5):
+        x, info = h.amg_solve(s.b, rtol=0.0, max_iter=j)
+        assert info.iterations == j and info.status == O.ERR_NOT_CONVERGED
+        want = xs - np.linalg.matrix_power(E, j) @ xs
+        assert np.linalg.norm(x - want) <= 1e-11 * np.linalg.norm(xs)
+    rtol = 1e-8
+    bn = np.linalg.norm(s.b)
+    Ej = np.eye(s.n)
+    for j in range(1, 200):
+        Ej = E @ Ej
+        rel = np.linalg.norm(s.b - A @ (xs - Ej @ xs)) / bn
+        if rel <= rtol:
+            break
+    assert abs(rel / rtol - 1.0) > 1e-3  # not a borderline count
+    x, info = h.amg_solve(s.b, rtol=rtol)
+    assert info.status == O.OK and info.iterations == j
+    assert info.rel_res_true <= rtol
+
+
+def test_amg_solver_edge_cases():
+    s = W.poisson2d(12)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=16)
+    x, info = h.amg_solve(np.zeros(s.n), x0=np.ones(s.n))
+    assert info.iterations == 0 and info.status == O.OK and not np.any(x)
+    xs = np.linalg.solve(s.dense(), s.b)
+    x, info = h.amg_solve(s.b, x0=xs, rtol=1e-8)
+    assert info.iterations == 0 and info.status == O.OK and np.array_equal(x, xs)
+    x, info = h.amg_solve(s.b, rtol=1e-8, max_iter=0)
+    assert info.iterations == 0 and info.status == O.ERR_NOT_CONVERGED and not np.any(x)
+    # a stationary iteration converges linearly: residuals fall every cycle
+    rels = [h.amg_solve(s.b, rtol=0.0, max_iter=j)[1].rel_res_true for j in range(1, 8)]
+    assert all(b < a for a, b in zip(rels, rels[1:]))
