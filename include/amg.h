@@ -7,8 +7,10 @@
  *   - setup: pairwise heavy-edge matching (Sec. 2.1.1-2.1.2, Algorithms 2-3),
  *     piecewise-constant prolongation P, Galerkin A_c = P^T A P (Sec. 2.1.1),
  *     coarsest factorisation once (Sec. 2), all split from the solve (Sec. 3);
- *   - solve: V-cycle (Algorithm 1), AMG-preconditioned CG (Algorithm 4) and
- *     BiCG(Stab) (Algorithm 5), stopping on ||b - A x||_2 (Sec. 4).
+ *   - solve: V-cycle (Algorithm 1) or the W- and F-cycles that Sec. 2 and
+ *     Sec. 3 name, AMG as a solver (Sec. 3.1), AMG-preconditioned CG
+ *     (Algorithm 4) and BiCG(Stab) (Algorithm 5), stopping on ||b - A x||_2
+ *     (Sec. 4).
  *
  * Conventions shared by every entry point
  *   - All array arguments are DEVICE pointers on the current CUDA device
@@ -59,6 +61,13 @@ typedef enum {
 
 typedef enum { AMG_COARSE_AUTO = 0, AMG_COARSE_DENSE = 1, AMG_COARSE_CG = 2 } amg_coarse_solver;
 
+/* Multigrid cycle (Sec. 2 lists V-, W- and F-cycles; Algorithm 1 is the V).
+ * The coarse correction of level k is, below the coarsest level: one cycle of
+ * level k+1 (V), two (W), or an F-cycle followed by a V-cycle of level k+1
+ * (F); the first from a zero guess, the second from the first one's result.
+ * The coarsest level is solved once per coarse correction. */
+typedef enum { AMG_CYCLE_V = 0, AMG_CYCLE_W = 1, AMG_CYCLE_F = 2 } amg_cycle_kind;
+
 /* Setup and cycle parameters (amg_default_params fills the defaults).
  *   passes       pairwise matching passes per level (2: aggregates of <= 4; Table 2 /
  *                "pairwise, 2 passes")
@@ -76,7 +85,10 @@ typedef enum { AMG_COARSE_AUTO = 0, AMG_COARSE_DENSE = 1, AMG_COARSE_CG = 2 } am
  *                refinement steps per solve (x += X (f - A x)), chosen at setup
  *                so the result has FP64 accuracy (FP64 inverse if refinement
  *                cannot reach it)
- *   precision    value storage / arithmetic of the V-cycle (outer Krylov is FP64) */
+ *   precision    value storage / arithmetic of the V-cycle (outer Krylov is FP64)
+ *   cycle        amg_cycle_kind of every cycle the hierarchy runs (AMG_CYCLE_V).
+ *                The W-cycle keeps M^{-1} symmetric for symmetric A; the
+ *                F-cycle does not, so PCG with it should be flexible. */
 typedef struct {
   int passes;
   int max_levels;
@@ -87,6 +99,7 @@ typedef struct {
   int nu_post;
   int coarse_solver;
   int precision;
+  int cycle;
 } amg_params;
 
 /* Result of a Krylov solve.  iterations counts completed iterations (a
@@ -120,11 +133,25 @@ amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t
                      const double *d_val, const amg_params *params, amg_stream_t stream,
                      amg_hierarchy **out);
 
-/* One V-cycle from a zero initial guess (Algorithm 1 with x_0 = 0, as used
- * for z = M^{-1} r in Algorithms 4-5): d_z = M^{-1} d_r, both length n.  The
+/* One multigrid cycle from a zero initial guess (Algorithm 1 with x_0 = 0, as
+ * used for z = M^{-1} r in Algorithms 4-5; the W- or F-cycle when the
+ * hierarchy's params.cycle selects it): d_z = M^{-1} d_r, both length n.  The
  * two arrays must not overlap.  In FP32 / FP16-storage precision the input
  * is rounded to FP32 and the output widened back to FP64. */
 amg_status amg_vcycle(const amg_hierarchy *h, const double *d_r, double *d_z, amg_stream_t stream);
+
+/* AMG as a solver (Sec. 3.1, compared with AMG-PCG in Sec. 4.2): the
+ * stationary iteration x_{j+1} = x_j + M^{-1}(b - A x_j), M^{-1} one cycle of
+ * the hierarchy's kind from a zero guess.  d_x holds x_0 on entry, the last
+ * iterate on exit.  After every cycle the residual b - A x_j is recomputed
+ * from x_j; the solve stops when its 2-norm is <= rtol ||b||_2 or after
+ * max_iter cycles (iterations counts cycles; rel_res_recurrence and
+ * rel_res_true both report that residual).  b = 0 gives x = 0 and 0
+ * iterations.  info may be NULL.
+ * Errors: INVALID_ARG, BREAKDOWN (non-finite residual), NOT_CONVERGED,
+ * TIMEOUT, CUDA. */
+amg_status amg_solve(const amg_hierarchy *h, const double *d_b, double *d_x, double rtol, int max_iter,
+                     amg_stream_t stream, amg_solve_info *info);
 
 /* AMG-preconditioned CG (Sec. 3.2, Algorithm 4; residual update read as
  * r_{j+1} = r_j - alpha A p_j).  d_x holds x_0 on entry, the solution on exit.
@@ -149,8 +176,8 @@ amg_status bicgstab_solve(const amg_hierarchy *h, const double *d_b, double *d_x
  * system, each running its whole solve (same arguments and stopping rule as
  * pcg_solve, applied per system).  hs[i] is the hierarchy of system i (each
  * hierarchy at most once per call; every hierarchy must have a dense
- * coarsest level of at most 2048 rows (an FP64 inverse) and the same
- * precision, FP64 or FP32;
+ * coarsest level of at most 2048 rows (an FP64 inverse), the V-cycle and the
+ * same precision, FP64 or FP32;
  * AMG_ERR_UNSUPPORTED otherwise); d_b[i], d_x[i] are its device right-hand
  * side and initial guess / solution.  Block reductions only: the result of a
  * system does not depend on the rest of the batch.  infos (host, length nsys,

@@ -27,10 +27,11 @@ AMG_ERR_INVALID_ARG, AMG_ERR_INVALID_CSR, AMG_ERR_ZERO_DIAG, AMG_ERR_OOM = 1, 2,
 AMG_ERR_BREAKDOWN, AMG_ERR_NOT_CONVERGED, AMG_ERR_TIMEOUT, AMG_ERR_CUDA, AMG_ERR_UNSUPPORTED = 5, 6, 7, 8, 9
 AMG_FP64, AMG_FP32, AMG_FP16_STORAGE = 0, 1, 2
 AMG_COARSE_AUTO, AMG_COARSE_DENSE, AMG_COARSE_CG = 0, 1, 2
+AMG_CYCLE_V, AMG_CYCLE_W, AMG_CYCLE_F = 0, 1, 2
 
 # every symbol include/amg.h declares
 EXPORTS = (
-    "amg_default_params", "amg_setup", "amg_vcycle", "pcg_solve", "bicgstab_solve", "amg_num_levels",
+    "amg_default_params", "amg_setup", "amg_vcycle", "amg_solve", "pcg_solve", "bicgstab_solve", "amg_num_levels",
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
@@ -63,6 +64,7 @@ class amg_params(C.Structure):
         ("nu_post", C.c_int),
         ("coarse_solver", C.c_int),
         ("precision", C.c_int),
+        ("cycle", C.c_int),
     ]
 
 
@@ -100,6 +102,7 @@ def lib(build_if_missing: bool = False):
             l.amg_default_params.argtypes = [C.POINTER(amg_params)]
             l.amg_setup.argtypes = [i32, i64, vp, vp, vp, C.POINTER(amg_params), vp, C.POINTER(vp)]
             l.amg_vcycle.argtypes = [vp, vp, vp, vp]
+            l.amg_solve.argtypes = [vp, vp, vp, d, i32, vp, C.POINTER(amg_solve_info)]
             l.pcg_solve.argtypes = [vp, vp, vp, d, i32, i32, vp, C.POINTER(amg_solve_info)]
             l.bicgstab_solve.argtypes = [vp, vp, vp, d, i32, vp, C.POINTER(amg_solve_info)]
             l.amg_num_levels.argtypes = [vp]
@@ -218,6 +221,19 @@ def amg_vcycle(h: Hierarchy, r: torch.Tensor, z: torch.Tensor, stream=None) -> N
     st = lib().amg_vcycle(h.handle, _dev(r, torch.float64, "r"), _dev(z, torch.float64, "z"), _stream(stream))
     if st != AMG_OK:
         raise AmgError(st, "amg_vcycle")
+
+
+def amg_solve(h: Hierarchy, b: torch.Tensor, x: torch.Tensor, rtol: float = 1e-8, max_iter: int = 1000,
+              stream=None, check: bool = False) -> amg_solve_info:
+    """AMG as a solver (stationary cycles).  x holds x0 on entry.  Returns the
+    solve info; with check=True a status other than AMG_OK raises."""
+    info = amg_solve_info()
+    st = lib().amg_solve(h.handle, _dev(b, torch.float64, "b"), _dev(x, torch.float64, "x"), float(rtol),
+                         int(max_iter), _stream(stream), C.byref(info))
+    if st not in (AMG_OK, AMG_ERR_NOT_CONVERGED, AMG_ERR_BREAKDOWN) or (check and st != AMG_OK):
+        raise AmgError(st, "amg_solve")
+    info.status = st
+    return info
 
 
 def pcg_solve(h: Hierarchy, b: torch.Tensor, x: torch.Tensor, rtol: float = 1e-8, max_iter: int = 1000,

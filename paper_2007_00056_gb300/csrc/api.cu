@@ -151,6 +151,7 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->nu_post = 1;
   p->coarse_solver = AMG_COARSE_AUTO;
   p->precision = AMG_FP64;
+  p->cycle = AMG_CYCLE_V;
   return AMG_OK;
 }
 
@@ -215,6 +216,7 @@ extern "C" void amg_destroy(amg_hierarchy *h) {
   if (h->g_vcycle) cudaGraphExecDestroy(h->g_vcycle);
   if (h->g_pcg) cudaGraphExecDestroy(h->g_pcg);
   if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
+  if (h->g_amg) cudaGraphExecDestroy(h->g_amg);
   prof_flush(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   // stream-ordered frees back into the library pool, on the hierarchy's own stream

@@ -268,6 +268,7 @@ amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **o
   if (h->batch_desc) { *out = (const BatchSys *)h->batch_desc; return AMG_OK; }
   if (!h->dense || !h->ainv || h->lev[h->L].n > BATCH_MAX_COARSE) return AMG_ERR_UNSUPPORTED;
   if (h->prm.precision == AMG_FP16_STORAGE) return AMG_ERR_UNSUPPORTED;
+  if (h->prm.cycle != AMG_CYCLE_V) return AMG_ERR_UNSUPPORTED;
   const bool f32 = h->prm.precision == AMG_FP32;
   BatchSys d = {};
   d.L = h->L;

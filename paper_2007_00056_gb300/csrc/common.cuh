@@ -132,8 +132,8 @@ struct amg_hierarchy {
   cudaStream_t stream = nullptr;       // stream of amg_setup (stream-ordered allocations)
   cudaStream_t last_stream = nullptr;  // stream of the latest call that used the hierarchy
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr;
-  long long g_pcg_nodes = 0, g_bicg_nodes = 0;
+  cudaGraphExec_t g_vcycle = nullptr, g_pcg = nullptr, g_bicg = nullptr, g_amg = nullptr;
+  long long g_pcg_nodes = 0, g_bicg_nodes = 0, g_amg_nodes = 0;
   int graphs_ok = 1;
   int solves = 0;            // Krylov solves run on this hierarchy (graphs from the second one)
   Profiler prof;

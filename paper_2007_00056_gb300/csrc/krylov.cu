@@ -1,4 +1,5 @@
-// krylov.cu -- AMG-preconditioned CG (Algorithm 4) and BiCGStab (Algorithm 5).
+// krylov.cu -- AMG-preconditioned CG (Algorithm 4), BiCGStab (Algorithm 5)
+// and AMG as a stand-alone stationary solver (Sec. 3.1).
 //
 // The outer iteration is FP64 in every precision mode.  All scalars (alpha,
 // beta, omega, rho, residual norms) live in a device KState; each reduction
@@ -311,6 +312,43 @@ __global__ void k_axpy_half(int n, double *__restrict__ x, const double *__restr
 }
 
 // ---------------------------------------------------------------------------
+// AMG as a solver: x_{j+1} = x_j + M^{-1}(b - A x_j)
+// ---------------------------------------------------------------------------
+// x += z
+__global__ void k_amg_correct(int n, double *__restrict__ x, const double *__restrict__ z, const KState *st) {
+  if (is_done(st)) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + z[i];
+}
+
+// r = b - A x recomputed from the new iterate; stopping test on ||r||
+template <int TPR>
+__global__ void k_amg_residual(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                               const double *__restrict__ val, const double *__restrict__ b,
+                               const double *__restrict__ x, double *__restrict__ r, double *part, unsigned *counter,
+                               KState *st) {
+  if (is_done(st)) return;
+  double v[1] = {0.0};
+  KROW_LOOP_BEGIN(TPR, n)
+  int rb = 0, re = 0;
+  if (valid) { rb = __ldg(&rp[row]); re = __ldg(&rp[row + 1]); }
+  double ax = row_dot64<TPR>(ci, val, rb, re, _sub, x);
+  if (valid && _sub == 0) {
+    double ri = b[row] - ax;
+    r[row] = ri;
+    v[0] += ri * ri;
+  }
+  KROW_LOOP_END
+  double tot[1];
+  if (grid_sum_last<1>(v, part, counter, tot) && threadIdx.x == 0) {
+    st->it += 1;
+    st->rel = sqrt(tot[0]) / st->bnorm;
+    if (st->rel <= st->rtol) { st->done = 1; st->status = AMG_OK; }
+    else if (!isfinite(st->rel)) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
+    else if (st->it >= st->max_iter) { st->done = 1; st->status = AMG_ERR_NOT_CONVERGED; }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host drivers
 // ---------------------------------------------------------------------------
 namespace {
@@ -407,6 +445,19 @@ amg_status bicg_iteration(amg_hierarchy *h, cudaStream_t s) {
     k_bicg_p<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->kp, h->st);
 
   }
+  return amg_cuda_status(cudaGetLastError());
+}
+
+// One cycle of AMG as a solver: z = M^{-1} r, x += z, r = b - A x.
+amg_status amg_iteration(amg_hierarchy *h, cudaStream_t s) {
+  Level &l = h->lev[0];
+  const int n = l.n;
+  AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
+  {
+    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
+    k_amg_correct<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kz, h->st);
+  }
+  KDISPATCH(l, k_amg_residual, n, l.rp, l.ci, l.val, h->kb, h->kx, h->kr, h->part, h->counter + KSLOT_A, h->st);
   return amg_cuda_status(cudaGetLastError());
 }
 
@@ -521,8 +572,9 @@ bool bad_scalar(double v) { return !(v >= 0.0) || std::isinf(v); }
 void reset_graphs(amg_hierarchy *h) {
   if (h->g_pcg) cudaGraphExecDestroy(h->g_pcg);
   if (h->g_bicg) cudaGraphExecDestroy(h->g_bicg);
-  h->g_pcg = h->g_bicg = nullptr;
-  h->g_pcg_nodes = h->g_bicg_nodes = 0;
+  if (h->g_amg) cudaGraphExecDestroy(h->g_amg);
+  h->g_pcg = h->g_bicg = h->g_amg = nullptr;
+  h->g_pcg_nodes = h->g_bicg_nodes = h->g_amg_nodes = 0;
 }
 
 extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol, int max_iter,
@@ -573,5 +625,16 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
       k_axpy_half<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kph, h->st);
 
     }
+  return end_solve(h, d_x, s, info);
+}
+
+extern "C" amg_status amg_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol, int max_iter,
+                                amg_stream_t stream, amg_solve_info *info) {
+  if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
+  amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
+  cudaStream_t s = (cudaStream_t)stream;
+  h->last_stream = s;
+  AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, 0, s));
+  AMG_TRY(run_iterations(h, amg_iteration, &h->g_amg, &h->g_amg_nodes, s));
   return end_solve(h, d_x, s, info);
 }

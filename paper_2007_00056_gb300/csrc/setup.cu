@@ -721,6 +721,7 @@ amg_status validate_params(const amg_params *p) {
   if (p->nu_pre < 1 || p->nu_post < 0 || p->nu_pre > 64 || p->nu_post > 64) return AMG_ERR_INVALID_ARG;
   if (p->coarse_solver < 0 || p->coarse_solver > 2) return AMG_ERR_INVALID_ARG;
   if (p->precision < 0 || p->precision > 2) return AMG_ERR_INVALID_ARG;
+  if (p->cycle < AMG_CYCLE_V || p->cycle > AMG_CYCLE_F) return AMG_ERR_INVALID_ARG;
   return AMG_OK;
 }
 

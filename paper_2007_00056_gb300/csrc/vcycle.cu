@@ -1260,99 +1260,104 @@ void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KSta
                      (const double *)c.dinv, f, x, h->cg, st, h->eflags);
 }
 
-// Runs the V-cycle given f0 (level-0 right-hand side, in the level's own
-// scaling) and writes out0.  Levels below L are scaled in the FP16 mode; the
-// coarsest level L is never scaled.
+// One multigrid cycle of level k on A_k x = f (Algorithm 1; W- and F-cycles
+// by the coarse correction's recursion), written to out.  guess == nullptr
+// starts from x = 0 as Algorithm 1 does; otherwise from *guess, which may be
+// out itself (it is consumed by the first smoothing sweep).  Vectors of
+// levels below L are in their level's scaling in the FP16 mode; the coarsest
+// level L is never scaled and is solved, not cycled.
 template <typename T, typename V>
-void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const KState *st) {
+void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, int kind, cudaStream_t s,
+                 const KState *st) {
   using S = Sel<T, V>;
   const int L = h->L;
+  if (k == L) {
+    coarse_solve<T>(h, f, out, s, st);
+    return;
+  }
   const T omega = (T)h->prm.omega;
   const int nu_pre = h->prm.nu_pre, nu_post = h->prm.nu_post;
   const double sz = sizeof(T), szv = sizeof(V);
-  const T *fk[AMG_MAX_LEVELS];
-  T *cur[AMG_MAX_LEVELS];
-  for (int k = 0; k <= L; ++k) fk[k] = (k == 0) ? f0 : S::f(h->lev[k]);
-  // down sweep
-  for (int k = 0; k < L; ++k) {
-    Level &l = h->lev[k];
-    Level &c = h->lev[k + 1];
-    T *a = S::x(l), *b = S::t(l);
-    const T *dinv = S::dinv(l);
-    const V *val = S::val(l);
-    const double BA = bytes_A(l, (int)szv);
-    if (nu_pre == 1 && l.fuse_pre) {
-      LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
-      DISPATCH_ROWS(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, fk[k], a, b, st);
-      cur[k] = a;
+  Level &l = h->lev[k];
+  Level &c = h->lev[k + 1];
+  T *a = S::x(l), *b = S::t(l);
+  const T *dinv = S::dinv(l);
+  const V *val = S::val(l);
+  const double BA = bytes_A(l, (int)szv);
+  // presmoothing (nu_pre >= 1 sweeps), then the residual in b
+  if (!guess && nu_pre == 1 && l.fuse_pre) {
+    LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
+    DISPATCH_ROWS(l, k_residual0, l.n, l.perm, l.rp, l.ci, val, dinv, omega, f, a, b, st);
+  } else {
+    if (!guess) {
+      LaunchScope ls(h, s, PK_JACOBI0, k, 3.0 * sz * l.n);
+      k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, f, dinv, omega, a, st);
     } else {
-      {
-        LaunchScope ls(h, s, PK_JACOBI0, k, 3.0 * sz * l.n);
-        k_jacobi0<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, fk[k], dinv, omega, a, st);
-      }
-      for (int sw = 1; sw < nu_pre; ++sw) {
-        LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        launch_jacobi<T, V>(h, l, val, dinv, omega, a, fk[k], b, s, st);
-        std::swap(a, b);
-      }
-      cur[k] = a;
-      {
-        LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
-        launch_residual<T, V>(h, l, val, a, fk[k], b, s, st);
-      }
+      LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
+      launch_jacobi<T, V>(h, l, val, dinv, omega, guess, f, a, s, st);
     }
-    {
-      const float *isig_c = (k + 1 < L) ? S::isig(c) : nullptr;
-      LaunchScope ls(h, s, PK_RESTRICT, k, (sz + 4.0) * l.n + (sz + 4.0) * c.n + 4.0);
-      k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, S::sig(l), isig_c,
-                                                                        S::f(c), st);
+    for (int sw = 1; sw < nu_pre; ++sw) {
+      LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
+      launch_jacobi<T, V>(h, l, val, dinv, omega, a, f, b, s, st);
+      std::swap(a, b);
     }
+    LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
+    launch_residual<T, V>(h, l, val, a, f, b, s, st);
   }
-  // coarsest
-  T *xc = (L == 0) ? out0 : S::y(h->lev[L]);
-  coarse_solve<T>(h, fk[L], xc, s, st);
-  // up sweep
-  for (int k = L - 1; k >= 0; --k) {
-    Level &l = h->lev[k];
-    const int nc = h->lev[k + 1].n;
-    const float *sig = S::sig(l);
-    const float *isig_c = (k + 1 < L) ? S::isig(h->lev[k + 1]) : nullptr;
-    T *final_out = (k == 0) ? out0 : S::y(l);
-    T *in = cur[k];
-    T *other = (in == S::x(l)) ? S::t(l) : S::x(l);
-    const T *dinv = S::dinv(l);
-    const V *val = S::val(l);
-    const double BA = bytes_A(l, (int)szv);
-    if (nu_post == 0) {
-      LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
-      k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, final_out, st);
-    } else {
-      // curb: current iterate; spare: a free buffer distinct from final_out
-      T *curb, *spare;
-      int sweeps = nu_post;
-      if (l.fuse_post) {
-        T *o = (nu_post == 1) ? final_out : other;
-        LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
-        DISPATCH_ROWS(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, fk[k], o, st);
-        curb = o;
-        spare = in;
-        sweeps -= 1;
-      } else {
-        LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
-        k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, other, st);
-        curb = other;
-        spare = in;
-      }
-      for (int sw = 0; sw < sweeps; ++sw) {
-        T *dst = (sw == sweeps - 1) ? final_out : spare;
-        LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
-        launch_jacobi<T, V>(h, l, val, dinv, omega, curb, fk[k], dst, s, st);
-        spare = curb;
-        curb = dst;
-      }
-    }
-    xc = final_out;
+  // restriction f_{k+1} = P^T r
+  const float *isig_c = (k + 1 < L) ? S::isig(c) : nullptr;
+  {
+    LaunchScope ls(h, s, PK_RESTRICT, k, (sz + 4.0) * l.n + (sz + 4.0) * c.n + 4.0);
+    k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, S::sig(l), isig_c,
+                                                                      S::f(c), st);
   }
+  // coarse correction in y_{k+1}: one cycle (V), two (W), or an F- then a
+  // V-cycle (F) of level k+1, the second from the first one's result; the
+  // coarsest level is solved once
+  T *xc = S::y(c);
+  const T *fc = S::f(c);
+  cycle_level<T, V>(h, k + 1, fc, nullptr, xc, kind, s, st);
+  if (k + 1 < L && kind == AMG_CYCLE_W) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_W, s, st);
+  if (k + 1 < L && kind == AMG_CYCLE_F) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_V, s, st);
+  // prolongation and postsmoothing into out
+  const float *sig = S::sig(l);
+  const int nc = c.n;
+  T *in = a;
+  T *other = b;
+  if (nu_post == 0) {
+    LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
+    k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, out, st);
+    return;
+  }
+  // curb: current iterate; spare: a free buffer distinct from out
+  T *curb, *spare;
+  int sweeps = nu_post;
+  if (l.fuse_post) {
+    T *o = (nu_post == 1) ? out : other;
+    LaunchScope ls(h, s, PK_PROLONG_JACOBI, k, BA + (4.0 * sz + 4.0) * l.n + sz * nc);
+    DISPATCH_ROWS(l, k_prolong_jacobi, l.n, l.perm, l.rp, l.ci, val, dinv, omega, in, l.agg, xc, sig, isig_c, f, o,
+                  st);
+    curb = o;
+    spare = in;
+    sweeps -= 1;
+  } else {
+    LaunchScope ls(h, s, PK_PROLONG, k, (2.0 * sz + 4.0) * l.n + sz * nc);
+    k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, other, st);
+    curb = other;
+    spare = in;
+  }
+  for (int sw = 0; sw < sweeps; ++sw) {
+    T *dst = (sw == sweeps - 1) ? out : spare;
+    LaunchScope ls(h, s, PK_JACOBI, k, BA + 4.0 * sz * l.n);
+    launch_jacobi<T, V>(h, l, val, dinv, omega, curb, f, dst, s, st);
+    spare = curb;
+    curb = dst;
+  }
+}
+
+template <typename T, typename V>
+void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const KState *st) {
+  cycle_level<T, V>(h, 0, f0, nullptr, out0, h->prm.cycle, s, st);
 }
 
 }  // namespace
