@@ -18,7 +18,13 @@
  *    zeros skipped (Sec. 2.1.1 and Algorithm 3 put both directed entries in
  *    the edge list, so a pair is first met at the larger one);
  *  - ties between equal weights go to the smaller index: the total edge order
- *    is (w descending, min(i,j) ascending, max(i,j) ascending);
+ *    is (w descending, min(i,j) ascending, max(i,j) ascending); as an option,
+ *    the order Algorithm 3 prints (its edge list sorted lexicographically
+ *    descending, so ties go to the larger index: w descending, max(i,j)
+ *    descending, min(i,j) descending);
+ *  - as an option outside the paper, the edge weight divided by
+ *    sqrt(|a_ii| |a_jj|) (a diagonally scaled weight, computed as
+ *    max(|a_ij|,|a_ji|) / sqrt(|a_ii| * |a_jj|));
  *  - aggregate number = rank of the aggregate's smallest member;
  *  - "2 passes": two pairwise matchings per level, the second one on the
  *    Galerkin product of the first (aggregates of up to four nodes);
@@ -37,7 +43,7 @@
  *    level k+1 (W), or one F-cycle then one V-cycle of level k+1 (F), the
  *    first from a zero guess and the second from the first one's result; the
  *    coarsest level is solved once per coarse correction;
- *  - AMG as a solver (Sec. 3.1, Sec. 4.2) is the stationary iteration
+ *  - AMG as a solver (Sec. 3.1, Sec. 4.4) is the stationary iteration
  *    x_{j+1} = x_j + M^{-1}(b - A x_j) with M^{-1} one cycle from a zero
  *    guess, stopping once ||b - A x_j|| <= rtol ||b||.
  */
@@ -120,6 +126,34 @@ static int edge_cmp(const void *pa, const void *pb) {
   return 0;
 }
 
+/* Total edge order of Algorithm 3's lexicographically descending sort:
+ * heavier first; equal weights -> larger max endpoint, then larger min. */
+static int edge_cmp_desc(const void *pa, const void *pb) {
+  const edge_t *a = (const edge_t *)pa, *b = (const edge_t *)pb;
+  if (a->w > b->w) return -1;
+  if (a->w < b->w) return 1;
+  if (a->v != b->v) return a->v > b->v ? -1 : 1;
+  if (a->u != b->u) return a->u > b->u ? -1 : 1;
+  return 0;
+}
+
+/* |a_ii| of every row (0 when the diagonal is not stored). */
+static double *abs_diag(int n, const int *rp, const int *ci, const double *val) {
+  double *d = (double *)calloc((size_t)(n ? n : 1), sizeof(double));
+  if (!d) return NULL;
+  for (int i = 0; i < n; ++i)
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) d[i] = fabs(val[e]);
+  return d;
+}
+
+/* Weight of the directed entry a_ij: |a_ij|, or with edge_weight = 1
+ * |a_ij| / sqrt(|a_ii| * |a_jj|). */
+static double entry_weight(double a_ij, const double *d, int i, int j, int edge_weight) {
+  if (edge_weight == 1) return fabs(a_ij) / sqrt(d[i] * d[j]);
+  return fabs(a_ij);
+}
+
 /* Edge-based HEM (Sec. 2.1.2, Algorithm 3): list every stored off-diagonal
  * nonzero as an edge weighted |a_ij|, sort the list heaviest first, then walk
  * it and pair both endpoints whenever both are still unpaired.  Each directed
@@ -127,24 +161,27 @@ static int edge_cmp(const void *pa, const void *pb) {
  * later copy finds both ends taken and does nothing.  Ties use the total
  * order of edge_cmp (smaller index first).  mate[i] = partner or -1.
  * Returns the number of pairs, or -1 on allocation failure. */
-int orc_match_greedy(int n, const int *rp, const int *ci, const double *val, int *mate) {
+int orc_match_greedy_opt(int n, const int *rp, const int *ci, const double *val, int tie_break,
+                         int edge_weight, int *mate) {
+  double *d = abs_diag(n, rp, ci, val);
+  if (!d) return -1;
   long long m = 0;
   for (int i = 0; i < n; ++i)
     for (int e = rp[i]; e < rp[i + 1]; ++e)
       if (ci[e] != i && val[e] != 0.0) ++m;
   edge_t *T = (edge_t *)malloc((size_t)(m ? m : 1) * sizeof(edge_t));
-  if (!T) return -1;
+  if (!T) { free(d); return -1; }
   long long t = 0;
   for (int i = 0; i < n; ++i)
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
       int j = ci[e];
       if (j == i || val[e] == 0.0) continue;
-      T[t].w = fabs(val[e]);
+      T[t].w = entry_weight(val[e], d, i, j, edge_weight);
       T[t].u = i < j ? i : j;
       T[t].v = i < j ? j : i;
       ++t;
     }
-  qsort(T, (size_t)m, sizeof(edge_t), edge_cmp);
+  qsort(T, (size_t)m, sizeof(edge_t), tie_break == 1 ? edge_cmp_desc : edge_cmp);
   for (int i = 0; i < n; ++i) mate[i] = -1;
   int pairs = 0;
   for (long long k = 0; k < m; ++k) {
@@ -156,7 +193,12 @@ int orc_match_greedy(int n, const int *rp, const int *ci, const double *val, int
     }
   }
   free(T);
+  free(d);
   return pairs;
+}
+
+int orc_match_greedy(int n, const int *rp, const int *ci, const double *val, int *mate) {
+  return orc_match_greedy_opt(n, rp, ci, val, 0, 0, mate);
 }
 
 /* Weighted neighbour lists of the undirected graph of A (Sec. 2.1: A is the
@@ -165,9 +207,10 @@ int orc_match_greedy(int n, const int *rp, const int *ci, const double *val, int
  * from both directions of every stored entry. */
 typedef struct { int *rp; int *nb; double *w; } wgraph_t;
 
-static int wgraph_build(int n, const int *rp, const int *ci, const double *val, wgraph_t *g) {
+static int wgraph_build(int n, const int *rp, const int *ci, const double *val, int edge_weight, wgraph_t *g) {
+  double *d = abs_diag(n, rp, ci, val);
   int *deg = (int *)calloc((size_t)n + 1, sizeof(int));
-  if (!deg) return -1;
+  if (!deg || !d) { free(deg); free(d); return -1; }
   for (int i = 0; i < n; ++i)
     for (int e = rp[i]; e < rp[i + 1]; ++e)
       if (ci[e] != i && val[e] != 0.0) { deg[i]++; deg[ci[e]]++; }
@@ -186,7 +229,7 @@ static int wgraph_build(int n, const int *rp, const int *ci, const double *val, 
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
       int j = ci[e];
       if (j == i || val[e] == 0.0) continue;
-      double a = fabs(val[e]);
+      double a = entry_weight(val[e], d, i, j, edge_weight);
       /* add (i -> j) and (j -> i), keeping the larger weight for repeats */
       int ends[2][2] = {{i, j}, {j, i}};
       for (int s = 0; s < 2; ++s) {
@@ -203,7 +246,7 @@ static int wgraph_build(int n, const int *rp, const int *ci, const double *val, 
     for (long long k = start[i]; k < start[i] + fill[i]; ++k) { g->nb[o] = g->nb[k]; g->w[o] = g->w[k]; ++o; }
   }
   g->rp[n] = (int)o;
-  free(deg); free(fill); free(start);
+  free(deg); free(fill); free(start); free(d);
   return 0;
 }
 
@@ -211,15 +254,17 @@ static void wgraph_free(wgraph_t *g) { free(g->rp); free(g->nb); free(g->w); }
 
 /* Matching by synchronous rounds of mutual-heaviest-neighbour handshakes: in
  * each round every unpaired node picks its heaviest unpaired neighbour
- * (equal weights -> smaller index) using the state at the start of the round;
+ * (equal weights -> smaller index; larger with tie_break = 1) using the state
+ * at the start of the round;
  * two nodes that picked each other are paired.  Rounds repeat until a round
  * pairs nothing; nodes still unpaired stay single (Sec. 2.1.1: a node without
  * an unmatched neighbour becomes a coarse node by itself).  *rounds counts
  * every round run, the final empty one included.  Returns the number of
  * pairs, or -1 on allocation failure. */
-int orc_match_rounds(int n, const int *rp, const int *ci, const double *val, int *mate, int *rounds) {
+int orc_match_rounds_opt(int n, const int *rp, const int *ci, const double *val, int tie_break, int edge_weight,
+                         int *mate, int *rounds) {
   wgraph_t g;
-  if (wgraph_build(n, rp, ci, val, &g)) return -1;
+  if (wgraph_build(n, rp, ci, val, edge_weight, &g)) return -1;
   int *pick = (int *)malloc((size_t)(n ? n : 1) * sizeof(int));
   for (int i = 0; i < n; ++i) mate[i] = -1;
   int pairs = 0, r = 0;
@@ -232,7 +277,10 @@ int orc_match_rounds(int n, const int *rp, const int *ci, const double *val, int
       for (int k = g.rp[i]; k < g.rp[i + 1]; ++k) {
         int j = g.nb[k];
         if (mate[j] >= 0) continue;
-        if (pick[i] < 0 || g.w[k] > best || (g.w[k] == best && j < pick[i])) { best = g.w[k]; pick[i] = j; }
+        if (pick[i] < 0 || g.w[k] > best || (g.w[k] == best && (tie_break == 1 ? j > pick[i] : j < pick[i]))) {
+          best = g.w[k];
+          pick[i] = j;
+        }
       }
     }
     int new_pairs = 0;
@@ -247,6 +295,10 @@ int orc_match_rounds(int n, const int *rp, const int *ci, const double *val, int
   free(pick);
   wgraph_free(&g);
   return pairs;
+}
+
+int orc_match_rounds(int n, const int *rp, const int *ci, const double *val, int *mate, int *rounds) {
+  return orc_match_rounds_opt(n, rp, ci, val, 0, 0, mate, rounds);
 }
 
 /* Node-based HEM as printed in Algorithm 2 (Sec. 2.1.1), kept only as a
@@ -357,6 +409,8 @@ typedef struct {
   int nu_pre, nu_post, coarse_solver; /* 0 auto, 1 dense LU, 2 CG */
   int matcher;                        /* 0 greedy EHEM order, 1 literal rounds */
   int cycle;                          /* 0 V, 1 W, 2 F (Sec. 2 names all three) */
+  int tie_break;                      /* 0 smaller index, 1 larger (Algorithm 3's order) */
+  int edge_weight;                    /* 0 max(|a_ij|,|a_ji|), 1 / sqrt(|a_ii a_jj|) */
 } orc_params;
 
 typedef struct {
@@ -392,8 +446,9 @@ static int coarsen_pass(const orc_params *prm, int n, const int *rp, const int *
   int *mate = (int *)malloc((size_t)(n ? n : 1) * sizeof(int));
   if (!mate) return ORC_ERR_OOM;
   int r = 0;
-  int pairs = prm->matcher == 1 ? orc_match_rounds(n, rp, ci, val, mate, &r)
-                                : orc_match_greedy(n, rp, ci, val, mate);
+  int pairs = prm->matcher == 1
+                  ? orc_match_rounds_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate, &r)
+                  : orc_match_greedy_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate);
   if (pairs < 0) { free(mate); return ORC_ERR_OOM; }
   *rounds = r;
   int nc = orc_aggregates(n, mate, agg);
@@ -469,6 +524,8 @@ void orc_default_params(orc_params *p) {
   p->coarse_solver = 0;
   p->matcher = 0;
   p->cycle = 0;
+  p->tie_break = 0;
+  p->edge_weight = 0;
 }
 
 void orc_destroy(orc_hier *h) {
@@ -793,7 +850,7 @@ int orc_pcg(orc_hier *h, const double *b, double *x, double rtol, int max_iter, 
   return st;
 }
 
-/* AMG as a solver (Sec. 3.1, Sec. 4.2): the stationary iteration
+/* AMG as a solver (Sec. 3.1, Sec. 4.4): the stationary iteration
  * x_{j+1} = x_j + M^{-1}(b - A x_j), M^{-1} one cycle of the configured kind
  * from the zero guess.  x holds x_0 on entry.  Stops once
  * ||b - A x_j|| <= rtol ||b|| (the residual recomputed from x_j after every

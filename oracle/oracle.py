@@ -52,6 +52,8 @@ class Params(C.Structure):
         ("coarse_solver", C.c_int),
         ("matcher", C.c_int),
         ("cycle", C.c_int),
+        ("tie_break", C.c_int),
+        ("edge_weight", C.c_int),
     ]
 
     def __init__(self, **kw):
@@ -85,6 +87,9 @@ def lib():
             l.orc_check_csr.argtypes = [C.c_int, C.c_longlong, _i32p, _i32p]
             l.orc_match_greedy.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p]
             l.orc_match_rounds.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.POINTER(C.c_int)]
+            l.orc_match_greedy_opt.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, C.c_int, _i32p]
+            l.orc_match_rounds_opt.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, C.c_int, _i32p,
+                                               C.POINTER(C.c_int)]
             l.orc_nhem.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p]
             l.orc_aggregates.argtypes = [C.c_int, _i32p, _i32p]
             l.orc_galerkin.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _i32p, _i32p, _f64p]
@@ -124,22 +129,30 @@ def check_csr(rp, ci):
     return lib().orc_check_csr(len(rp) - 1, int(rp[-1]) if len(rp) else 0, rp, ci)
 
 
-def match_greedy(rp, ci, val):
-    """Greedy edge-based HEM (Algorithm 3) in the smaller-index total order: mate array."""
+def match_greedy(rp, ci, val, tie_break=0, edge_weight=0):
+    """Greedy edge-based HEM (Algorithm 3): mate array.  tie_break 0 orders
+    equal weights by smaller index, 1 by larger (Algorithm 3's descending
+    sort); edge_weight 1 divides by sqrt(|a_ii a_jj|)."""
     rp, ci, val = _csr(rp, ci, val)
     n = len(rp) - 1
     mate = np.empty(n, dtype=np.int32)
-    lib().orc_match_greedy(n, rp, ci, val, mate)
+    if tie_break == 0 and edge_weight == 0:
+        lib().orc_match_greedy(n, rp, ci, val, mate)
+    else:
+        lib().orc_match_greedy_opt(n, rp, ci, val, int(tie_break), int(edge_weight), mate)
     return mate
 
 
-def match_rounds(rp, ci, val):
+def match_rounds(rp, ci, val, tie_break=0, edge_weight=0):
     """Synchronous handshake rounds run to their fixed point: (mate, rounds)."""
     rp, ci, val = _csr(rp, ci, val)
     n = len(rp) - 1
     mate = np.empty(n, dtype=np.int32)
     r = C.c_int(0)
-    lib().orc_match_rounds(n, rp, ci, val, mate, C.byref(r))
+    if tie_break == 0 and edge_weight == 0:
+        lib().orc_match_rounds(n, rp, ci, val, mate, C.byref(r))
+    else:
+        lib().orc_match_rounds_opt(n, rp, ci, val, int(tie_break), int(edge_weight), mate, C.byref(r))
     return mate, r.value
 
 

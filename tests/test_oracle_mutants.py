@@ -22,7 +22,7 @@ MUTANTS = [
      "test_worked_example_matches_paper"),
     ("tie_break_larger_index", "if (a->u != b->u) return a->u < b->u ? -1 : 1;",
      "if (a->u != b->u) return a->u > b->u ? -1 : 1;", "test_greedy_matching_bruteforce"),
-    ("rounds_tie_break", "(g.w[k] == best && j < pick[i])", "(g.w[k] == best && j > pick[i])",
+    ("rounds_tie_break", "(tie_break == 1 ? j > pick[i] : j < pick[i])", "(tie_break == 1 ? j > pick[i] : j > pick[i])",
      "test_handshake_rounds_reach_greedy_matching"),
     ("numbering_by_largest", "if (mate[i] < 0 || i < mate[i]) agg[i] = C++;",
      "if (mate[i] < 0 || i > mate[i]) agg[i] = C++;", "test_aggregates_partition_and_numbering"),
@@ -36,6 +36,10 @@ MUTANTS = [
      "alpha = gamma_new / delta;", "test_coarse_cg_finite_termination_two_eigenvalues"),
     ("lu_no_pivoting", "if (fabs(a[(size_t)i * n + k]) > best)", "if (0 && fabs(a[(size_t)i * n + k]) > best)",
      "test_dense_lu_matches_numpy"),
+    ("desc_tie_order_wrong_direction", "if (a->v != b->v) return a->v > b->v ? -1 : 1;",
+     "if (a->v != b->v) return a->v < b->v ? -1 : 1;", "test_descending_tie_order_bruteforce"),
+    ("scaled_weight_without_sqrt", "return fabs(a_ij) / sqrt(d[i] * d[j]);", "return fabs(a_ij) / (d[i] * d[j]);",
+     "test_scaled_weight_bruteforce_and_invariance"),
     ("w_second_cycle_from_zero", "kind == 1) mg_cycle(h, k + 1, fc, xc, 1, 0);",
      "kind == 1) mg_cycle(h, k + 1, fc, xc, 1, 1);", "test_cycles_match_error_propagation_recursion"),
     ("w_single_coarse_cycle", "if (k + 1 < h->L && kind == 1)", "if (0 && k + 1 < h->L && kind == 1)",

@@ -590,3 +590,124 @@ def test_amg_solver_edge_cases():
     # a stationary iteration converges linearly: residuals fall every cycle
     rels = [h.amg_solve(s.b, rtol=0.0, max_iter=j)[1].rel_res_true for j in range(1, 8)]
     assert all(b < a for a, b in zip(rels, rels[1:]))
+
+
+# --------------------------------------------------------------------------
+# Matching options: Algorithm 3's own tie order, diagonally scaled weights
+# --------------------------------------------------------------------------
+
+def _bruteforce_greedy_key(a, key, weight=None):
+    """Lexicographically first maximal matching in the edge order `key`
+    (enumerating every matching); weight(i, j, a_ij) replaces |a_ij|."""
+    n = a.shape[0]
+    E = {}
+    for i in range(n):
+        for j in range(n):
+            if i != j and a[i, j] != 0:
+                u, v = min(i, j), max(i, j)
+                w = abs(a[i, j]) if weight is None else weight(i, j, a[i, j])
+                E[(u, v)] = max(E.get((u, v), 0.0), w)
+    order = sorted(E, key=lambda e: key(E[e], e[0], e[1]))
+    rank = {e: r for r, e in enumerate(order)}
+    best = None
+    edges = list(E)
+    for k in range(0, n // 2 + 1):
+        for combo in itertools.combinations(edges, k):
+            ends = [x for e in combo for x in e]
+            if len(set(ends)) < len(ends):
+                continue
+            used = set(ends)
+            if any(u not in used and v not in used for u, v in edges):
+                continue
+            r = sorted(rank[e] for e in combo)
+            if best is None or r < best[0]:
+                best = (r, combo)
+    mate = -np.ones(n, dtype=np.int32)
+    for u, v in best[1]:
+        mate[u], mate[v] = v, u
+    return mate
+
+
+def _tiny_tied(seed):
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 9))
+    mask = np.triu(rng.random((n, n)) < 0.5, 1)
+    a = np.where(mask, -rng.integers(1, 3, (n, n)).astype(float), 0.0)
+    a = a + a.T
+    a[np.diag_indices(n)] = rng.integers(4, 7, n).astype(float)
+    return a
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_descending_tie_order_bruteforce(seed):
+    """Algorithm 3 sorts its edge list lexicographically descending: equal
+    weights go to the larger (max, then min) endpoint."""
+    a = _tiny_tied(seed)
+    s = W.from_dense(a)
+    want = _bruteforce_greedy_key(a, lambda w, u, v: (-w, -v, -u))
+    np.testing.assert_array_equal(O.match_greedy(s.rp, s.ci, s.val, tie_break=1), want)
+    mate_r, _ = O.match_rounds(s.rp, s.ci, s.val, tie_break=1)
+    np.testing.assert_array_equal(mate_r, want)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_descending_tie_order_is_the_reversed_numbering(seed):
+    """Renumbering i -> N-1-i turns the descending tie order into the default
+    (smaller index) one, on graphs with many ties."""
+    rng = np.random.default_rng(seed)
+    s = W.random_spd(int(rng.integers(5, 120)), float(rng.uniform(0.05, 0.3)), seed, int_weights=True)
+    a = s.dense()
+    r = a[::-1, ::-1].copy()
+    sr = W.from_dense(r)
+    m_desc = O.match_greedy(s.rp, s.ci, s.val, tie_break=1)
+    m_rev = O.match_greedy(sr.rp, sr.ci, sr.val)
+    n = s.n
+    back = np.where(m_rev[::-1] >= 0, n - 1 - m_rev[::-1], -1)
+    np.testing.assert_array_equal(m_desc, back)
+    mate_r, _ = O.match_rounds(s.rp, s.ci, s.val, tie_break=1)
+    np.testing.assert_array_equal(mate_r, m_desc)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_scaled_weight_bruteforce_and_invariance(seed):
+    """Weight max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|): brute force on tiny graphs;
+    invariant under a symmetric positive diagonal scaling D A D; equal to the
+    plain matching when the diagonal is constant."""
+    a = _tiny_tied(seed)
+    d = np.abs(np.diag(a))
+    s = W.from_dense(a)
+    want = _bruteforce_greedy_key(a, lambda w, u, v: (-w, u, v),
+                                  weight=lambda i, j, x: abs(x) / np.sqrt(d[i] * d[j]))
+    np.testing.assert_array_equal(O.match_greedy(s.rp, s.ci, s.val, edge_weight=1), want)
+    np.testing.assert_array_equal(O.match_rounds(s.rp, s.ci, s.val, edge_weight=1)[0], want)
+    rng = np.random.default_rng(seed)
+    b = W.random_spd(int(rng.integers(5, 100)), 0.2, seed)  # real weights: no ties
+    D = rng.uniform(0.5, 2.0, b.n)
+    sc = W.from_dense(D[:, None] * b.dense() * D[None, :])
+    np.testing.assert_array_equal(O.match_greedy(sc.rp, sc.ci, sc.val, edge_weight=1),
+                                  O.match_greedy(b.rp, b.ci, b.val, edge_weight=1))
+    p = W.poisson2d(9)  # constant diagonal 4
+    np.testing.assert_array_equal(O.match_greedy(p.rp, p.ci, p.val, edge_weight=1),
+                                  O.match_greedy(p.rp, p.ci, p.val))
+
+
+def test_matching_options_reach_the_hierarchy():
+    """The options change the aggregates of a tie-heavy grid (descending order)
+    and of a lognormal system (scaled weights), and every level stays the
+    Galerkin product of its aggregates."""
+    s = W.poisson2d(11)  # odd rows: the two tie orders pair a row from opposite ends
+    a0 = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=16).level(0)[3]
+    a1 = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=16, tie_break=1).level(0)[3]
+    assert not np.array_equal(a0, a1)
+    s = W.lognormal3d(8, seed=2)
+    for kw in (dict(tie_break=1), dict(edge_weight=1)):
+        h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=20, **kw)
+        for k in range(h.num_levels - 1):
+            rp, ci, val, agg = h.level(k)
+            A = _dense(rp, ci, val, len(rp) - 1)
+            P = _P(agg, h.level_info(k + 1)[0])
+            rpc, cic, valc, _ = h.level(k + 1)
+            np.testing.assert_allclose(_dense(rpc, cic, valc, P.shape[1]), P.T @ A @ P, rtol=1e-13, atol=1e-13)
+    sizes_plain = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=20).sizes()
+    sizes_scaled = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=20, edge_weight=1).sizes()
+    assert sizes_scaled != sizes_plain
