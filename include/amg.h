@@ -68,6 +68,20 @@ typedef enum { AMG_COARSE_AUTO = 0, AMG_COARSE_DENSE = 1, AMG_COARSE_CG = 2 } am
  * The coarsest level is solved once per coarse correction. */
 typedef enum { AMG_CYCLE_V = 0, AMG_CYCLE_W = 1, AMG_CYCLE_F = 2 } amg_cycle_kind;
 
+/* Order of equal edge weights in the matching.  AMG_TIE_SMALLER: total edge
+ * order (w descending, min(i,j) ascending, max(i,j) ascending), i.e. a node
+ * prefers the smaller of two equally heavy neighbours.  AMG_TIE_LARGER: the
+ * order of Algorithm 3's lexicographically descending sort (w descending,
+ * max(i,j) descending, min(i,j) descending): the larger neighbour. */
+typedef enum { AMG_TIE_SMALLER = 0, AMG_TIE_LARGER = 1 } amg_tie_break;
+
+/* Edge weight of {i,j}.  AMG_WEIGHT_ABS: max(|a_ij|, |a_ji|) (Sec. 2.1).
+ * AMG_WEIGHT_SCALED, an option the paper does not have: that weight divided
+ * by sqrt(|a_ii| |a_jj|), the weight of the symmetrically scaled matrix
+ * D^-1/2 A D^-1/2, which keeps coarsening variable-coefficient problems
+ * whose plain weights stall it. */
+typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
+
 /* Setup and cycle parameters (amg_default_params fills the defaults).
  *   passes       pairwise matching passes per level (2: aggregates of <= 4; Table 2 /
  *                "pairwise, 2 passes")
@@ -88,7 +102,9 @@ typedef enum { AMG_CYCLE_V = 0, AMG_CYCLE_W = 1, AMG_CYCLE_F = 2 } amg_cycle_kin
  *   precision    value storage / arithmetic of the V-cycle (outer Krylov is FP64)
  *   cycle        amg_cycle_kind of every cycle the hierarchy runs (AMG_CYCLE_V).
  *                The W-cycle keeps M^{-1} symmetric for symmetric A; the
- *                F-cycle does not, so PCG with it should be flexible. */
+ *                F-cycle does not, so PCG with it should be flexible.
+ *   tie_break    amg_tie_break of the matching (AMG_TIE_SMALLER)
+ *   edge_weight  amg_edge_weight of the matching (AMG_WEIGHT_ABS) */
 typedef struct {
   int passes;
   int max_levels;
@@ -100,6 +116,8 @@ typedef struct {
   int coarse_solver;
   int precision;
   int cycle;
+  int tie_break;
+  int edge_weight;
 } amg_params;
 
 /* Result of a Krylov solve.  iterations counts completed iterations (a
@@ -140,7 +158,7 @@ amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t
  * is rounded to FP32 and the output widened back to FP64. */
 amg_status amg_vcycle(const amg_hierarchy *h, const double *d_r, double *d_z, amg_stream_t stream);
 
-/* AMG as a solver (Sec. 3.1, compared with AMG-PCG in Sec. 4.2): the
+/* AMG as a solver (Sec. 3.1, compared with AMG-PCG in Sec. 4.4): the
  * stationary iteration x_{j+1} = x_j + M^{-1}(b - A x_j), M^{-1} one cycle of
  * the hierarchy's kind from a zero guess.  d_x holds x_0 on entry, the last
  * iterate on exit.  After every cycle the residual b - A x_j is recomputed

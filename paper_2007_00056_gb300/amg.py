@@ -28,6 +28,8 @@ AMG_ERR_BREAKDOWN, AMG_ERR_NOT_CONVERGED, AMG_ERR_TIMEOUT, AMG_ERR_CUDA, AMG_ERR
 AMG_FP64, AMG_FP32, AMG_FP16_STORAGE = 0, 1, 2
 AMG_COARSE_AUTO, AMG_COARSE_DENSE, AMG_COARSE_CG = 0, 1, 2
 AMG_CYCLE_V, AMG_CYCLE_W, AMG_CYCLE_F = 0, 1, 2
+AMG_TIE_SMALLER, AMG_TIE_LARGER = 0, 1
+AMG_WEIGHT_ABS, AMG_WEIGHT_SCALED = 0, 1
 
 # every symbol include/amg.h declares
 EXPORTS = (
@@ -65,6 +67,8 @@ class amg_params(C.Structure):
         ("coarse_solver", C.c_int),
         ("precision", C.c_int),
         ("cycle", C.c_int),
+        ("tie_break", C.c_int),
+        ("edge_weight", C.c_int),
     ]
 
 

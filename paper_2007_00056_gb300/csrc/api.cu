@@ -152,6 +152,8 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->coarse_solver = AMG_COARSE_AUTO;
   p->precision = AMG_FP64;
   p->cycle = AMG_CYCLE_V;
+  p->tie_break = AMG_TIE_SMALLER;
+  p->edge_weight = AMG_WEIGHT_ABS;
   return AMG_OK;
 }
 

@@ -67,17 +67,37 @@ __global__ void k_nonfinite(long long nnz, const double *__restrict__ val, unsig
 // ---------------------------------------------------------------------------
 // Edge weights: w_e = max(|a_ij|, |a_ji|) for e = (i, j), j != i; 0 = no edge.
 // (Sec. 2.1: a_ij is the edge weight; Algorithm 3 lists both directions.)
+// scaled != 0 (an option outside the paper): w_e / sqrt(|a_ii| * |a_jj|),
+// which a zero diagonal turns into an error.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double abs_diag(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                           const double *__restrict__ val, int i) {
+  const int p = find_col(ci, rp[i], rp[i + 1], i);
+  return p >= 0 ? fabs(val[p]) : 0.0;
+}
+
 __global__ void k_weights(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                          const double *__restrict__ val, double *__restrict__ w, unsigned *eflags) {
+                          const double *__restrict__ val, int scaled, double *__restrict__ w, unsigned *eflags) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const double di = scaled ? abs_diag(rp, ci, val, i) : 1.0;
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     int j = ci[e];
     if (j == i) { w[e] = 0.0; continue; }
     int q = find_col(ci, rp[j], rp[j + 1], i);
-    if (q < 0) { atomicOr(eflags, AMG_EFLAG_NONSYM); w[e] = fabs(val[e]); continue; }
-    w[e] = fmax(fabs(val[e]), fabs(val[q]));
+    double m;
+    if (q < 0) {
+      atomicOr(eflags, AMG_EFLAG_NONSYM);
+      m = fabs(val[e]);
+    } else {
+      m = fmax(fabs(val[e]), fabs(val[q]));
+    }
+    if (scaled) {
+      const double dd = di * abs_diag(rp, ci, val, j);
+      if (!(dd > 0.0) || isinf(dd)) { atomicOr(eflags, AMG_EFLAG_ZERO_DIAG); m = 0.0; }
+      else m = m / sqrt(dd);
+    }
+    w[e] = m;
   }
 }
 
@@ -123,7 +143,7 @@ __device__ __forceinline__ int round_count(int n_host, const int *n_dev, const i
 // Picks of the dirty nodes; -1 when a node has no free neighbour left.
 __global__ void k_hem_pick(int nd_host, const int *nd_dev, const int *prev_matched, const int32_t *__restrict__ D,
                            const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
-                           const int32_t *__restrict__ mate, int32_t *__restrict__ pick) {
+                           int tie_larger, const int32_t *__restrict__ mate, int32_t *__restrict__ pick) {
   const int nd = round_count(nd_host, nd_dev, prev_matched);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nd; t += gridDim.x * blockDim.x) {
     const int i = D[t];
@@ -134,8 +154,9 @@ __global__ void k_hem_pick(int nd_host, const int *nd_dev, const int *prev_match
       if (we <= 0.0) continue;
       const int j = ci[e];
       if (mate[j] != HEM_FREE) continue;
-      // columns ascend, so on equal weight the first one met is the smaller index
-      if (best < 0 || we > bw) { best = j; bw = we; }
+      // columns ascend, so on equal weight the first one met is the smaller
+      // index and the last one the larger
+      if (best < 0 || we > bw || (tie_larger && we == bw)) { best = j; bw = we; }
     }
     pick[i] = best;
   }
@@ -206,8 +227,8 @@ __global__ void k_hem_dirty(const int *__restrict__ matched, const int32_t *__re
 __global__ void __launch_bounds__(1024)
     k_hem_rounds_block(int r0, int max_rounds, int cap, int nd, int32_t *__restrict__ Da, int32_t *__restrict__ Db,
                        int *__restrict__ stamp, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                       const double *__restrict__ w, int32_t *__restrict__ mate, int32_t *__restrict__ pick,
-                       int32_t *__restrict__ M, int *out) {
+                       const double *__restrict__ w, int tie_larger, int32_t *__restrict__ mate,
+                       int32_t *__restrict__ pick, int32_t *__restrict__ M, int *out) {
   __shared__ int s_nm, s_nn;
   int32_t *D = Da, *Dn = Db;
   int k = 0, finished = 0, which = 0;
@@ -222,7 +243,7 @@ __global__ void __launch_bounds__(1024)
         if (we <= 0.0) continue;
         const int j = ci[e];
         if (mate[j] != HEM_FREE) continue;
-        if (best < 0 || we > bw) { best = j; bw = we; }
+        if (best < 0 || we > bw || (tie_larger && we == bw)) { best = j; bw = we; }
       }
       pick[i] = best;
     }
@@ -626,7 +647,10 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
                         int *rounds, cudaStream_t st) {
   const int n = in.n;
   const int T = AMG_THREADS;
-  k_weights<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, in.val, S.w, h->eflags); count_launch();
+  const int tie_larger = h->prm.tie_break == AMG_TIE_LARGER ? 1 : 0;
+  k_weights<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, in.val, h->prm.edge_weight == AMG_WEIGHT_SCALED ? 1 : 0, S.w,
+                                      h->eflags);
+  count_launch();
   AMG_TRY(check_flags(h, st));
   // S.flag holds the round stamps and S.first the matched list while the
   // rounds run; the numbering below overwrites both
@@ -642,7 +666,7 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
     if (!frontier_rounds && nd <= HEM_BLOCK_CAP) {
       // small list: rounds inside one block until it grows or the matching ends
       k_hem_rounds_block<<<1, 1024, 0, st>>>(r, HEM_BLOCK_ROUNDS, HEM_BLOCK_CAP, nd, fa, fb, S.flag, in.rp, in.ci,
-                                             S.w, S.mate, S.pick, S.first, S.cnt + 36);
+                                             S.w, tie_larger, S.mate, S.pick, S.first, S.cnt + 36);
       count_launch();
       AMG_CUDA(cudaMemcpyAsync(S.host, S.cnt + 36, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
       AMG_CUDA(cudaStreamSynchronize(st));
@@ -658,7 +682,8 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
       const int *nd_dev = b ? S.cnt + 2 * (b - 1) + 1 : nullptr;
       const int *prev = b ? S.cnt + 2 * (b - 1) : nullptr;
       const int rr = r + b;
-      k_hem_pick<<<grid, T, 0, st>>>(nd, nd_dev, prev, ba, in.rp, in.ci, S.w, S.mate, S.pick); count_launch();
+      k_hem_pick<<<grid, T, 0, st>>>(nd, nd_dev, prev, ba, in.rp, in.ci, S.w, tie_larger, S.mate, S.pick);
+      count_launch();
       const int full = frontier_rounds ? 1 : 0;
       k_hem_match<<<grid, T, 0, st>>>(nd, nd_dev, prev, ba, S.flag, rr, full, S.pick, S.mate, S.first, bb,
                                        S.cnt + 2 * b);
@@ -722,6 +747,8 @@ amg_status validate_params(const amg_params *p) {
   if (p->coarse_solver < 0 || p->coarse_solver > 2) return AMG_ERR_INVALID_ARG;
   if (p->precision < 0 || p->precision > 2) return AMG_ERR_INVALID_ARG;
   if (p->cycle < AMG_CYCLE_V || p->cycle > AMG_CYCLE_F) return AMG_ERR_INVALID_ARG;
+  if (p->tie_break != AMG_TIE_SMALLER && p->tie_break != AMG_TIE_LARGER) return AMG_ERR_INVALID_ARG;
+  if (p->edge_weight != AMG_WEIGHT_ABS && p->edge_weight != AMG_WEIGHT_SCALED) return AMG_ERR_INVALID_ARG;
   return AMG_OK;
 }
 
