@@ -350,9 +350,10 @@ def vcycle_rate(h, b, reps=10):
 
 
 def _solve_timed(sys_, params, krylov, dev, profile=False, tune=False):
-    """Setup + Krylov solve of one system from device-resident inputs; CUDA
-    events on the current stream.  Returns times, the solve info, x and (with
-    profile) the V-cycle's algorithmic bytes and device time."""
+    """Setup + solve of one system from device-resident inputs ("pcg": flexible
+    PCG, "bicgstab", or "amg": AMG as a stationary solver); CUDA events on the
+    current stream.  Returns times, the solve info, x and (with profile) the
+    V-cycle's algorithmic bytes and device time."""
     import torch
 
     from paper_2007_00056_gb300 import amg
@@ -369,9 +370,9 @@ def _solve_timed(sys_, params, krylov, dev, profile=False, tune=False):
         amg.amg_autotune(h)
     if profile:
         amg.amg_profile_enable(h, True)
-    solve = amg.pcg_solve if krylov == "pcg" else amg.bicgstab_solve
+    solve = {"pcg": amg.pcg_solve, "bicgstab": amg.bicgstab_solve, "amg": amg.amg_solve}[krylov]
     kw = {"flexible": True} if krylov == "pcg" else {}
-    info = solve(h, b, x, rtol=RTOL, max_iter=1000, **kw)
+    info = solve(h, b, x, rtol=RTOL, max_iter=5000 if krylov == "amg" else 1000, **kw)
     e2.record(stream)
     torch.cuda.synchronize()
     vc_bytes = vc_ms = 0.0
@@ -449,6 +450,106 @@ def run_configs(dev, peak):
     line("poisson2d_64 coarse_max=64", W.config_poisson2d_64(), amg.AMG_FP64, "pcg", coarse_max=64)
     torch.cuda.empty_cache()
     return out
+
+
+def run_cycles(dev, sys_main):
+    """AMG as a stand-alone solver against AMG-PCG (Sec. 4.4 compares the
+    two), each with the V-, W- and F-cycle, on the benchmark system and on a
+    1024^2 P1 finite-element system (Table 1's P1 shape, 1,048,576 unknowns).
+    Each line: setup and solve time of a second run after a warm-up whose
+    hierarchy is autotuned, cycles or iterations, true relative residual.
+    `amg_solver_over_pcg` is the time to solution of AMG as a solver over that
+    of AMG-PCG, both with V-cycles."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    lines, ratios = [], {}
+    for name, s in (("lognormal3d_128", sys_main), ("fem_p1_1024 jitter 0.25", W.fem_p1_jittered(1024, seed=0))):
+        t = {}
+        for method in ("pcg", "amg"):
+            for cname, kind in (("V", amg.AMG_CYCLE_V), ("W", amg.AMG_CYCLE_W), ("F", amg.AMG_CYCLE_F)):
+                params = amg.amg_default_params(cycle=kind)
+                _solve_timed(s, params, method, dev, tune=True)  # warm-up; its hierarchy is autotuned
+                r = _solve_timed(s, params, method, dev)
+                info = r["info"]
+                tts = r["setup_ms"] + r["solve_ms"]
+                t[(method, cname)] = tts
+                lines.append({"system": name, "n": s.n,
+                              "method": "AMG-PCG (flexible)" if method == "pcg" else "AMG as a solver",
+                              "cycle": cname, "status": amg.status_string(info.status),
+                              "iterations": info.iterations, "rel_res_true": info.rel_res_true,
+                              "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"], "time_to_solution_ms": tts,
+                              "ms_per_iteration": r["solve_ms"] / max(1, info.iterations), "levels": r["levels"]})
+        ratios[name] = t[("amg", "V")] / t[("pcg", "V")]
+        torch.cuda.empty_cache()
+    return {"lines": lines, "amg_solver_over_pcg": ratios, "rtol": RTOL}
+
+
+def run_scaled_weight(dev, sys_main):
+    """The benchmark system with the diagonally scaled edge weight, an option
+    outside the paper (max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|)): hierarchy sizes,
+    setup and FP64 flexible PCG time, second run after an autotuned warm-up.
+    Not the headline: the headline uses the paper's weight |a_ij|."""
+    from paper_2007_00056_gb300 import amg
+
+    params = amg.amg_default_params(edge_weight=amg.AMG_WEIGHT_SCALED)
+    _solve_timed(sys_main, params, "pcg", dev, tune=True)
+    r = _solve_timed(sys_main, params, "pcg", dev)
+    info = r["info"]
+    return {"system": "lognormal3d_128", "edge_weight": "max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|)",
+            "status": amg.status_string(info.status), "iterations": info.iterations,
+            "rel_res_true": info.rel_res_true, "levels": r["levels"], "setup_ms": r["setup_ms"],
+            "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"]}
+
+
+def run_complexity(dev):
+    """Complexity of AMG as a solver (Sec. 4.3 measures it on P1 finite
+    elements at four uniform refinements, Table 1): the P1 family at
+    312^2, 626^2, 1253^2 and 2507^2 unknowns (Table 1's P1L1-P1L4 sizes within
+    0.3%), V-cycles, FP64, time to 1e-8 (setup + solve, second run after an
+    autotuned warm-up), and the exponent p of a least-squares fit t ~ N^p.
+    Also the coarsest-solver comparison of Sec. 4.2 on the 1253^2 system,
+    whose hierarchy stops at 7,089 rows: the same hierarchy with its coarsest
+    level solved by the dense inverse (forced above the default size limit)
+    or by CG."""
+    import math
+
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    lines = []
+    coarse = []
+    for m in (312, 626, 1253, 2507):
+        s = W.fem_p1_jittered(m, seed=0)
+        params = amg.amg_default_params()
+        _solve_timed(s, params, "amg", dev, tune=True)
+        r = _solve_timed(s, params, "amg", dev)
+        info = r["info"]
+        lines.append({"system": f"fem_p1_{m}", "n": s.n, "nnz": s.nnz, "status": amg.status_string(info.status),
+                      "cycles": info.iterations, "rel_res_true": info.rel_res_true, "setup_ms": r["setup_ms"],
+                      "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"],
+                      "levels": r["levels"]})
+        if m == 1253:
+            for name, cs in (("dense inverse", amg.AMG_COARSE_DENSE), ("CG", amg.AMG_COARSE_CG)):
+                pc = amg.amg_default_params(coarse_solver=cs)
+                _solve_timed(s, pc, "amg", dev, tune=True)
+                rc = _solve_timed(s, pc, "amg", dev)
+                coarse.append({"system": f"fem_p1_{m}", "coarsest_solver": name, "coarsest_rows": rc["levels"][-1],
+                               "cycles": rc["info"].iterations, "setup_ms": rc["setup_ms"],
+                               "solve_ms": rc["solve_ms"], "time_to_solution_ms": rc["setup_ms"] + rc["solve_ms"]})
+        del s
+        torch.cuda.empty_cache()
+    xs = [math.log(l["n"]) for l in lines]
+    ys = [math.log(l["time_to_solution_ms"]) for l in lines]
+    mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+    p = sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    return {"lines": lines, "exponent": p, "coarsest_solver": coarse,
+            "note": "AMG as a solver, V-cycle, FP64, rtol 1e-8; the paper reports about N^1.1 on its CPU/GPU "
+                    "implementations"}
 
 
 # ---------------------------------------------------------------------------
@@ -656,9 +757,12 @@ def main():
                           f"samples ({statistics.mean(ts):.3f} s each), extrapolated to {it_gpu} iterations"),
                "time_to_solution_s": t_solve}
 
-    configs = None
+    configs = cycles = complexity = scaled = None
     if rank == 0 and world == 1 and not args.no_configs:
         configs = run_configs(dev, peak)
+        cycles = run_cycles(dev, sys_)
+        complexity = run_complexity(dev)
+        scaled = run_scaled_weight(dev, sys_)
 
     serving = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
@@ -685,7 +789,8 @@ def main():
             "roofline": roofline, "hbm_level0": hbm_level0, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
-            "configs_measured": configs, "serving": serving,
+            "configs_measured": configs, "cycles": cycles, "complexity": complexity,
+            "option_scaled_weight": scaled, "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -22,8 +22,10 @@
 // inverse would take over about 25 ms) are inverted in FP32 and each coarse
 // solve refines in FP64 (r = f - A_L x, x += X r) a
 // number of times fixed here at setup by measuring the convergence on a test
-// vector; when the refinement does not reach FP64 accuracy the inverse is
-// recomputed in FP64.
+// vector: the fewest steps whose normwise backward error
+// ||f - A x||_inf / (||A||_inf ||x||_inf + ||f||_inf) is at most GJ_BACKWARD_TOL,
+// the accuracy of a backward-stable FP64 solve, plus one step of margin.  When
+// the refinement does not get there the inverse is recomputed in FP64.
 #include "common.cuh"
 
 #define GJ_THREADS 1024
@@ -32,6 +34,7 @@
 #define GJ_TJ 256                // update kernel: columns per block (one per thread)
 #define GJ_TI 32                 // update kernel: rows per block
 #define GJ_REFINE_MAX 12         // refinement steps tried at setup
+#define GJ_BACKWARD_TOL (16.0 * 2.220446049250313e-16)  // accepted backward error of the refined solve
 
 namespace {
 
@@ -318,9 +321,7 @@ amg_status gj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   return amg_cuda_status(cudaGetLastError());
 }
 
-// Refinement test: f = A_L v for v_i = 1 + (i mod 7)/8, then x = X f and up to
-// GJ_REFINE_MAX steps x += X (f - A_L x); returns the number of steps after
-// which ||x - v||_inf <= 4 eps ||v||_inf, or -1.
+// Refinement test vector: f = A_L v for v_i = 1 + (i mod 7)/8.
 __global__ void k_refine_rhs(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const double *__restrict__ val, double *__restrict__ f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -349,7 +350,28 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
     const int TB = AMG_THREADS;
     k_refine_rhs<<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, f);
     count_launch();
-    std::vector<double> hx(m);
+    // the coarsest matrix and f on the host, for the backward error of each trial
+    const long long nnz = c.nnz;
+    std::vector<int32_t> hrp(m + 1), hci(nnz);
+    std::vector<double> hval(nnz), hf(m), hx(m);
+    cudaError_t ce = cudaMemcpyAsync(hrp.data(), c.rp, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && nnz)
+      ce = cudaMemcpyAsync(hci.data(), c.ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess && nnz)
+      ce = cudaMemcpyAsync(hval.data(), c.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hf.data(), f, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) {
+      pool_free(f, st);
+      return amg_cuda_status(ce);
+    }
+    double norm_a = 0.0, norm_f = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double rs = 0.0;
+      for (int e = hrp[i]; e < hrp[i + 1]; ++e) rs += std::fabs(hval[e]);
+      norm_a = std::max(norm_a, rs);
+      norm_f = std::max(norm_f, std::fabs(hf[i]));
+    }
     int steps = -1;
     for (int s = 0; s <= GJ_REFINE_MAX; ++s) {
       amg_status rs = dense_refined_solve<double>(h, f, x, s, st, nullptr);
@@ -360,15 +382,17 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
         pool_free(f, st);
         return rs;
       }
-      double err = 0.0;
+      double res = 0.0, norm_x = 0.0;
       bool finite = true;
       for (int i = 0; i < m; ++i) {
-        const double v = 1.0 + (double)(i % 7) / 8.0;
         if (!std::isfinite(hx[i])) finite = false;
-        err = std::max(err, std::fabs(hx[i] - v));
+        norm_x = std::max(norm_x, std::fabs(hx[i]));
+        double ax = 0.0;
+        for (int e = hrp[i]; e < hrp[i + 1]; ++e) ax += hval[e] * hx[hci[e]];
+        res = std::max(res, std::fabs(hf[i] - ax));
       }
       if (!finite) break;
-      if (err <= 4.0 * 2.220446049250313e-16 * (1.0 + 6.0 / 8.0)) {
+      if (res <= GJ_BACKWARD_TOL * (norm_a * norm_x + norm_f)) {
         steps = s;
         break;
       }

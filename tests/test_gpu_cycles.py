@@ -1,5 +1,5 @@
 """W- and F-cycles (Sec. 2 names V, W and F) and AMG as a stand-alone solver
-(Sec. 3.1, compared with AMG-PCG in Sec. 4.2) on the GPU against the oracle.
+(Sec. 3.1, compared with AMG-PCG in Sec. 4.4) on the GPU against the oracle.
 
 Tolerances follow test_gpu_solve.py: a cycle differs from the oracle's only by
 summation order and fused multiply-adds, so 1e-12 relative with a dense
@@ -216,7 +216,7 @@ def test_full_size_lognormal_128_amg_solver_and_w_cycle_pcg():
     its_solver = info.iterations
     x = torch.zeros_like(b)
     info_v = amg.pcg_solve(h, b, x, rtol=1e-8, flexible=True)
-    assert info_v.iterations < its_solver  # Krylov acceleration needs fewer cycles (Sec. 4.2)
+    assert info_v.iterations < its_solver  # Krylov acceleration needs fewer cycles (Sec. 4.4)
     h.close()
     h = amg.amg_setup(rp, ci, val, amg.amg_default_params(cycle=amg.AMG_CYCLE_W))
     x = torch.zeros_like(b)

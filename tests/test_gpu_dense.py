@@ -25,6 +25,8 @@ CASES = [
     ("random_spd_m2083_fp32_ragged_panels", lambda: W.random_spd(2083, 0.004, 6), dict(coarse_max=2083)),
     ("convdiff2d_48_nonsymmetric_fp32_m2304", lambda: W.convdiff2d(48, peclet=300.0), dict(coarse_max=4096)),
     ("lognormal3d_14_fp32_m2744", lambda: W.lognormal3d(14, seed=3), dict(coarse_max=4096)),
+    ("fem_p1_50_fp32_m2500", lambda: W.fem_p1_jittered(50, seed=3), dict(coarse_max=2500)),
+    ("fem_p1_60_fp32_m3600", lambda: W.fem_p1_jittered(60, seed=4), dict(coarse_max=4096)),
     ("aniso3d_20_two_levels", lambda: W.anisotropic3d(20), dict(coarse_max=2100)),
 ]
 
@@ -61,6 +63,26 @@ def test_dense_coarse_fp32_vcycle():
     amg.amg_vcycle(h, b, z)
     # FP32 storage of the right-hand side and the result bounds the accuracy
     assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < 1e-6
+
+
+@pytest.mark.parametrize("make", [lambda: W.fem_p1_jittered(50, seed=3), lambda: W.lognormal3d(14, seed=3)],
+                         ids=["fem_p1_50", "lognormal3d_14"])
+def test_real_valued_coarsest_keeps_fp32_inverse(make):
+    """Matrices with non-integer entries round A v in FP64, so no solve can
+    return v to the last bit; the refinement is accepted on its backward error
+    and the FP32 inverse is kept (the batched solver, which needs an FP64
+    inverse, then refuses the hierarchy)."""
+    s = make()
+    rp, ci, val, b = to_cuda(s)
+    h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=4096))
+    assert h.num_levels == 1 and s.n > 2048
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_batch_pcg([h], [b], [torch.zeros_like(b)], rtol=1e-8)
+    assert e.value.status == amg.AMG_ERR_UNSUPPORTED
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    x = np.linalg.solve(s.dense(), s.b)
+    assert rel_err(z.cpu().numpy(), x) < 1e-11
 
 
 def test_batched_solver_requires_fp64_inverse():
