@@ -170,10 +170,16 @@ __global__ void k_pcg_beta(int n, const double *__restrict__ r, const double *__
   if (is_done(st)) return;
   const bool flex = st->flexible != 0;
   double v[2] = {0.0, 0.0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    double zi = z[i], ri = r[i];
-    v[0] += ri * zi;
-    if (flex) v[1] += zi * (ri - rold[i]);
+  // two loops rather than a test inside one: a predicated-off FP64
+  // instruction still costs its FP64 pipe time on this GPU
+  if (flex) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double zi = z[i], ri = r[i];
+      v[0] += ri * zi;
+      v[1] += zi * (ri - rold[i]);
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += r[i] * z[i];
   }
   double tot[2];
   if (grid_sum_last<2>(v, part, counter, tot) && threadIdx.x == 0) {

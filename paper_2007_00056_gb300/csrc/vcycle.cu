@@ -332,6 +332,15 @@ __global__ void __launch_bounds__(ST_ROWS)
   }
 }
 
+// Scaled levels exist only in the FP16-storage mode, whose vectors are FP32.
+// FP64 kernels compile the scaling out: the compiler turns the pointer tests
+// into predication, and on this GPU a predicated-off FP64 instruction (here
+// the float-to-double conversion and the multiply) still occupies the slow
+// FP64 pipe -- it made the FP64 prolongation FP64-bound at a third of the
+// HBM rate.
+template <typename T>
+struct MayScale { static constexpr bool value = !std::is_same<T, double>::value; };
+
 // Coarse correction of fine row i: x_c[agg_i], times isig_c[agg_i] when the
 // coarse level is scaled and times sig_i when the fine level is scaled.
 template <typename T>
@@ -339,8 +348,10 @@ __device__ __forceinline__ T coarse_corr(const T *__restrict__ xc, const int32_t
                                          const float *__restrict__ sig, const float *__restrict__ isig_c, int i) {
   const int a = __ldg(&agg[i]);
   T c = __ldg(&xc[a]);
-  if (isig_c) c *= (T)__ldg(&isig_c[a]);
-  if (sig) c *= (T)__ldg(&sig[i]);
+  if constexpr (MayScale<T>::value) {
+    if (isig_c) c *= (T)__ldg(&isig_c[a]);
+    if (sig) c *= (T)__ldg(&sig[i]);
+  }
   return c;
 }
 
@@ -373,14 +384,31 @@ __global__ void k_prolong(int n, const T *__restrict__ x, const int32_t *__restr
   if (is_done(st)) return;
   const long long S = (long long)gridDim.x * blockDim.x;
   for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
+    // the round's aggregate ids and x first (read once: streaming loads),
+    // then the dependent gathers of x_c, so both waits overlap across the round
     T xv[STREAM_U], cv[STREAM_U];
+    int a[STREAM_U];
 #pragma unroll
     for (int u = 0; u < STREAM_U; ++u) {
       const long long i = i0 + u * S;
-      if (i < n) {
-        xv[u] = x[i];
-        cv[u] = coarse_corr(xc, agg, sig, isig_c, (int)i);
+      a[u] = i < n ? __ldcs(&agg[i]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      xv[u] = i < n ? __ldcs(&x[i]) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < STREAM_U; ++u) {
+      const long long i = i0 + u * S;
+      T c = __ldg(&xc[a[u]]);
+      if constexpr (MayScale<T>::value) {
+        if (i < n) {
+          if (isig_c) c *= (T)__ldg(&isig_c[a[u]]);
+          if (sig) c *= (T)__ldg(&sig[i]);
+        }
       }
+      cv[u] = c;
     }
 #pragma unroll
     for (int u = 0; u < STREAM_U; ++u) {
@@ -400,12 +428,18 @@ __global__ void k_restrict(int nc, const int32_t *__restrict__ mrp, const int32_
   for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
     int b = mrp[I], e = mrp[I + 1];
     int i = mem[b];
-    T s = sig ? t[i] * (T)sig[i] : t[i];
-    for (int k = b + 1; k < e; ++k) {
-      i = mem[k];
-      s += sig ? t[i] * (T)sig[i] : t[i];
+    if constexpr (MayScale<T>::value) {
+      T s = sig ? t[i] * (T)sig[i] : t[i];
+      for (int k = b + 1; k < e; ++k) {
+        i = mem[k];
+        s += sig ? t[i] * (T)sig[i] : t[i];
+      }
+      fc[I] = isig_c ? s * (T)isig_c[I] : s;
+    } else {
+      T s = t[i];
+      for (int k = b + 1; k < e; ++k) s += t[mem[k]];
+      fc[I] = s;
     }
-    fc[I] = isig_c ? s * (T)isig_c[I] : s;
   }
 }
 
