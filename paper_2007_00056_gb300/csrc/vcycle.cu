@@ -558,22 +558,44 @@ __global__ void k_gemv32(int m, const float *__restrict__ X, const V *__restrict
   if (is_done(st)) return;
   const int lane = threadIdx.x & 31;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  // rows read as float4 when every row starts on 16 bytes (four partial sums
-  // per lane), else one element at a time
-  const bool vec = (m % 4) == 0 && ((uintptr_t)X & 15) == 0;
+  // rows (and an FP32 v) read as float4 when every row starts on 16 bytes
+  // (four partial sums per lane), in batches of GEMV_BATCH loads per lane
+  // issued before their products so that enough of the row is in flight;
+  // else one element at a time
+  constexpr int GEMV_BATCH = 8;
+  const bool vec = (m % 4) == 0 && ((uintptr_t)X & 15) == 0 &&
+                   (!std::is_same<V, float>::value || ((uintptr_t)v & 15) == 0);
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < m; i += warps) {
     const float *row = X + (size_t)i * m;
     float s = 0.0f;
     if (vec) {
       const float4 *row4 = (const float4 *)row;
+      const int m4 = m / 4;
       float s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-#pragma unroll 4
-      for (int q = lane; q < m / 4; q += 32) {
-        const float4 a = __ldg(&row4[q]);
-        s = fmaf(a.x, (float)v[4 * q], s);
-        s1 = fmaf(a.y, (float)v[4 * q + 1], s1);
-        s2 = fmaf(a.z, (float)v[4 * q + 2], s2);
-        s3 = fmaf(a.w, (float)v[4 * q + 3], s3);
+      for (int q0 = lane; q0 < m4; q0 += 32 * GEMV_BATCH) {
+        float4 a[GEMV_BATCH], b[GEMV_BATCH];
+#pragma unroll
+        for (int u = 0; u < GEMV_BATCH; ++u) {
+          const int q = q0 + 32 * u;
+          a[u] = q < m4 ? __ldg(&row4[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < GEMV_BATCH; ++u) {
+          const int q = q0 + 32 * u;
+          if constexpr (std::is_same<V, float>::value) {
+            b[u] = q < m4 ? __ldg(&((const float4 *)v)[q]) : make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            b[u] = q < m4 ? make_float4((float)v[4 * q], (float)v[4 * q + 1], (float)v[4 * q + 2], (float)v[4 * q + 3])
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < GEMV_BATCH; ++u) {
+          s = fmaf(a[u].x, b[u].x, s);
+          s1 = fmaf(a[u].y, b[u].y, s1);
+          s2 = fmaf(a[u].z, b[u].z, s2);
+          s3 = fmaf(a[u].w, b[u].w, s3);
+        }
       }
       s = (s + s1) + (s2 + s3);
     } else {
