@@ -92,7 +92,8 @@ typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
  *   omega        damped-Jacobi weight of the smoother S_k (2/3)
  *   nu_pre, nu_post  pre- and post-smoothing sweeps (1, 1; Table 2 uses 6, 6)
  *   coarse_solver    AMG_COARSE_AUTO: dense if the coarsest level has <= coarse_max
- *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2).
+ *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2),
+ *                on one thread block cluster up to 2048 rows, else on the whole GPU.
  *                The dense solve applies the inverse formed at setup by blocked
  *                Gauss-Jordan elimination with partial pivoting: in FP64 up to
  *                2048 rows; above that in FP32 with a fixed number of FP64
@@ -266,6 +267,13 @@ amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream);
  * hardware conversions.  Device pointers, n >= 0; AMG_ERR_INVALID_ARG for a
  * null pointer with n > 0.  Asynchronous on `stream`. */
 amg_status amg_selftest_convert(int64_t n, const double *d_in, float *d_f32, double *d_f64, amg_stream_t stream);
+
+/* Coarsest CG form of h: the number of CTAs of the thread block cluster that
+ * solves a small coarsest level (16 or 8, for at most 2048 rows when the
+ * device schedules such a cluster), 0 when the grid-wide cooperative kernel
+ * solves it, -1 when the coarsest level is solved by the dense inverse or h
+ * is NULL. */
+int amg_coarse_cg_cluster_size(const amg_hierarchy *h);
 
 /* Kernel kinds reported by the per-kernel profiler.  Each kind is tracked per
  * level (0 = finest); Krylov kinds are reported at level 0. */

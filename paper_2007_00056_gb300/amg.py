@@ -37,7 +37,7 @@ EXPORTS = (
     "amg_level_info", "amg_export_level", "amg_setup_rounds", "amg_destroy", "amg_status_string",
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
-    "amg_selftest_wait_timeout", "amg_selftest_convert", "amg_last_cuda_error",
+    "amg_selftest_wait_timeout", "amg_selftest_convert", "amg_last_cuda_error", "amg_coarse_cg_cluster_size",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
@@ -132,6 +132,7 @@ def lib(build_if_missing: bool = False):
             l.amg_level_set_config.argtypes = [vp, i32, i32, i32, i32]
             l.amg_level_config.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             l.amg_coarse_cg_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, C.POINTER(i32)]
+            l.amg_coarse_cg_cluster_size.argtypes = [vp]
             _lib = l
     return _lib
 
@@ -337,6 +338,12 @@ def amg_profile_table(h: Hierarchy):
                                  gbs=(by / (ms * 1e-3) / 1e9) if ms > 0 else 0.0))
     rows.sort(key=lambda r: -r["ms"])
     return rows
+
+
+def amg_coarse_cg_cluster_size(h: Hierarchy) -> int:
+    """CTAs of the cluster that solves the coarsest level by CG (0: the whole
+    GPU; -1: dense inverse)."""
+    return lib().amg_coarse_cg_cluster_size(h.handle)
 
 
 NOALLOC_MAX_N = 262144

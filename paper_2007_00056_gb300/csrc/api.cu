@@ -230,6 +230,11 @@ extern "C" void amg_destroy(amg_hierarchy *h) {
   delete h;
 }
 
+extern "C" int amg_coarse_cg_cluster_size(const amg_hierarchy *h) {
+  if (!h || h->dense) return -1;
+  return h->cg.cl.size;
+}
+
 extern "C" unsigned long long amg_kernel_launches(void) { return __atomic_load_n(&g_amg_launches, __ATOMIC_RELAXED); }
 
 extern "C" amg_status amg_profile_enable(amg_hierarchy *h, int on) {

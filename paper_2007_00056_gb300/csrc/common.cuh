@@ -94,6 +94,16 @@ struct Profiler {
 // memory (CG_STATE vectors of n + AMG_PAD, by position), reduction partials,
 // barrier counter and iteration counters.
 #define CG_STATE 10                 // r, u, w, m, n, z, q, s, p, x
+// Coarsest CG on one thread block cluster (cluster_cg.cu): used for coarsest
+// levels of at most CCG_MAX_N rows when the device schedules the cluster;
+// size = 0 leaves the level to the grid-wide kernel.
+#define CCG_MAX_N 2048
+struct ClusterCG {
+  int size = 0;       // CTAs in the cluster (16 or 8)
+  int rows_per = 0;   // rows per CTA
+  size_t smem = 0;    // dynamic shared memory per CTA
+};
+
 struct CoarseCG {
   int n = 0, grid = 0, threads = 0;
   size_t smem = 0;           // dynamic shared memory per block (matrix slice staging)
@@ -105,6 +115,7 @@ struct CoarseCG {
   unsigned *bar = nullptr;   // [0] monotonic arrival counter
   int *iters = nullptr;
   unsigned long long *iters_total = nullptr;  // sum of CG iterations over launches
+  ClusterCG cl;              // cluster form for small levels (cl.size = 0: not used)
 };
 
 struct amg_hierarchy {
@@ -283,6 +294,11 @@ template <typename T>
 amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st);
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
+amg_status cluster_cg_config(int n, ClusterCG *cc);
+template <typename T>
+amg_status cluster_cg_launch(const ClusterCG &cc, int n, const int32_t *rp, const int32_t *ci, const double *val,
+                             const double *dinv, const T *f, T *x, int *iters, unsigned long long *iters_total,
+                             const KState *st, cudaStream_t s);
 amg_status read_eflags(amg_hierarchy *h, cudaStream_t s, unsigned *flags);
 #ifndef CG_THREADS
 #define CG_THREADS 512

@@ -1299,6 +1299,13 @@ void coarse_solve(amg_hierarchy *h, const T *f, T *x, cudaStream_t s, const KSta
     k_gemv_dense<T><<<grid_for((long long)c.n * 32, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, h->ainv, f, x, st);
     return;
   }
+  if (h->cg.cl.size > 0) {
+    // small level: one thread block cluster (the launch error, if any, is
+    // reported by the caller's cudaGetLastError)
+    LaunchScope ls(h, s, PK_COARSE_CG, h->L, bytes_A(c, 8) + 10.0 * 8.0 * c.n);
+    cluster_cg_launch<T>(h->cg.cl, c.n, c.rp, c.ci, c.val, c.dinv, f, x, h->cg.iters, h->cg.iters_total, st, s);
+    return;
+  }
   cudaMemsetAsync(h->cg.bar, 0, 2 * sizeof(unsigned), s);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(h->cg.grid);
@@ -1467,6 +1474,7 @@ amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
   AMG_CUDA(cudaMemsetAsync(cg.iters_total, 0, sizeof(unsigned long long), s));
   AMG_TRY(coarse_cg_config(c.n, &cg));
   AMG_TRY(coarse_cg_prepare(c.n, c.rp, cg, s));
+  AMG_TRY(cluster_cg_config(c.n, &cg.cl));
   return AMG_OK;
 }
 
