@@ -396,27 +396,18 @@ amg_status pcg_iteration(amg_hierarchy *h, cudaStream_t s) {
   const int n = l.n;
   KDISPATCH(l, k_pcg_spmv, n, l.rp, l.ci, l.val, h->kp, h->kq, h->part, h->counter + KSLOT_A, h->st);
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 6.0 * 8.0 * n);
-
     k_pcg_update<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kr, h->krold, h->kp, h->kq, h->part,
                                                       h->counter + KSLOT_B, h->st);
-
   }
   AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-
     k_pcg_beta<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->krold, h->kz, h->part, h->counter + KSLOT_C, h->st);
-
   }
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-
     k_pcg_p<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kz, h->kp, h->st);
-
   }
   return amg_cuda_status(cudaGetLastError());
 }
@@ -428,28 +419,19 @@ amg_status bicg_iteration(amg_hierarchy *h, cudaStream_t s) {
   AMG_TRY(vcycle_run(h, h->kp, h->kph, s, h->st));
   KDISPATCH2(l, k_bicg_spmv, 1, n, l.rp, l.ci, l.val, h->kph, h->kq, h->krb, h->part, h->counter + KSLOT_A, h->st);
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-
     k_bicg_s<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->ks, h->part, h->counter + KSLOT_B, h->st);
-
   }
   AMG_TRY(vcycle_run(h, h->ks, h->ksh, s, h->st));
   KDISPATCH2(l, k_bicg_spmv, 2, n, l.rp, l.ci, l.val, h->ksh, h->kt, h->ks, h->part, h->counter + KSLOT_A, h->st);
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 9.0 * 8.0 * n);
-
     k_bicg_xr<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kr, h->ks, h->kt, h->kph, h->ksh, h->krb, h->part,
                                                    h->counter + KSLOT_C, h->st);
-
   }
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 4.0 * 8.0 * n);
-
     k_bicg_p<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->kp, h->st);
-
   }
   return amg_cuda_status(cudaGetLastError());
 }
@@ -593,11 +575,8 @@ extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, doub
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, flexible ? 1 : 0, s));
   AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-
     k_pcg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kz, h->kp, h->part, h->counter + KSLOT_B, h->st);
-
   }
   AMG_CUDA(cudaGetLastError());
   AMG_TRY(run_iterations(h, pcg_iteration, &h->g_pcg, &h->g_pcg_nodes, s));
@@ -613,11 +592,8 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
   const int n = h->lev[0].n;
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, 0, s));
   {
-
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 4.0 * 8.0 * n);
-
     k_bicg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->krb, h->kp, h->part, h->counter + KSLOT_B, h->st);
-
   }
   AMG_CUDA(cudaGetLastError());
   AMG_TRY(run_iterations(h, bicg_iteration, &h->g_bicg, &h->g_bicg_nodes, s));
@@ -625,11 +601,8 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
   AMG_CUDA(cudaStreamSynchronize(s));
   if (h->st_host->half == 1)
     {
-
       LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-
       k_axpy_half<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kph, h->st);
-
     }
   return end_solve(h, d_x, s, info);
 }
