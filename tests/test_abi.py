@@ -44,6 +44,7 @@ def test_default_params_and_strings(lib):
     p = amg.amg_default_params()
     assert (p.passes, p.max_levels, p.coarse_max, p.nu_pre, p.nu_post) == (2, 10, 4096, 1, 1)
     assert p.stall_ratio == 0.85 and abs(p.omega - 2.0 / 3.0) < 1e-16
+    assert (p.cycle, p.tie_break, p.edge_weight) == (amg.AMG_CYCLE_V, amg.AMG_TIE_SMALLER, amg.AMG_WEIGHT_ABS)
     assert lib.amg_default_params(None) == amg.AMG_ERR_INVALID_ARG
     for s in range(10):
         assert len(amg.status_string(s)) >= 2
@@ -64,10 +65,15 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     assert lib.amg_setup(5, 10, 8, 8, 8, C.byref(bad), None, C.byref(out)) == amg.AMG_ERR_INVALID_ARG
     bad = amg.amg_default_params(omega=2.5)
     assert lib.amg_setup(5, 10, 8, 8, 8, C.byref(bad), None, C.byref(out)) == amg.AMG_ERR_INVALID_ARG
+    for kw in (dict(cycle=3), dict(cycle=-1), dict(tie_break=2), dict(edge_weight=-1)):
+        bad = amg.amg_default_params(**kw)
+        assert lib.amg_setup(5, 10, 8, 8, 8, C.byref(bad), None, C.byref(out)) == amg.AMG_ERR_INVALID_ARG
     assert lib.amg_vcycle(None, 8, 16, None) == amg.AMG_ERR_INVALID_ARG
     info = amg.amg_solve_info()
     assert lib.pcg_solve(None, 8, 16, 1e-8, 10, 0, None, C.byref(info)) == amg.AMG_ERR_INVALID_ARG
     assert lib.bicgstab_solve(None, 8, 16, 1e-8, 10, None, C.byref(info)) == amg.AMG_ERR_INVALID_ARG
+    assert lib.amg_solve(None, 8, 16, 1e-8, 10, None, C.byref(info)) == amg.AMG_ERR_INVALID_ARG
+    assert lib.amg_coarse_cg_cluster_size(None) == -1
     assert lib.amg_num_levels(None) == -1
     assert lib.amg_setup_rounds(None, 0, 0) == -1
     lib.amg_destroy(None)  # no-op
