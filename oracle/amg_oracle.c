@@ -13,7 +13,7 @@
  * no blocking, fusion or reordering.  Sums run in plain index order.  Build with
  * -O2 -ffp-contract=off so that no multiply-add is contracted.
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - edge weight of {i,j}: w_ij = max(|a_ij|, |a_ji|), diagonal and explicit
  *    zeros skipped (Sec. 2.1.1 and Algorithm 3 put both directed entries in
  *    the edge list, so a pair is first met at the larger one);
