@@ -13,8 +13,10 @@
 // barrier rather than an atomic counter in global memory.  A coarsest level of
 // up to about two thousand rows is bound by synchronisation and latency, not
 // by FP64 work, and 16 SMs with the cluster barrier finish an iteration
-// 10-15% sooner than the grid-wide kernel (5.6 against 6.6 us at 1728 rows);
+// 15-20% sooner than the grid-wide kernel (5.2 against 6.6 us at 1728 rows);
 // from about four thousand rows the FP64 work of 16 SMs makes it slower.
+// 128 threads per CTA (one row per thread up to 2048 rows): block barriers
+// over four warps cost less than over sixteen, and they dominate the stalls.
 //
 // Rows are split into C contiguous ranges of `rows_per` rows (the last ones
 // may be short or empty); the owner of column c is c / rows_per.  m and the
@@ -30,7 +32,7 @@
 
 namespace cgr = cooperative_groups;
 
-#define CCG_THREADS 512
+#define CCG_THREADS 128
 #define CCG_RTOL 1e-12
 #define CCG_MAXIT 1000
 #define CCG_GATHER 8      // neighbours gathered per round by one thread
