@@ -87,3 +87,40 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(amg, "lib_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         amg.lib()
+
+
+def _header_text():
+    text = open(os.path.join(ROOT, "include", "amg.h")).read()
+    return re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+
+
+def test_binding_constants_match_the_header():
+    """Every enum constant the binding defines has the header's value."""
+    from paper_2007_00056_gb300 import amg
+
+    consts = dict((m.group(1), int(m.group(2)))
+                  for m in re.finditer(r"\b(AMG_[A-Z0-9_]+)\s*=\s*(-?\d+)", _header_text()))
+    checked = 0
+    for name, value in consts.items():
+        if hasattr(amg, name):
+            assert getattr(amg, name) == value, name
+            checked += 1
+    assert checked >= 20
+
+
+def test_params_struct_layout_matches_the_header():
+    """amg_params and amg_solve_info: same fields, order and C types as the header."""
+    from paper_2007_00056_gb300 import amg
+
+    text = _header_text()
+    ctype = {"int": C.c_int, "double": C.c_double, "amg_status": C.c_int}
+    for struct, cls in (("amg_params", amg.amg_params), ("amg_solve_info", amg.amg_solve_info)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + struct + r"\s*;", text).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            typ, names = decl.split(None, 1)
+            fields += [(n.strip(), ctype[typ]) for n in names.split(",")]
+        assert [(n, t) for n, t in cls._fields_] == fields, struct
