@@ -36,8 +36,8 @@
  *    p_0 = r_0, rbar_0 = r_0 and p_{j+1} = r_{j+1} + beta (p_j - omega A p~_j);
  *  - the coarsest solve of Algorithm 1 is A_L^{-1} f_L by dense LU with partial
  *    pivoting, or, when A_L is too large for a dense factor, Jacobi-PCG to a
- *    relative residual of 1e-12 (the CG coarse solver of Sec. 4.2), written
- *    in the Chronopoulos-Gear arrangement of CG;
+ *    relative residual of 1e-12 (the CG coarse solver of Sec. 4.2), in the
+ *    textbook recurrence of preconditioned CG;
  *  - the W- and F-cycles, which Sec. 2 and Sec. 3 only name, take their
  *    textbook form: the coarse correction of level k is gamma = 2 cycles of
  *    level k+1 (W), or one F-cycle then one V-cycle of level k+1 (F), the
@@ -662,50 +662,39 @@ int orc_level_export(const orc_hier *h, int k, int *rp, int *ci, double *val, in
 
 /* Jacobi-preconditioned CG on the coarsest matrix from x = 0 until
  * ||r|| <= 1e-12 ||f|| or 1000 iterations (CG as the coarse solver, Sec. 4.2),
- * in the Chronopoulos-Gear arrangement of CG, which computes the three inner
- * products of an iteration together.  With u = D^-1 r and w = A u:
- *   gamma = (r,u), delta = (w,u), alpha_0 = gamma_0/delta_0, beta_0 = 0;
- *   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
- *   beta' = gamma'/gamma, alpha' = gamma'/(delta' - beta' gamma'/alpha).
- * In exact arithmetic the iterates are those of standard preconditioned CG. */
+ * in the textbook recurrence of preconditioned CG with M = D (the diagonal):
+ *   r = f, z = D^-1 r, p = z;  repeat: q = A p, alpha = (r,z)/(p,q),
+ *   x += alpha p, r -= alpha q, stop if ||r|| is small enough,
+ *   z = D^-1 r, beta = (r,z)_new/(r,z)_old, p = z + beta p. */
 static int coarse_cg(orc_hier *h, const double *f, double *x) {
   const orc_level *l = &h->lev[h->L];
   int n = l->n;
   double *r = (double *)malloc((size_t)n * sizeof(double));
-  double *u = (double *)malloc((size_t)n * sizeof(double));
-  double *w = (double *)malloc((size_t)n * sizeof(double));
-  double *p = (double *)calloc((size_t)n, sizeof(double));
-  double *s = (double *)calloc((size_t)n, sizeof(double));
+  double *z = (double *)malloc((size_t)n * sizeof(double));
+  double *p = (double *)malloc((size_t)n * sizeof(double));
+  double *q = (double *)malloc((size_t)n * sizeof(double));
   for (int i = 0; i < n; ++i) { x[i] = 0.0; r[i] = f[i]; }
   double fn = norm2(n, f);
   int it = 0;
   if (fn > 0.0) {
-    for (int i = 0; i < n; ++i) u[i] = r[i] / l->diag[i];
-    orc_spmv(n, l->rp, l->ci, l->val, u, w);
-    double gamma = dot(n, r, u);
-    double delta = dot(n, w, u);
-    double alpha = gamma / delta, beta = 0.0;
+    for (int i = 0; i < n; ++i) { z[i] = r[i] / l->diag[i]; p[i] = z[i]; }
+    double rz = dot(n, r, z);
     for (it = 1; it <= 1000; ++it) {
-      for (int i = 0; i < n; ++i) {
-        p[i] = u[i] + beta * p[i];
-        s[i] = w[i] + beta * s[i];
-        x[i] += alpha * p[i];
-        r[i] -= alpha * s[i];
-      }
-      for (int i = 0; i < n; ++i) u[i] = r[i] / l->diag[i];
-      orc_spmv(n, l->rp, l->ci, l->val, u, w);
-      double gamma_new = dot(n, r, u);
-      delta = dot(n, w, u);
-      if (norm2(n, r) <= 1e-12 * fn) break;
-      beta = gamma_new / gamma;
-      alpha = gamma_new / (delta - beta * gamma_new / alpha);
-      gamma = gamma_new;
+      orc_spmv(n, l->rp, l->ci, l->val, p, q);
+      double alpha = rz / dot(n, p, q);
       if (!isfinite(alpha)) break;
+      for (int i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+      if (norm2(n, r) <= 1e-12 * fn) break;
+      for (int i = 0; i < n; ++i) z[i] = r[i] / l->diag[i];
+      double rz_new = dot(n, r, z);
+      double beta = rz_new / rz;
+      rz = rz_new;
+      for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
     }
     if (it > 1000) it = 1000;
   }
   h->coarse_cg_iters = it;
-  free(r); free(u); free(w); free(p); free(s);
+  free(r); free(z); free(p); free(q);
   return ORC_OK;
 }
 
@@ -783,6 +772,16 @@ static double true_rel_res(const orc_level *l, const double *b, const double *x,
   return r;
 }
 
+/* Optional record of the search directions of orc_pcg, for tests of the CG
+ * recurrence: while set, iteration j (1-based, j <= trace_max) stores its
+ * direction p_j at trace[(j - 1) n .. j n - 1].  Not thread-safe. */
+static double *pcg_trace = NULL;
+static int pcg_trace_max = 0;
+void orc_set_pcg_trace(double *trace, int max_vectors) {
+  pcg_trace = trace;
+  pcg_trace_max = trace ? max_vectors : 0;
+}
+
 /* AMG-preconditioned CG (Sec. 3.2, Algorithm 4), with the sign of the
  * residual update read as r_{j+1} = r_j - alpha A p_j.  x holds x_0 on entry.
  * Stops once ||r_j|| <= rtol ||b|| (checked after each residual update).
@@ -817,6 +816,7 @@ int orc_pcg(orc_hier *h, const double *b, double *x, double rtol, int max_iter, 
     for (int i = 0; i < n; ++i) p[i] = z[i];
     double rz = dot(n, r, z);
     for (it = 1; it <= max_iter; ++it) {
+      if (it <= pcg_trace_max) memcpy(pcg_trace + (size_t)(it - 1) * n, p, (size_t)n * sizeof(double));
       orc_spmv(n, l->rp, l->ci, l->val, p, q);
       double pq = dot(n, p, q);
       if (pq == 0.0 || !isfinite(pq) || !isfinite(rz)) { st = ORC_ERR_BREAKDOWN; break; }

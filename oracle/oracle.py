@@ -18,6 +18,7 @@ _SRC = os.path.join(_HERE, "amg_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
+_trace_lock = threading.Lock()
 _lib = None
 
 # status codes of the oracle (mirrors the meaning, not the code, of the library's)
@@ -104,6 +105,7 @@ def lib():
             l.orc_level_export.argtypes = [C.c_void_p, C.c_int, _i32p, _i32p, _f64p, C.c_void_p]
             l.orc_vcycle.argtypes = [C.c_void_p, _f64p, _f64p]
             l.orc_pcg.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.c_int, C.POINTER(_Info)]
+            l.orc_set_pcg_trace.argtypes = [C.c_void_p, C.c_int]
             l.orc_bicgstab.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.POINTER(_Info)]
             l.orc_amg_solve.argtypes = [C.c_void_p, _f64p, _f64p, C.c_double, C.c_int, C.POINTER(_Info)]
             _lib = l
@@ -275,6 +277,18 @@ class Hierarchy:
         lib().orc_pcg(self._h, np.ascontiguousarray(b, dtype=np.float64), x, rtol, max_iter,
                       int(flexible), C.byref(info))
         return x, SolveInfo(info)
+
+    def pcg_directions(self, b, rtol=1e-8, max_iter=1000, flexible=False):
+        """PCG as pcg() does, also returning its search directions: (x, info,
+        P) with P[j - 1] the direction p_j of iteration j."""
+        P = np.zeros((max(max_iter, 1), self.n))
+        with _trace_lock:
+            lib().orc_set_pcg_trace(P.ctypes.data_as(C.c_void_p), max_iter)
+            try:
+                x, info = self.pcg(b, rtol=rtol, max_iter=max_iter, flexible=flexible)
+            finally:
+                lib().orc_set_pcg_trace(None, 0)
+        return x, info, P[:info.iterations]
 
     def amg_solve(self, b, x0=None, rtol=1e-8, max_iter=1000):
         """AMG as a solver: x_{j+1} = x_j + M^{-1}(b - A x_j) until the tolerance."""

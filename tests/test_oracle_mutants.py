@@ -30,10 +30,19 @@ MUTANTS = [
      "test_pcg_matches_dense_solve_to_1e10"),
     ("bicgstab_p_update", "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];",
      "test_krylov_finite_termination_two_eigenvalues"),
-    ("coarse_cg_steepest_descent", "      beta = gamma_new / gamma;\n", "      beta = 0.0 * gamma_new / gamma;\n",
+    ("coarse_cg_steepest_descent", "      double beta = rz_new / rz;\n", "      double beta = 0.0 * rz_new / rz;\n",
      "test_coarse_cg_solver_agrees_with_dense or test_coarse_cg_finite_termination_two_eigenvalues"),
-    ("coarse_cg_alpha_without_correction", "alpha = gamma_new / (delta - beta * gamma_new / alpha);",
-     "alpha = gamma_new / delta;", "test_coarse_cg_finite_termination_two_eigenvalues"),
+    ("coarse_cg_residual_sign", "x[i] += alpha * p[i]; r[i] -= alpha * q[i];",
+     "x[i] += alpha * p[i]; r[i] += alpha * q[i];",
+     "test_coarse_cg_solver_agrees_with_dense or test_coarse_cg_finite_termination_two_eigenvalues"),
+    ("flexible_beta_sign", "beta = s / rz;", "beta = -s / rz;",
+     "test_flexible_beta_keeps_consecutive_directions_a_conjugate"),
+    ("flexible_beta_is_fletcher_reeves", "s += z[i] * (r[i] - rold[i]);", "s += z[i] * r[i];",
+     "test_flexible_beta_keeps_consecutive_directions_a_conjugate"),
+    ("stall_rule_not_strict", "if ((double)cur_n / (double)f->n > prm->stall_ratio) {",
+     "if ((double)cur_n / (double)f->n >= prm->stall_ratio) {", "test_hierarchy_stops_before_a_stalled_level"),
+    ("stall_ratio_against_finest", "if ((double)cur_n / (double)f->n > prm->stall_ratio) {",
+     "if ((double)cur_n / (double)h->lev[0].n > prm->stall_ratio) {", "test_hierarchy_stops_before_a_stalled_level"),
     ("lu_no_pivoting", "if (fabs(a[(size_t)i * n + k]) > best)", "if (0 && fabs(a[(size_t)i * n + k]) > best)",
      "test_dense_lu_matches_numpy"),
     ("desc_tie_order_wrong_direction", "if (a->v != b->v) return a->v > b->v ? -1 : 1;",

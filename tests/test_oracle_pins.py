@@ -259,6 +259,43 @@ def test_hierarchy_levels_are_galerkin_products():
                                    rtol=1e-12, atol=1e-12)
 
 
+def _two_pass_level_sizes(s, levels):
+    """Sizes of the candidate levels of s built from the pinned building blocks
+    (greedy matching, numbering by smallest member, Galerkin product), two
+    pairwise passes per level, without any stop rule."""
+    rp, ci, val = s.rp, s.ci, s.val
+    sizes = [len(rp) - 1]
+    for _ in range(levels):
+        for _ in range(2):
+            agg, nc = O.aggregates(O.match_greedy(rp, ci, val))
+            rp, ci, val = O.galerkin(rp, ci, val, agg, nc)
+        sizes.append(len(rp) - 1)
+    return sizes
+
+
+def test_hierarchy_stops_before_a_stalled_level():
+    """Reading of Table 2's level rule: a level is not added when its size
+    ratio N_{k+1}/N_k to the level above exceeds stall_ratio.  On a lognormal
+    8^3 system the hub-star stall sets in after four levels (ratios 0.31, 0.38,
+    0.57, 0.77, then 0.89): with coarse_max = 1 and 30 allowed levels, only the
+    stall can stop the hierarchy, and it must stop exactly there.  A ratio
+    equal to stall_ratio does not stop it (the rule is a strict >)."""
+    s = W.lognormal3d(8, seed=1)
+    cand = _two_pass_level_sizes(s, 8)
+    ratios = [cand[k + 1] / cand[k] for k in range(len(cand) - 1)]
+    first_stall = next(k for k, r in enumerate(ratios) if r > 0.85)
+    assert first_stall >= 3  # the stall is measured against the level above, not the finest
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=1, max_levels=30, stall_ratio=0.85)
+    assert h.sizes() == cand[:first_stall + 1]
+    # stall_ratio equal to the ratio of the last kept level: that level stays
+    eq = ratios[first_stall - 1]
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=1, max_levels=30, stall_ratio=eq)
+    assert h.sizes() == cand[:first_stall + 1]
+    # just below it: that level is the first stalled one and is not added
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=1, max_levels=30, stall_ratio=np.nextafter(eq, 0.0))
+    assert h.sizes() == cand[:first_stall]
+
+
 # --------------------------------------------------------------------------
 # Coarse solve, V-cycle, Krylov
 # --------------------------------------------------------------------------
@@ -428,6 +465,34 @@ def test_krylov_finite_termination_two_eigenvalues():
     assert info.status == O.OK and info.iterations <= 2
     _, info = h.bicgstab(b, rtol=1e-13, max_iter=50)
     assert info.status == O.OK and info.iterations <= 2
+
+
+@pytest.mark.parametrize("coarse_solver", [1, 2])
+def test_flexible_beta_keeps_consecutive_directions_a_conjugate(coarse_solver):
+    """Flexible CG (reading R-C9): beta = (z_{j+1}, r_{j+1} - r_j)/(z_j, r_j).
+    With r_{j+1} - r_j = -alpha A p_j and alpha = (r_j, z_j)/(p_j, A p_j) this
+    beta equals -(z_{j+1}, A p_j)/(p_j, A p_j), so p_{j+1} = z_{j+1} + beta p_j
+    is A-conjugate to p_j for ANY preconditioner.  The F-cycle is a fixed but
+    nonsymmetric M^{-1} (pinned below), where the Fletcher-Reeves beta loses
+    that property; the check therefore tells the two formulas apart."""
+    s = W.lognormal3d(12, seed=3)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=100, cycle=2, coarse_solver=coarse_solver)
+    a = s.dense()
+
+    def worst(P):
+        out = 0.0
+        for j in range(len(P) - 1):
+            ap = a @ P[j]
+            out = max(out, abs(P[j + 1] @ ap) / np.sqrt((P[j + 1] @ (a @ P[j + 1])) * (P[j] @ ap)))
+        return out
+
+    x, info, P = h.pcg_directions(s.b, rtol=1e-10, max_iter=60, flexible=True)
+    assert info.status == O.OK and len(P) >= 10
+    assert worst(P) < 1e-12
+    np.testing.assert_allclose(x, np.linalg.solve(a, s.b), rtol=1e-8, atol=1e-10)
+    # the same check on Fletcher-Reeves directions fails by orders of magnitude
+    _, _, P_fr = h.pcg_directions(s.b, rtol=1e-10, max_iter=60, flexible=False)
+    assert worst(P_fr) > 1e-6
 
 
 def test_coarse_cg_finite_termination_two_eigenvalues():
