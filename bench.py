@@ -1,13 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 aggregation-AMG PCG solver.
 
-Workload (one step): the 3D 7-point lognormal-coefficient diffusion system on
-128^3 cells (2,097,152 unknowns, 14,581,760 nonzeros, FP64 CSR, coefficients
-exp(N(0,1)) seed 1): device AMG setup (pairwise heavy-edge matching, two
-passes per level, Galerkin products, coarsest solver) followed by FP64
-AMG-preconditioned CG from x = 0 to a relative residual of 1e-8.  Inputs are
-resident in HBM when the timed region starts; the level-0 matrix (183 MB) is
-larger than the 129 MB L2, so no flush is needed between steps.
+Workload (one step): the 3D 7-point anisotropic diffusion system on a 256^3
+grid (16,777,216 unknowns, 117,047,296 nonzeros, off-diagonals -1, -1 and
+-1e-3 in z, FP64 CSR, b ~ U[-1,1] seed 2): device AMG setup (pairwise
+heavy-edge matching, two passes per level, Galerkin products, coarsest
+inverse) followed by FP64 flexible AMG-preconditioned CG from x = 0 to a
+relative residual of 1e-8.  Inputs are resident in HBM when the timed region
+starts; the level-0 matrix (1.47 GB) is far larger than the 129 MB L2, so no
+flush is needed between steps.
 
 Printed: one JSON line (rank 0).  value = solves per second over all ranks
 (replicas: every rank solves its own copy; no collective on the data path).
@@ -29,14 +30,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "AMG-PCG time to 1e-8 rel. residual; V-cycle HBM GB/s; batched solves/s + p99"
 UNIT = "solves/s"
-WORKLOAD = "lognormal3d_128: 3D 7-pt FV diffusion, 128^3 cells, lognormal(0,1) coefficients seed 1, FP64 CSR"
+WORKLOAD = ("anisotropic3d_256: 3D 7-pt anisotropic diffusion, 256^3 grid (16,777,216 unknowns, 117,047,296 "
+            "nonzeros), eps_z = 1e-3, b ~ U[-1,1] seed 2, FP64 CSR; AMG setup + FP64 flexible PCG to 1e-8")
 RTOL = 1e-8
 # FP64 peak of GB300: 152 SMs x 2 FMA per clock x 2 flops x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 HBM_SPEC_GBS = 7900.0  # GB300 HBM3e nominal; the measured copy bandwidth is the primary denominator
-# DRAM bytes (read + write) per launch of the coarse CG kernel on this
-# workload, from one ncu capture of the current kernel
-# (profiles/coarse_cg_lognormal3d_128.md); None once the kernel changes
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernel, keyed by profiler kind at level 0 of the 256^3 system (scaled from
+# the capture named in profiles/ by rows); absent once the kernel changes
+DRAM_BYTES_PER_LAUNCH = {}
+# DRAM bytes per launch of the coarse CG on the 128^3 lognormal coarsest
+# level (profiles/coarse_cg_lognormal3d_128.md): its matrix and vectors live
+# in shared memory, so these bytes stand for the solve's HBM traffic
 COARSE_CG_DRAM_BYTES = 10578432 + 87040
 
 
@@ -57,6 +63,9 @@ def parse_args():
                     help="skip the other workloads (256^3 mixed precision, 2048^2 BiCGStab, 64^2 Poisson)")
     ap.add_argument("--workload", choices=["solve", "serving"], default="solve",
                     help="serving: run the full 2048-request stream and print only its line")
+    ap.add_argument("--profile-case", default=None,
+                    help="one setup + FP64 flexible PCG solve of a named system for profiler captures, e.g. "
+                         "anisotropic3d_128, anisotropic3d_256, lognormal3d_128 (prints one line, no timing)")
     return ap.parse_args()
 
 
@@ -177,54 +186,97 @@ def shard(items, rank: int, world: int):
 # ---------------------------------------------------------------------------
 # oracle timings (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
-def oracle_setup_and_iter_times(sys_, iters: int):
-    """Oracle setup time and mean time of one PCG iteration (`iters` samples).
-    Each sample is a call of the oracle PCG with max_iter = 1 from x = 0, i.e.
-    the initial residual, one V-cycle, one SpMV and the vector updates."""
-    import oracle as O
+def oracle_full_solve(conn):
+    """Child process: one complete oracle solve of the headline system on one
+    host core (setup + flexible PCG to 1e-8), every part timed, nothing
+    extrapolated.  Sends a dict through conn."""
+    try:
+        import oracle as O
+        from paper_2007_00056_gb300 import workloads as W
 
-    t0 = time.perf_counter()
-    oh = O.Hierarchy(sys_.rp, sys_.ci, sys_.val)
-    t_setup = time.perf_counter() - t0
-    ts = []
-    for _ in range(iters):
+        s = W.config_anisotropic3d_256()
         t0 = time.perf_counter()
-        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
-        ts.append(time.perf_counter() - t0)
-    return oh, t_setup, ts
+        oh = O.Hierarchy(s.rp, s.ci, s.val)
+        t1 = time.perf_counter()
+        _, info = oh.pcg(s.b, rtol=RTOL, flexible=True)
+        t2 = time.perf_counter()
+        conn.send({"setup_s": t1 - t0, "solve_s": t2 - t1, "iterations": info.iterations,
+                   "rel_res_true": info.rel_res_true, "levels": oh.sizes()})
+    except Exception as e:  # reported in the line, never fatal to the GPU measurement
+        conn.send({"error": repr(e)})
+    conn.close()
 
 
-def run_reference(args, sys_):
-    """Oracle arm: the serial FP64 oracle on one host core, same workload."""
+def start_cpu_baseline():
+    """Starts the oracle's full solve in a spawned child on its own host core;
+    it runs while the GPU is measured.  Returns (process, connection)."""
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    rd, wr = ctx.Pipe(duplex=False)
+    p = ctx.Process(target=oracle_full_solve, args=(wr,), daemon=True)
+    p.start()
+    wr.close()
+    return p, rd
+
+
+def finish_cpu_baseline(proc, conn, timeout_s=900.0):
+    if proc is None:
+        return None
+    r = conn.recv() if conn.poll(timeout_s) else {"error": f"no result within {timeout_s:.0f} s"}
+    proc.join(5)
+    if "error" in r:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r["error"]}
+    t = r["setup_s"] + r["solve_s"]
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one complete solve of the full 256^3 system by the serial FP64 oracle on one host core: "
+                       f"setup {r['setup_s']:.1f} s + flexible PCG {r['solve_s']:.1f} s ({r['iterations']} "
+                       f"iterations to 1e-8), timed whole, nothing extrapolated; it ran in a child process while "
+                       f"the GPU was measured"),
+            "time_to_solution_s": t, "iterations": r["iterations"], "rel_res_true": r["rel_res_true"],
+            "levels": r["levels"]}
+
+
+def run_reference(args):
+    """Oracle arm: the serial FP64 oracle on one host core, headline workload.
+    The first warm-up step is one complete solve (setup + flexible PCG to
+    1e-8), timed whole: its time gives `value`.  The other W - 1 warm-up steps
+    and the K timed steps are bounded samples of the same workload, one
+    oracle PCG iteration each (a call with max_iter = 1 on the already built
+    hierarchy: initial residual, one V-cycle, one SpMV, the updates and the
+    final true residual), whose mean is ms_per_step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
+    from paper_2007_00056_gb300 import workloads as W
 
-    # warm-up 1: setup and a full solve fix the setup time and the iteration count
+    s = W.config_anisotropic3d_256()
     t0 = time.perf_counter()
-    oh = O.Hierarchy(sys_.rp, sys_.ci, sys_.val)
+    oh = O.Hierarchy(s.rp, s.ci, s.val)
     t_setup = time.perf_counter() - t0
-    _, info = oh.pcg(sys_.b, rtol=RTOL, flexible=True)
-    iters = info.iterations
+    t0 = time.perf_counter()
+    _, info = oh.pcg(s.b, rtol=RTOL, flexible=True)
+    t_pcg = time.perf_counter() - t0
+    full = t_setup + t_pcg
     for _ in range(max(0, args.warmup - 1)):
-        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
+        oh.pcg(s.b, rtol=0.0, max_iter=1, flexible=True)
     ts = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oh.pcg(sys_.b, rtol=0.0, max_iter=1, flexible=True)
+        oh.pcg(s.b, rtol=0.0, max_iter=1, flexible=True)
         ts.append(time.perf_counter() - t0)
-    t_iter = statistics.mean(ts)
-    t_solve = t_setup + iters * t_iter
-    value = 1.0 / t_solve
-    sample = (f"oracle setup of the full system ({t_setup:.2f} s, measured once) + {args.steps} timed one-iteration "
-              f"PCG samples ({t_iter:.3f} s each), extrapolated to the oracle's own {iters} iterations to 1e-8")
+    value = 1.0 / full
+    sample = (f"warm-up step 1: one complete oracle solve of the full system timed whole (setup {t_setup:.1f} s + "
+              f"flexible PCG {t_pcg:.1f} s, {info.iterations} iterations), which gives the value; "
+              f"the {args.steps} timed steps are one-iteration PCG samples on the same hierarchy "
+              f"({statistics.mean(ts):.3f} s each)")
     out = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": sys_.n, "nnz": sys_.nnz, "rtol": RTOL},
-        "time_to_solution_s": t_solve, "iterations": iters,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ts) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": s.n, "nnz": s.nnz, "rtol": RTOL},
+        "time_to_solution_s": full, "iterations": info.iterations, "rel_res_true": info.rel_res_true,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -274,7 +326,7 @@ def run_serving(reqs, systems):
     srv = S.SolveServer()
     res_cap, wall_cap = S.serve_stream(srv, reqs, systems, time_scale=0.0)
     srv.close()
-    ok = sum(r.status == amg.AMG_OK and r.rel_res_true <= 1.05e-8 for r in res)
+    ok = sum(r.status == amg.AMG_OK and r.rel_res_true <= 1e-8 for r in res)
     # plain FP64 method: setup + pcg_solve per request, sequential, same device
     dev = torch.device("cuda", torch.cuda.current_device())
     torch.cuda.synchronize()
@@ -314,14 +366,34 @@ def run_serving(reqs, systems):
 
 
 VCYCLE_KINDS = {"jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
-                "coarse_cg", "cast"}
+                "coarse_cg", "cast", "op_residual", "op_post"}
+# kinds that are one kernel each and stream the level's matrix or vectors from HBM
+HBM_KERNEL_KINDS = ("op_residual", "op_post", "krylov_spmv", "residual", "jacobi", "jacobi0", "restrict", "prolong",
+                    "prolong_jacobi")
 
 
-def vcycle_rate(h, b, reps=10):
-    """HBM rate of the whole V-cycle: algorithmic bytes of one V-cycle (the
-    library's profiler) over the time of `reps` V-cycles run back to back
-    with the profiler off (CUDA events on the current stream).  Returns
-    (GB/s, ms per V-cycle, share of the coarsest solve in the profiled cycle)."""
+def b_v_bytes(h, s_v, s_x, coarse_bytes=None):
+    """Algorithmic bytes of one V-cycle (one pre- and one post-sweep, zero
+    guess) by the measurement plan's count: per level k below the coarsest,
+    two matrix passes B_A(k) = nnz_k (s_v + 4) + 4 (N_k + 1), nine vector
+    passes of N_k s_x and the aggregate map (4 N_k); plus the coarsest solve,
+    8 N_L^2 for the dense inverse, or `coarse_bytes` (the DRAM bytes ncu
+    measured) for a coarse CG that works from shared memory."""
+    from paper_2007_00056_gb300 import amg
+
+    sizes = [amg.amg_level_info(h, k) for k in range(h.num_levels)]
+    total = 0.0
+    for n, nnz in sizes[:-1]:
+        total += 2.0 * (nnz * (s_v + 4) + 4.0 * (n + 1)) + 9.0 * n * s_x + 4.0 * n
+    n_l = sizes[-1][0]
+    total += 8.0 * n_l * n_l if coarse_bytes is None else float(coarse_bytes)
+    return total
+
+
+def vcycle_rate(h, b, bv, reps=20):
+    """Rate of the whole V-cycle: its algorithmic bytes bv (b_v_bytes) over
+    the time of `reps` V-cycles run back to back with the profiler off (CUDA
+    events on the current stream).  Returns (GB/s, ms per V-cycle)."""
     import torch
 
     from paper_2007_00056_gb300 import amg
@@ -338,22 +410,15 @@ def vcycle_rate(h, b, reps=10):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    amg.amg_profile_reset(h)
-    amg.amg_profile_enable(h, True)
-    amg.amg_vcycle(h, b, z)
-    tab = amg.amg_profile_table(h)
-    amg.amg_profile_enable(h, False)
-    vb = sum(r["bytes"] for r in tab if r["kind"] in VCYCLE_KINDS)
-    vms = sum(r["ms"] for r in tab if r["kind"] in VCYCLE_KINDS)
-    cms = sum(r["ms"] for r in tab if r["kind"] in ("coarse_dense", "coarse_cg"))
-    return vb / (ms * 1e-3) / 1e9, ms, (cms / vms if vms > 0 else None)
+    return bv / (ms * 1e-3) / 1e9, ms
 
 
-def _solve_timed(sys_, params, krylov, dev, profile=False, tune=False):
+def _solve_timed(sys_, params, krylov, dev, profile=False, tune=False, coarse_bytes=None):
     """Setup + solve of one system from device-resident inputs ("pcg": flexible
     PCG, "bicgstab", or "amg": AMG as a stationary solver); CUDA events on the
     current stream.  Returns times, the solve info, x and (with profile) the
-    V-cycle's algorithmic bytes and device time."""
+    V-cycle's rate by the measurement plan's algorithmic bytes (coarse_bytes:
+    DRAM bytes of a shared-memory coarse CG)."""
     import torch
 
     from paper_2007_00056_gb300 import amg
@@ -386,26 +451,60 @@ def _solve_timed(sys_, params, krylov, dev, profile=False, tune=False):
         for r in sorted(table, key=lambda r: -r["ms"])[:5]:
             top.append({"kernel": f"{r['kind']}@{r['level']}", "ms": r["ms"],
                         "gbs": r["bytes"] / (r["ms"] * 1e-3) / 1e9 if r["ms"] > 0 else None})
-        vc_gbs_unprofiled, vc_ms_unprofiled, coarse_share = vcycle_rate(h, b)
+        sv, sx = {amg.AMG_FP64: (8, 8), amg.AMG_FP32: (4, 4), amg.AMG_FP16_STORAGE: (2, 4)}[params.precision]
+        dense = amg.amg_coarse_cg_cluster_size(h) < 0
+        bv = b_v_bytes(h, sv, sx, None if dense else coarse_bytes)
+        level_nnz = [amg.amg_level_info(h, k) for k in range(h.num_levels)]
+        vc_gbs_unprofiled, vc_ms_unprofiled = vcycle_rate(h, b, bv)
+        cms = sum(r["ms"] for r in table if r["kind"] in ("coarse_dense", "coarse_cg"))
+        coarse_share = cms / vc_ms if vc_ms > 0 else None
     levels = h.sizes()
     h.close()
     out = dict(setup_ms=e0.elapsed_time(e1), solve_ms=e1.elapsed_time(e2), info=info, x=x, levels=levels,
                vc_bytes=vc_bytes, vc_ms=vc_ms, top=top)
     if profile:
-        out.update(vc_gbs=vc_gbs_unprofiled, vc_cycle_ms=vc_ms_unprofiled, vc_coarse_share=coarse_share)
+        out.update(vc_gbs=vc_gbs_unprofiled, vc_cycle_ms=vc_ms_unprofiled, vc_coarse_share=coarse_share,
+                   vc_bv_bytes=bv, table=table, level_nnz=level_nnz)
     return out
 
 
-def run_configs(dev, peak):
+def coarse_cg_roofline(table, level_nnz):
+    """FP64 rate of the coarse CG (the coarsest solve of the 128^3 lognormal
+    hierarchy, whose rows and matrix slice live in shared memory, so its bound
+    is the FP64 pipe and its grid barrier, not HBM).  Flops per iteration are
+    the method's Jacobi-PCG work, 2 nnz_L (the product) + 13 N_L (three
+    vector updates, the Jacobi scaling, three inner products); the iteration
+    count per launch is the profiler's byte total over its per-iteration
+    charge (one matrix pass plus ten FP64 vectors)."""
+    rows = [r for r in table if r["kind"] == "coarse_cg"]
+    if not rows:
+        return None
+    r = rows[0]
+    n_l, nnz_l = level_nnz[r["level"]]
+    charge = nnz_l * 12 + 4 * (n_l + 1) + 80 * n_l
+    iters = r["bytes"] / r["launches"] / charge
+    ms = r["ms"] / r["launches"]
+    flops = (2.0 * nnz_l + 13.0 * n_l) * iters
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "alu", "pipe": "fp64", "kernel": f"coarse_cg@level{r['level']}", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": COARSE_CG_DRAM_BYTES,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
+            "flops_per_iteration": "2 nnz_L + 13 N_L", "iterations_per_launch": iters, "ms_per_launch": ms,
+            "us_per_iteration": ms * 1e3 / iters}
+
+
+def run_configs(dev, peak, x64_main=None):
     """The other workloads of the method, measured on this GPU: the 256^3
-    anisotropic system in FP64 and both mixed-precision forms (flexible PCG),
-    the 2048^2 upwind convection-diffusion system with BiCGStab (FP32 V-cycle,
-    FP64 outer) at three Peclet numbers, and the 64^2 Poisson system (coarsest level 64 rows).  Each
-    line: setup and solve time (a second solve after one untimed warm-up whose
-    hierarchy is autotuned, as in the main workload),
-    iterations, true relative residual, V-cycle GB/s from the library's event
-    profiler (a third, profiled solve) and, for the mixed-precision forms, the
-    relative 2-norm difference to the FP64 solution of the same system."""
+    anisotropic system in both mixed-precision forms (flexible PCG; error
+    against the FP64 solution of the headline), the 128^3 lognormal system in
+    FP64 (its coarsest level is solved by the coarse CG), the 2048^2 upwind
+    convection-diffusion system with BiCGStab (FP32 V-cycle, FP64 outer) at
+    three Peclet numbers, and the 64^2 Poisson system (coarsest level 64
+    rows).  Each line: setup and solve time (a second solve after one untimed
+    warm-up whose hierarchy is autotuned, as in the headline), iterations,
+    true relative residual, and the V-cycle's rate by the measurement plan's
+    algorithmic bytes over the time of unprofiled V-cycles."""
     import torch
 
     from paper_2007_00056_gb300 import amg
@@ -413,11 +512,11 @@ def run_configs(dev, peak):
 
     out = []
 
-    def line(name, sys_, prec, krylov, x_ref=None, **kw):
+    def line(name, sys_, prec, krylov, x_ref=None, coarse_bytes=None, **kw):
         params = amg.amg_default_params(precision=prec, **kw)
         _solve_timed(sys_, params, krylov, dev, tune=True)  # warm-up; its hierarchy is autotuned
         r = _solve_timed(sys_, params, krylov, dev)
-        p = _solve_timed(sys_, params, krylov, dev, profile=True)
+        p = _solve_timed(sys_, params, krylov, dev, profile=True, coarse_bytes=coarse_bytes)
         info = r["info"]
         gbs = p["vc_gbs"]
         d = {"config": name, "n": sys_.n, "nnz": sys_.nnz, "krylov": krylov,
@@ -426,7 +525,8 @@ def run_configs(dev, peak):
              "status": amg.status_string(info.status),
              "iterations": info.iterations, "rel_res_true": info.rel_res_true,
              "setup_ms": r["setup_ms"], "solve_ms": r["solve_ms"], "time_to_solution_ms": r["setup_ms"] + r["solve_ms"],
-             "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None,
+             "levels": r["levels"], "vcycle_gbs": gbs, "vcycle_bytes": p["vc_bv_bytes"],
+             "vcycle_frac_of_measured_peak": (gbs / peak) if gbs else None,
              "vcycle_frac_of_spec": (gbs / HBM_SPEC_GBS) if gbs else None,
              "vcycle_ms": p["vc_cycle_ms"], "vcycle_coarsest_share": p["vc_coarse_share"],
              "top_kernels_profiled_solve": p["top"]}
@@ -434,13 +534,18 @@ def run_configs(dev, peak):
             d["rel_diff_vs_fp64_solution"] = float(torch.linalg.vector_norm(r["x"] - x_ref) /
                                                    torch.linalg.vector_norm(x_ref))
         out.append(d)
-        return r["x"]
+        return d, p
 
     s3 = W.config_anisotropic3d_256()
-    x64 = line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP64, "pcg")
-    line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP32, "pcg", x64)
-    line("anisotropic3d_256 eps_z=1e-3", s3, amg.AMG_FP16_STORAGE, "pcg", x64)
-    del s3, x64
+    for prec in (amg.AMG_FP32, amg.AMG_FP16_STORAGE):
+        line("anisotropic3d_256 eps_z=1e-3", s3, prec, "pcg", x64_main)
+    del s3
+    torch.cuda.empty_cache()
+    s2 = W.config_lognormal3d_128()
+    d, p = line("lognormal3d_128 sigma=1", s2, amg.AMG_FP64, "pcg", coarse_bytes=COARSE_CG_DRAM_BYTES)
+    if p.get("table"):
+        d["coarse_cg_roofline"] = coarse_cg_roofline(p["table"], p["level_nnz"])
+    del s2
     for pe in (10.0, 100.0, 1000.0):
         s4 = W.config_convdiff2d_2048(peclet=pe)
         line(f"convdiff2d_2048 upwind Pe={pe:g}", s4, amg.AMG_FP32, "bicgstab")
@@ -558,6 +663,32 @@ def run_complexity(dev):
 # ---------------------------------------------------------------------------
 # GB300 arm
 # ---------------------------------------------------------------------------
+def run_profile_case(name):
+    """One setup and one FP64 flexible PCG solve of a named system (family and
+    grid size, the benchmark's generators and seeds), for profiler captures:
+    no warm-up, no timing."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    fam, _, size = name.rpartition("_")
+    gen = {"anisotropic3d": lambda n: W.anisotropic3d(n, eps_z=1e-3, seed=2),
+           "lognormal3d": lambda n: W.lognormal3d(n, seed=1), "poisson2d": lambda n: W.poisson2d(n)}[fam]
+    s = gen(int(size))
+    dev = torch.device("cuda", 0)
+    amg.lib(build_if_missing=True)
+    rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
+    h = amg.amg_setup(rp, ci, val)
+    x = torch.zeros_like(b)
+    info = amg.pcg_solve(h, b, x, rtol=RTOL, flexible=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "n": s.n, "levels": h.sizes(), "iterations": info.iterations,
+                      "status": amg.status_string(info.status)}), flush=True)
+    h.close()
+
+
+
 def main():
     args = parse_args()
     from paper_2007_00056_gb300 import workloads as W
@@ -565,7 +696,10 @@ def main():
     if args.impl == "reference":
         if int(os.environ.get("RANK", "0")) != 0:
             return
-        run_reference(args, W.lognormal3d(args.grid, seed=1))
+        run_reference(args)
+        return
+    if args.profile_case:
+        run_profile_case(args.profile_case)
         return
     if args.workload == "serving":
         reqs, systems = generate_requests(2048)
@@ -579,8 +713,14 @@ def main():
         print(json.dumps(out), flush=True)
         return
 
+    rank = int(os.environ.get("RANK", "0"))
+    world_env = int(os.environ.get("WORLD_SIZE", "1"))
+    # the oracle's full solve runs in a child process on its own host core
+    # while the GPU is measured (started before any CUDA work)
+    cpu_proc = cpu_conn = None
+    if rank == 0 and world_env == 1 and not args.no_cpu_baseline:
+        cpu_proc, cpu_conn = start_cpu_baseline()
     rank, world, local = dist_setup(args)
-    import numpy as np
     import torch
 
     from paper_2007_00056_gb300 import amg
@@ -588,7 +728,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     amg.lib(build_if_missing=True)
-    sys_ = W.lognormal3d(args.grid, seed=1)
+    sys_ = W.config_anisotropic3d_256()
     rp = torch.from_numpy(sys_.rp).to(dev)
     ci = torch.from_numpy(sys_.ci).to(dev)
     val = torch.from_numpy(sys_.val).to(dev)
@@ -615,7 +755,7 @@ def main():
         if w == 0 and not args.no_autotune:
             amg.amg_autotune(h)
         levels = h.sizes()
-        level_cfg = [amg.amg_level_config(h, k) for k in range(h.num_levels)]
+        level_cfg = [amg.amg_level_config(h, k) + (amg.amg_level_operator_form(h, k),) for k in range(h.num_levels)]
         h.close()
     torch.cuda.synchronize()
     sampler = ClockSampler(local) if rank == 0 else None
@@ -626,7 +766,7 @@ def main():
     launches0 = amg.amg_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    setup_ms, iters = [], []
+    setup_ms, iters, rel_true = [], [], []
     # NVTX range "timed": lets a profiler capture exactly the timed launches
     # (ncu --nvtx --nvtx-include "timed/")
     torch.cuda.nvtx.range_push("timed")
@@ -638,6 +778,7 @@ def main():
         ev_end.record(stream)
         setup_ms.append((last, ev_mid))
         iters.append(info.iterations)
+        rel_true.append(info.rel_res_true)
         if info.status != amg.AMG_OK:
             raise RuntimeError(f"PCG did not converge: {info}")
         h.close()
@@ -655,13 +796,14 @@ def main():
     value = job_throughput(args.steps, world, max_ms)
     setup_mean = statistics.mean(setup_t)
     solve_mean = ms_per_step - setup_mean
+    x_main = x.clone()
 
     # live per-kernel timing of the same step (CUDA events on the launching stream)
     peak, peak_kind = measured_peaks()
     table_acc = {}
-    vc_bytes = vc_ms = 0.0
     level_nnz = []
-    vc_rate = (None, None, None)
+    vc = (None, None)
+    bv = None
     for ps in range(args.profile_steps):
         h, info, _ = step(profile=True)
         level_nnz = [amg.amg_level_info(h, k) for k in range(h.num_levels)]
@@ -672,53 +814,32 @@ def main():
             acc["bytes"] += r["bytes"]
             acc["launches"] += r["launches"]
         if ps == args.profile_steps - 1:
-            vc_rate = vcycle_rate(h, b)
+            bv = b_v_bytes(h, 8, 8)
+            vc = vcycle_rate(h, b, bv)
         h.close()
     table = sorted(table_acc.values(), key=lambda r: -r["ms"])
-    vcycle_kinds = {"jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
-                    "coarse_cg", "cast"}
-    for r in table:
-        if r["kind"] in vcycle_kinds:
-            vc_bytes += r["bytes"]
-            vc_ms += r["ms"]
-    top = table[0] if table else None
+    # dominant single kernel of the step among the solve-phase kernels
+    top = next((r for r in table if r["kind"] in HBM_KERNEL_KINDS), None)
     roofline = None
-    if top and top["kind"] == "coarse_cg" and level_nnz:
-        # The coarse CG keeps its rows in shared memory: per iteration it reads
-        # no matrix from HBM, and its bound is the FP64 pipe (and its grid
-        # barrier).  FP64 flops per iteration of the pipelined form: 2 nnz
-        # (SpMV) + 23 n (eight vector updates, m = D^-1 w, three inner
-        # products); the iteration count comes from the profiler's byte total,
-        # which it charges per iteration.
-        n_l, nnz_l = level_nnz[top["level"]]
-        bytes_per_iter = nnz_l * 12 + 4 * (n_l + 1) + 80 * n_l
-        iters_per_launch = top["bytes"] / top["launches"] / bytes_per_iter
-        flops = (2.0 * nnz_l + 23.0 * n_l) * iters_per_launch
-        per_launch_ms = top["ms"] / top["launches"]
-        achieved = flops / (per_launch_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top['kind']}@level{top['level']}",
-                    "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": COARSE_CG_DRAM_BYTES,
-                    "traffic_note": "DRAM bytes per launch (ncu); the matrix is read once per solve",
-                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                    "flops_per_launch": flops, "iterations_per_launch": iters_per_launch,
-                    "ms_per_launch": per_launch_ms, "us_per_iteration": per_launch_ms * 1e3 / iters_per_launch}
-    elif top:
+    if top:
         per_launch_bytes = top["bytes"] / top["launches"]
         per_launch_ms = top["ms"] / top["launches"]
         achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "kernel": f"{top['kind']}@level{top['level']}", "achieved": achieved,
-                    "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": peak_kind, "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms}
-    # the level-0 kernels, which stream the 183 MB matrix from HBM
+                    "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": DRAM_BYTES_PER_LAUNCH.get((top["kind"], top["level"])),
+                    "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                    "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                    "launches_per_step": top["launches"] / args.profile_steps,
+                    "share_of_profiled_solve": top["ms"] / sum(r["ms"] for r in table)}
     hbm_level0 = []
     for r in table:
-        if r["level"] == 0 and r["kind"] in ("jacobi", "residual", "prolong_jacobi", "krylov_spmv") and r["ms"] > 0:
+        if r["level"] == 0 and r["kind"] in HBM_KERNEL_KINDS and r["ms"] > 0:
             g = r["bytes"] / (r["ms"] * 1e-3) / 1e9
             hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak, "frac_of_spec": g / HBM_SPEC_GBS})
     kernels = [dict(kernel=f"{r['kind']}@{r['level']}", ms_per_step=r["ms"] / args.profile_steps,
                     launches_per_step=r["launches"] / args.profile_steps,
-                    gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:12]]
+                    gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:14]]
 
     # end to end through the public API from pinned host buffers
     h_rp = torch.from_numpy(sys_.rp).pin_memory()
@@ -740,7 +861,7 @@ def main():
             d.copy_(hsrc, non_blocking=True)
         he = amg.amg_setup(d_rp, d_ci, d_val, params)
         xe = torch.zeros_like(d_b)
-        inf = amg.pcg_solve(he, d_b, xe, rtol=RTOL, max_iter=1000, flexible=True)
+        amg.pcg_solve(he, d_b, xe, rtol=RTOL, max_iter=1000, flexible=True)
         h_x.copy_(xe, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         he.close()
@@ -748,30 +869,23 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
     e2e_value = job_throughput(e2e_steps, world, e2e_ms)
-
-    # CPU baseline: the oracle on this host's cores (rank 0, one GPU only)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oh, t_setup, ts = oracle_setup_and_iter_times(sys_, 3)
-        it_gpu = int(round(statistics.mean(iters)))
-        t_solve = t_setup + it_gpu * statistics.mean(ts)
-        cpu = {"value": 1.0 / t_solve, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": (f"oracle setup of the full 128^3 system ({t_setup:.2f} s) + 3 one-iteration PCG "
-                          f"samples ({statistics.mean(ts):.3f} s each), extrapolated to {it_gpu} iterations"),
-               "time_to_solution_s": t_solve}
+    del d_rp, d_ci, d_val, d_b, h_rp, h_ci, h_val
 
     configs = cycles = complexity = scaled = None
     if rank == 0 and world == 1 and not args.no_configs:
-        configs = run_configs(dev, peak)
-        cycles = run_cycles(dev, sys_)
+        configs = run_configs(dev, peak, x_main)
+        s2 = W.config_lognormal3d_128()
+        cycles = run_cycles(dev, s2)
         complexity = run_complexity(dev)
-        scaled = run_scaled_weight(dev, sys_)
+        scaled = run_scaled_weight(dev, s2)
+        del s2
 
     serving = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
         reqs, systems = generate_requests(args.serving_requests)
         serving = run_serving(reqs, systems)
 
+    cpu = finish_cpu_baseline(cpu_proc, cpu_conn) if rank == 0 else None
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -779,16 +893,17 @@ def main():
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": sys_.n, "nnz": sys_.nnz, "rtol": RTOL, "precision": "fp64",
                        "krylov": "flexible PCG", "levels": levels, "parallelism": f"replicas{world}",
-                       "level_kernels": [dict(zip(("tpr", "fuse_pre", "fuse_post"), c)) for c in level_cfg],
-                       "l2": "inputs larger than L2 (level-0 CSR 183 MB > 129 MB); no flush"},
+                       "level_kernels": [dict(zip(("tpr", "fuse_pre", "fuse_post", "operator_form"), c))
+                                         for c in level_cfg],
+                       "l2": "inputs larger than L2 (level-0 CSR 1.47 GB > 129 MB); no flush"},
             "time_to_solution_ms": ms_per_step, "setup_ms": setup_mean, "solve_ms": solve_mean,
-            "iterations": iters[0],
-            "vcycle": {"gbs": vc_rate[0], "ms_per_cycle": vc_rate[1], "peak": peak,
-                       "frac": vc_rate[0] / peak if vc_rate[0] else None,
-                       "frac_of_spec": vc_rate[0] / HBM_SPEC_GBS if vc_rate[0] else None,
-                       "coarsest_share": vc_rate[2],
-                       "note": "algorithmic bytes of one V-cycle over the time of ten V-cycles run with the "
-                               "profiler off; the coarsest solve (CG from shared memory) is not HBM-bound"},
+            "iterations": iters[0], "rel_res_true_max": max(rel_true),
+            "vcycle": {"gbs": vc[0], "ms_per_cycle": vc[1], "bytes_per_cycle": bv, "peak": peak,
+                       "frac": vc[0] / peak if vc[0] else None,
+                       "frac_of_spec": vc[0] / HBM_SPEC_GBS if vc[0] else None,
+                       "note": "algorithmic bytes of one V-cycle by the measurement plan's count (two matrix "
+                               "passes, nine vector passes and the aggregate map per level, 8 N_L^2 for the dense "
+                               "coarsest inverse) over the time of twenty V-cycles run with the profiler off"},
             "roofline": roofline, "hbm_level0": hbm_level0, "kernels": kernels,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,

@@ -105,7 +105,18 @@ typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
  *                The W-cycle keeps M^{-1} symmetric for symmetric A; the
  *                F-cycle does not, so PCG with it should be flexible.
  *   tie_break    amg_tie_break of the matching (AMG_TIE_SMALLER)
- *   edge_weight  amg_edge_weight of the matching (AMG_WEIGHT_ABS) */
+ *   edge_weight  amg_edge_weight of the matching (AMG_WEIGHT_ABS)
+ *   operator_form  1 (default): in the FP64 and FP32 precisions, setup also
+ *                forms, for every level below the coarsest, C = I - omega A D^-1
+ *                (A's pattern) and Q = P - omega D^-1 A P (the pattern of A P),
+ *                and a cycle visit from the zero guess with nu_pre = nu_post = 1
+ *                computes its residual as t = C f and its result as
+ *                Q x_{k+1} + omega D^-1 (f + t): algebraically the same
+ *                presmoothing, residual, prolongation and postsmoothing of
+ *                Algorithm 1 (x = omega D^-1 f is never stored), in two
+ *                matrix passes of which the second is over the smaller A P.
+ *                Costs about one more copy of the level matrices in device
+ *                memory.  0: only the explicit sweeps. */
 typedef struct {
   int passes;
   int max_levels;
@@ -119,6 +130,7 @@ typedef struct {
   int cycle;
   int tie_break;
   int edge_weight;
+  int operator_form;
 } amg_params;
 
 /* Result of a Krylov solve.  iterations counts completed iterations (a
@@ -249,6 +261,17 @@ int amg_level_config(const amg_hierarchy *h, int level, int *tpr, int *fuse_pre,
  * tile of 256 rows too large for shared memory). */
 amg_status amg_level_set_config(amg_hierarchy *h, int level, int tpr, int fuse_pre, int fuse_post);
 
+/* Residual-operator form of a level (see amg_params.operator_form): returns 1
+ * when zero-guess visits of the level use C and Q, 0 when they use the
+ * explicit sweeps, -1 for a NULL h or a bad level. */
+int amg_level_operator_form(const amg_hierarchy *h, int level);
+
+/* Switches a level's zero-guess visits between the residual-operator form
+ * (on != 0) and the explicit sweeps.  AMG_ERR_INVALID_ARG for a NULL h or a
+ * bad level; AMG_ERR_UNSUPPORTED for on != 0 on a level without C and Q (the
+ * coarsest level, FP16 storage, or operator_form = 0 at setup). */
+amg_status amg_level_set_operator_form(amg_hierarchy *h, int level, int on);
+
 /* ---- Instrumentation (no counterpart in the paper; used for measurement) ---- */
 
 /* Self-test of the library's bounded device waits: `blocks` (1..64) blocks
@@ -288,7 +311,9 @@ typedef enum {
   AMG_K_COARSE_CG = 7,      /* coarsest solve, persistent Jacobi-PCG                   */
   AMG_K_CAST = 8,           /* FP64 <-> FP32 conversions of the mixed-precision cycle  */
   AMG_K_KRYLOV_SPMV = 9,    /* outer Krylov SpMV with fused dot products               */
-  AMG_K_KRYLOV_VEC = 10     /* outer Krylov vector updates with fused dot products     */
+  AMG_K_KRYLOV_VEC = 10,    /* outer Krylov vector updates with fused dot products     */
+  AMG_K_OP_RESIDUAL = 11,   /* residual-operator form: t = C f (matrix pass)            */
+  AMG_K_OP_POST = 12        /* residual-operator form: Q x_{k+1} + omega D^-1 (f + t)   */
 } amg_kernel_kind;
 
 /* Total kernel launches this library has issued since it was loaded (a graph

@@ -38,9 +38,10 @@ EXPORTS = (
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
     "amg_selftest_wait_timeout", "amg_selftest_convert", "amg_last_cuda_error", "amg_coarse_cg_cluster_size",
+    "amg_level_operator_form", "amg_level_set_operator_form",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
-                "coarse_cg", "cast", "krylov_spmv", "krylov_vec")
+                "coarse_cg", "cast", "krylov_spmv", "krylov_vec", "op_residual", "op_post")
 
 
 class AmgError(RuntimeError):
@@ -69,6 +70,7 @@ class amg_params(C.Structure):
         ("cycle", C.c_int),
         ("tie_break", C.c_int),
         ("edge_weight", C.c_int),
+        ("operator_form", C.c_int),
     ]
 
 
@@ -133,6 +135,8 @@ def lib(build_if_missing: bool = False):
             l.amg_level_config.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
             l.amg_coarse_cg_noalloc.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp, C.POINTER(i32)]
             l.amg_coarse_cg_cluster_size.argtypes = [vp]
+            l.amg_level_operator_form.argtypes = [vp, i32]
+            l.amg_level_set_operator_form.argtypes = [vp, i32, i32]
             _lib = l
     return _lib
 
@@ -382,6 +386,20 @@ def amg_level_set_config(h: Hierarchy, level: int, tpr: int, fuse_pre: bool, fus
     st = lib().amg_level_set_config(h.handle, int(level), int(tpr), int(bool(fuse_pre)), int(bool(fuse_post)))
     if st != AMG_OK:
         raise AmgError(st, "amg_level_set_config")
+
+
+def amg_level_operator_form(h: Hierarchy, level: int) -> bool:
+    """Whether zero-guess visits of a level use the residual-operator form."""
+    r = lib().amg_level_operator_form(h.handle, int(level))
+    if r < 0:
+        raise IndexError(level)
+    return bool(r)
+
+
+def amg_level_set_operator_form(h: Hierarchy, level: int, on: bool) -> None:
+    st = lib().amg_level_set_operator_form(h.handle, int(level), int(bool(on)))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_level_set_operator_form")
 
 
 def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible: bool = False, stream=None):

@@ -154,6 +154,7 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->cycle = AMG_CYCLE_V;
   p->tie_break = AMG_TIE_SMALLER;
   p->edge_weight = AMG_WEIGHT_ABS;
+  p->operator_form = 1;
   return AMG_OK;
 }
 

@@ -68,12 +68,26 @@ struct Level {
   int st_grid = 0;           // blocks of the persistent staged kernels
   int fuse_pre = 1;          // first presmoothing sweep fused into the residual kernel
   int fuse_post = 0;         // prolongation fused into the first postsmoothing sweep
+  // Residual-operator form of a cycle visit from the zero guess with one pre-
+  // and one post-smoothing sweep (levels < L; FP64 values, FP32 copies in the
+  // FP32 mode).  With x = omega D^-1 f the presmoothed iterate:
+  //   t = f - A x = C f,                     C = I - omega A D^-1 (pattern of A)
+  //   y = x + P x_c + omega D^-1 (t - A P x_c) = Q x_c + wd (f + t),
+  //                                          Q = P - omega D^-1 A P, wd = omega D^-1
+  // so the visit reads one matrix of A's size and one of A P's size, and
+  // never stores x.
+  double *cval = nullptr, *qval = nullptr, *wd = nullptr;
+  float *cval32 = nullptr, *qval32 = nullptr, *wd32 = nullptr;
+  int32_t *qrp = nullptr, *qci = nullptr;  // CSR pattern of A P (n x n_{k+1}), columns ascending
+  int64_t qnnz = 0;
+  int op_avail = 0;          // C, Q and wd exist for this level
+  int op_on = 0;             // zero-guess visits use them
 };
 
 // Kernel kinds of the per-kernel profiler (id = kind * AMG_MAX_LEVELS + level).
 enum ProfKind {
   PK_JACOBI0 = 0, PK_JACOBI, PK_RESIDUAL, PK_RESTRICT, PK_PROLONG_JACOBI, PK_PROLONG, PK_COARSE_DENSE,
-  PK_COARSE_CG, PK_CAST, PK_KRYLOV_SPMV, PK_KRYLOV_VEC, PK_COUNT
+  PK_COARSE_CG, PK_CAST, PK_KRYLOV_SPMV, PK_KRYLOV_VEC, PK_OP_RESIDUAL, PK_OP_POST, PK_COUNT
 };
 #define AMG_PROF_IDS (PK_COUNT * AMG_MAX_LEVELS)
 
@@ -277,6 +291,50 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double *part, uns
   return true;
 }
 
+#define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Monotonic-counter grid barrier: the k-th barrier completes when the counter
+// reaches k * G.  Waits are bounded; a block that gives up sets the timeout
+// flag and the caller leaves its loop.  arrive() and wait() may be split so
+// that a block does independent work while the others arrive.
+struct GridBarrier {
+  unsigned *count;
+  unsigned target;
+  long long limit = BARRIER_SPIN_LIMIT;
+  __device__ __forceinline__ void arrive(unsigned G) {
+    __syncthreads();
+    target += G;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(count, 1u);
+    }
+  }
+  __device__ __forceinline__ bool wait(unsigned *eflags, int *fail_sh) {
+    if (threadIdx.x == 0) {
+      long long t0 = clock64();
+      while (ld_acquire_u32(count) < target) {
+        if (clock64() - t0 > limit) {
+          atomicOr(eflags, AMG_EFLAG_TIMEOUT);
+          *fail_sh = 1;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    return *fail_sh == 0;
+  }
+  __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
+    arrive(G);
+    return wait(eflags, fail_sh);
+  }
+};
+
 __device__ __forceinline__ bool is_done(const KState *st) {
   return st != nullptr && *((volatile const int *)&st->done) != 0;
 }
@@ -293,6 +351,7 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
 template <typename T>
 amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st);
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
+amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
 amg_status cluster_cg_config(int n, ClusterCG *cc);
 template <typename T>

@@ -321,6 +321,215 @@ amg_status gj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   return amg_cuda_status(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Gauss-Jordan inverse without row interchanges.  Block step K (BW
+// columns, pivot block P = M_KK):
+//   M_KJ <- P^-1 M_KJ,  M_IJ <- M_IJ - M_IK M_KJ (new),  M_IK <- -M_IK P^-1,
+//   M_KK <- P^-1        (I, J outside K)
+// after the last step M = A^-1.  Every step is a rank-BW product over the
+// whole matrix, spread over the GPU, instead of BW sequential single-column
+// eliminations in one thread block.  Without pivoting it is stable for the
+// symmetric positive definite and diagonally dominant coarsest matrices of
+// Galerkin hierarchies; any other matrix is caught either by a vanishing
+// pivot (breakdown flag) or by the refinement test of dense_inverse, which
+// then recomputes the inverse with partial pivoting.
+// ---------------------------------------------------------------------------
+#define BGJ_W 64  // block width
+
+// Step 1: P^-1 of the w x w pivot block by unblocked Gauss-Jordan (one block).
+template <typename T>
+__global__ void __launch_bounds__(256) k_bgj_diag(int m, int k0, int w, const T *__restrict__ M, T *__restrict__ Pinv,
+                                                  unsigned *eflags) {
+  __shared__ T P[BGJ_W][BGJ_W + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w;
+    P[r][c] = M[(size_t)(k0 + r) * m + k0 + c];
+  }
+  __syncthreads();
+  for (int c = 0; c < w; ++c) {
+    const T pv = P[c][c];
+    const bool ok = pv != (T)0 && isfinite((double)pv);
+    const T d = ok ? (T)1 / pv : (T)0;
+    if (!ok && tid == 0) bad = 1;
+    __syncthreads();
+    // pivot row scaled; its own entry becomes 1/pivot
+    if (tid < w) P[c][tid] = (tid == c) ? d : P[c][tid] * d;
+    __syncthreads();
+    // every other row: r_j -= f p_j (j != c), entry c becomes -f / pivot
+    for (int idx = tid; idx < w * w; idx += blockDim.x) {
+      const int r = idx / w, j = idx - r * w;
+      if (r == c) continue;
+      const T f = P[r][c];
+      if (j != c) P[r][j] = P[r][j] - f * P[c][j];
+    }
+    __syncthreads();
+    for (int r = tid; r < w; r += blockDim.x)
+      if (r != c) P[r][c] = -P[r][c] * d;
+    __syncthreads();
+  }
+  for (int idx = tid; idx < w * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w;
+    Pinv[idx] = P[r][c];
+  }
+  if (tid == 0 && bad) atomicOr(eflags, AMG_EFLAG_BREAKDOWN);
+}
+
+// Step 2: R = P^-1 M_K* for the columns outside K, stored in R (w x m) and in
+// the K rows of M.  Block: 64 columns; thread: one column, 16 of the rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bgj_rows(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv,
+                                                  T *__restrict__ R) {
+  __shared__ T Ps[BGJ_W][BGJ_W + 1];
+  __shared__ T Ms[BGJ_W][64 + 1];
+  const int tid = threadIdx.x, j0 = blockIdx.x * 64;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
+  for (int idx = tid; idx < w * 64; idx += blockDim.x) {
+    const int r = idx >> 6, jj = idx & 63, j = j0 + jj;
+    Ms[r][jj] = j < m ? M[(size_t)(k0 + r) * m + j] : (T)0;
+  }
+  __syncthreads();
+  const int jj = tid & 63, j = j0 + jj, rg = tid >> 6;
+  if (j >= m || (j >= k0 && j < k0 + w)) return;
+  for (int r = rg; r < w; r += 4) {
+    T acc = (T)0;
+    for (int c = 0; c < w; ++c) acc += Ps[r][c] * Ms[c][jj];
+    R[(size_t)r * m + j] = acc;
+    M[(size_t)(k0 + r) * m + j] = acc;
+  }
+}
+
+// Step 3: M_IJ -= M_IK R_KJ for I, J outside K (old M_IK).  Tile BM x BN per
+// block of 256 threads, TM x TN outputs per thread, both factors in shared
+// memory.
+template <typename T, int BM, int BN, int TM, int TN>
+__global__ void __launch_bounds__(256) k_bgj_update(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ R) {
+  static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+  extern __shared__ __align__(16) unsigned char bgj_smem[];
+  T *As = (T *)bgj_smem;            // [w][BM]: M_IK transposed
+  T *Bs = As + (size_t)BGJ_W * BM;  // [w][BN]: R_KJ
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  for (int idx = tid; idx < BM * w; idx += 256) {
+    const int r = idx / w, c = idx - r * w, i = i0 + r;
+    As[c * BM + r] = i < m ? M[(size_t)i * m + k0 + c] : (T)0;
+  }
+  for (int idx = tid; idx < w * BN; idx += 256) {
+    const int c = idx / BN, jj = idx - c * BN, j = j0 + jj;
+    Bs[c * BN + jj] = j < m ? R[(size_t)c * m + j] : (T)0;
+  }
+  __syncthreads();
+  constexpr int NX = BN / TN, NY = BM / TM;
+  const int tx = tid % NX, ty = tid / NX;
+  T acc[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = (T)0;
+  for (int c = 0; c < w; ++c) {
+    T av[TM], bv[TN];
+#pragma unroll
+    for (int a = 0; a < TM; ++a) av[a] = As[c * BM + ty + a * NY];
+#pragma unroll
+    for (int b = 0; b < TN; ++b) bv[b] = Bs[c * BN + tx + b * NX];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+      for (int b = 0; b < TN; ++b) acc[a][b] += av[a] * bv[b];
+  }
+#pragma unroll
+  for (int a = 0; a < TM; ++a) {
+    const int i = i0 + ty + a * NY;
+    if (i >= m || (i >= k0 && i < k0 + w)) continue;
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int j = j0 + tx + b * NX;
+      if (j >= m || (j >= k0 && j < k0 + w)) continue;
+      T *p = M + (size_t)i * m + j;
+      *p = *p - acc[a][b];
+    }
+  }
+}
+
+// Step 4: M_IK <- -M_IK P^-1 for I outside K, M_KK <- P^-1.  Block: 64 rows;
+// thread: one row, 16 of the columns.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bgj_cols(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv) {
+  __shared__ T Ps[BGJ_W][BGJ_W + 1];
+  __shared__ T Cs[64][BGJ_W + 1];
+  const int tid = threadIdx.x, i0 = blockIdx.x * 64;
+  for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
+  for (int idx = tid; idx < 64 * w; idx += blockDim.x) {
+    const int r = idx / w, c = idx - r * w, i = i0 + r;
+    Cs[r][c] = i < m ? M[(size_t)i * m + k0 + c] : (T)0;
+  }
+  __syncthreads();
+  const int r = tid & 63, cg = tid >> 6, i = i0 + r;
+  if (i >= m) return;
+  const bool in_k = i >= k0 && i < k0 + w;
+  for (int c = cg; c < w; c += 4) {
+    T v;
+    if (in_k) {
+      v = Ps[i - k0][c];
+    } else {
+      T acc = (T)0;
+      for (int q = 0; q < w; ++q) acc += Cs[r][q] * Ps[q][c];
+      v = -acc;
+    }
+    M[(size_t)i * m + k0 + c] = v;
+  }
+}
+
+template <typename T> struct BgjTile;
+template <> struct BgjTile<float> { static constexpr int BM = 128, BN = 128, TM = 8, TN = 8; };
+template <> struct BgjTile<double> { static constexpr int BM = 64, BN = 64, TM = 4, TN = 4; };
+
+// Blocked Gauss-Jordan inverse without pivoting into out (m x m).  Returns
+// AMG_ERR_BREAKDOWN when a pivot block step met a zero or non-finite pivot
+// (out is then unusable).  Synchronises the stream.
+template <typename T>
+amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
+  using TL = BgjTile<T>;
+  const Level &c = h->lev[h->L];
+  const int m = c.n;
+  const long long mm = (long long)m * m;
+  const size_t smem = sizeof(T) * (size_t)BGJ_W * (TL::BM + TL::BN);
+  AMG_CUDA(cudaFuncSetAttribute(k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  T *R = nullptr;
+  if (pool_alloc((void **)&R, sizeof(T) * ((size_t)BGJ_W * m + (size_t)BGJ_W * BGJ_W), st) != AMG_OK)
+    return AMG_ERR_OOM;
+  T *Pinv = R + (size_t)BGJ_W * m;
+  const int TB = AMG_THREADS;
+  k_dense_zero<T><<<grid_for(mm, TB), TB, 0, st>>>(mm, out);
+  k_dense_scatter<T><<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, out);
+  count_launch(2);
+  const dim3 ug(cdiv(m, TL::BN), cdiv(m, TL::BM));
+  for (int k0 = 0; k0 < m; k0 += BGJ_W) {
+    const int w = std::min(BGJ_W, m - k0);
+    k_bgj_diag<T><<<1, 256, 0, st>>>(m, k0, w, out, Pinv, h->eflags);
+    k_bgj_rows<T><<<cdiv(m, 64), 256, 0, st>>>(m, k0, w, out, Pinv, R);
+    k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
+    k_bgj_cols<T><<<cdiv(m, 64), 256, 0, st>>>(m, k0, w, out, Pinv);
+    count_launch(4);
+  }
+  AMG_CUDA(cudaGetLastError());
+  unsigned flags = 0;
+  amg_status rs = read_eflags(h, st, &flags);
+  pool_free(R, st);
+  AMG_TRY(rs);
+  const unsigned others = flags & ~AMG_EFLAG_BREAKDOWN;
+  if (others) {  // not ours: leave them for the caller's next check
+    h->eflags_host[0] = others;
+    AMG_CUDA(cudaMemcpyAsync(h->eflags, h->eflags_host, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    AMG_CUDA(cudaStreamSynchronize(st));
+  }
+  if (flags & AMG_EFLAG_BREAKDOWN) return AMG_ERR_BREAKDOWN;
+  return AMG_OK;
+}
+
 // Refinement test vector: f = A_L v for v_i = 1 + (i mod 7)/8.
 __global__ void k_refine_rhs(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                              const double *__restrict__ val, double *__restrict__ f) {
@@ -329,6 +538,74 @@ __global__ void k_refine_rhs(int m, const int32_t *__restrict__ rp, const int32_
   double s = 0.0;
   for (int e = rp[i]; e < rp[i + 1]; ++e) s += val[e] * (1.0 + (double)(ci[e] % 7) / 8.0);
   f[i] = s;
+}
+
+}  // namespace
+
+namespace {
+
+// Refinement steps the FP32 inverse in h->ainv32 needs: the fewest steps s
+// whose refined solve of a test system has a normwise backward error of at
+// most GJ_BACKWARD_TOL, plus one step of margin; -1 when no s <= GJ_REFINE_MAX
+// gets there.
+amg_status refine_steps(amg_hierarchy *h, cudaStream_t st, int *steps_out) {
+  const Level &c = h->lev[h->L];
+  const int m = c.n;
+  *steps_out = -1;
+  double *f = nullptr;
+  if (pool_alloc((void **)&f, sizeof(double) * 2 * ((size_t)m + AMG_PAD), st) != AMG_OK) return AMG_ERR_OOM;
+  double *x = f + (m + AMG_PAD);
+  const int TB = AMG_THREADS;
+  k_refine_rhs<<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, f);
+  count_launch();
+  // the coarsest matrix and f on the host, for the backward error of each trial
+  const long long nnz = c.nnz;
+  std::vector<int32_t> hrp(m + 1), hci(nnz);
+  std::vector<double> hval(nnz), hf(m), hx(m);
+  cudaError_t ce = cudaMemcpyAsync(hrp.data(), c.rp, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess && nnz)
+    ce = cudaMemcpyAsync(hci.data(), c.ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess && nnz)
+    ce = cudaMemcpyAsync(hval.data(), c.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hf.data(), f, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) {
+    pool_free(f, st);
+    return amg_cuda_status(ce);
+  }
+  double norm_a = 0.0, norm_f = 0.0;
+  for (int i = 0; i < m; ++i) {
+    double rs = 0.0;
+    for (int e = hrp[i]; e < hrp[i + 1]; ++e) rs += std::fabs(hval[e]);
+    norm_a = std::max(norm_a, rs);
+    norm_f = std::max(norm_f, std::fabs(hf[i]));
+  }
+  for (int s = 0; s <= GJ_REFINE_MAX; ++s) {
+    amg_status rs = dense_refined_solve<double>(h, f, x, s, st, nullptr);
+    if (rs == AMG_OK && cudaMemcpyAsync(hx.data(), x, sizeof(double) * m, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      rs = AMG_ERR_CUDA;
+    if (rs == AMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rs = AMG_ERR_CUDA;
+    if (rs != AMG_OK) {
+      pool_free(f, st);
+      return rs;
+    }
+    double res = 0.0, norm_x = 0.0;
+    bool finite = true;
+    for (int i = 0; i < m; ++i) {
+      if (!std::isfinite(hx[i])) finite = false;
+      norm_x = std::max(norm_x, std::fabs(hx[i]));
+      double ax = 0.0;
+      for (int e = hrp[i]; e < hrp[i + 1]; ++e) ax += hval[e] * hx[hci[e]];
+      res = std::max(res, std::fabs(hf[i] - ax));
+    }
+    if (!finite) break;
+    if (res <= GJ_BACKWARD_TOL * (norm_a * norm_x + norm_f)) {
+      *steps_out = s + 1;  // one step of margin
+      break;
+    }
+  }
+  pool_free(f, st);
+  return AMG_OK;
 }
 
 }  // namespace
@@ -342,65 +619,23 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
   if (m > GJ_FP64_MAX) {
     AMG_TRY(hier_alloc(h, (void **)&h->ainv32, sizeof(float) * ((size_t)m * m + AMG_PAD)));
     AMG_TRY(hier_alloc(h, (void **)&h->dense_r, sizeof(double) * 2 * ((size_t)m + AMG_PAD)));
-    AMG_TRY(gj_inverse<float>(h, h->ainv32, st));
-    // measure the refinement on a test vector
-    double *f = nullptr;
-    if (pool_alloc((void **)&f, sizeof(double) * 2 * ((size_t)m + AMG_PAD), st) != AMG_OK) return AMG_ERR_OOM;
-    double *x = f + (m + AMG_PAD);
-    const int TB = AMG_THREADS;
-    k_refine_rhs<<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, f);
-    count_launch();
-    // the coarsest matrix and f on the host, for the backward error of each trial
-    const long long nnz = c.nnz;
-    std::vector<int32_t> hrp(m + 1), hci(nnz);
-    std::vector<double> hval(nnz), hf(m), hx(m);
-    cudaError_t ce = cudaMemcpyAsync(hrp.data(), c.rp, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess && nnz)
-      ce = cudaMemcpyAsync(hci.data(), c.ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess && nnz)
-      ce = cudaMemcpyAsync(hval.data(), c.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hf.data(), f, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-    if (ce != cudaSuccess) {
-      pool_free(f, st);
-      return amg_cuda_status(ce);
-    }
-    double norm_a = 0.0, norm_f = 0.0;
-    for (int i = 0; i < m; ++i) {
-      double rs = 0.0;
-      for (int e = hrp[i]; e < hrp[i + 1]; ++e) rs += std::fabs(hval[e]);
-      norm_a = std::max(norm_a, rs);
-      norm_f = std::max(norm_f, std::fabs(hf[i]));
-    }
-    int steps = -1;
-    for (int s = 0; s <= GJ_REFINE_MAX; ++s) {
-      amg_status rs = dense_refined_solve<double>(h, f, x, s, st, nullptr);
-      if (rs == AMG_OK && cudaMemcpyAsync(hx.data(), x, sizeof(double) * m, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        rs = AMG_ERR_CUDA;
-      if (rs == AMG_OK && cudaStreamSynchronize(st) != cudaSuccess) rs = AMG_ERR_CUDA;
-      if (rs != AMG_OK) {
-        pool_free(f, st);
-        return rs;
+    // FP32 inverse: first without row interchanges (blocked over the whole
+    // GPU), then, if a pivot vanished or the refinement does not reach FP64
+    // accuracy, with partial pivoting
+    for (int pivoting = 0; pivoting < 2; ++pivoting) {
+      if (!pivoting) {
+        amg_status rs = bgj_inverse<float>(h, h->ainv32, st);
+        if (rs == AMG_ERR_BREAKDOWN) continue;
+        AMG_TRY(rs);
+      } else {
+        AMG_TRY(gj_inverse<float>(h, h->ainv32, st));
       }
-      double res = 0.0, norm_x = 0.0;
-      bool finite = true;
-      for (int i = 0; i < m; ++i) {
-        if (!std::isfinite(hx[i])) finite = false;
-        norm_x = std::max(norm_x, std::fabs(hx[i]));
-        double ax = 0.0;
-        for (int e = hrp[i]; e < hrp[i + 1]; ++e) ax += hval[e] * hx[hci[e]];
-        res = std::max(res, std::fabs(hf[i] - ax));
+      int steps = -1;
+      AMG_TRY(refine_steps(h, st, &steps));
+      if (steps >= 0) {
+        h->dense_refine = steps;
+        return AMG_OK;
       }
-      if (!finite) break;
-      if (res <= GJ_BACKWARD_TOL * (norm_a * norm_x + norm_f)) {
-        steps = s;
-        break;
-      }
-    }
-    pool_free(f, st);
-    if (steps >= 0) {
-      h->dense_refine = steps + 1;  // one step of margin
-      return AMG_OK;
     }
     h->ainv32 = nullptr;  // refinement does not reach FP64 accuracy: FP64 inverse
   }

@@ -79,6 +79,36 @@ __global__ void k_init_residual(int n, const int32_t *__restrict__ rp, const int
   }
 }
 
+// Residual replacement after a stop on the recurrence residual whose true
+// residual misses the tolerance: r = b - A x, and the solve continues from x
+// (its iteration count and limit carry on) unless r already meets rtol.
+template <int TPR>
+__global__ void k_restart_residual(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                   const double *__restrict__ val, const double *__restrict__ b,
+                                   const double *__restrict__ x, double *__restrict__ r, double *part,
+                                   unsigned *counter, KState *st) {
+  double v[1] = {0.0};
+  KROW_LOOP_BEGIN(TPR, n)
+  int rb = 0, re = 0;
+  if (valid) { rb = __ldg(&rp[row]); re = __ldg(&rp[row + 1]); }
+  double ax = row_dot64<TPR>(ci, val, rb, re, _sub, x);
+  if (valid && _sub == 0) {
+    double ri = b[row] - ax;
+    r[row] = ri;
+    v[0] += ri * ri;
+  }
+  KROW_LOOP_END
+  double tot[1];
+  if (grid_sum_last<1>(v, part, counter, tot) && threadIdx.x == 0) {
+    st->rel = sqrt(tot[0]) / st->bnorm;
+    st->half = 0;
+    if (st->rel <= st->rtol) { st->done = 1; st->status = AMG_OK; }
+    else if (!isfinite(st->rel)) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
+    else if (st->it >= st->max_iter) { st->done = 1; st->status = AMG_ERR_NOT_CONVERGED; }
+    else { st->done = 0; st->status = AMG_ERR_NOT_CONVERGED; }
+  }
+}
+
 // ||b - A x|| / ||b|| recomputed from x (reported as rel_res_true).
 template <int TPR>
 __global__ void k_true_residual(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
@@ -528,6 +558,33 @@ amg_status begin_solve(amg_hierarchy *h, const double *b, const double *x0, doub
   return amg_cuda_status(cudaGetLastError());
 }
 
+// Restarts allowed per solve after a stop whose true residual misses rtol.
+#define KRYLOV_RESTARTS 4
+
+// After a stop on the recurrence residual: computes the true residual and,
+// when it misses rtol (the recurrence drifted) while iterations remain,
+// replaces r by b - A x and returns true so the caller restarts the method
+// from x.  At most KRYLOV_RESTARTS times per solve.
+amg_status true_residual_restart(amg_hierarchy *h, cudaStream_t s, int *restarts, bool *restart) {
+  const int n = h->lev[0].n;
+  Level &l = h->lev[0];
+  *restart = false;
+  AMG_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  const KState k0 = *h->st_host;
+  if (k0.status != AMG_OK || k0.bnorm == 0.0 || *restarts >= KRYLOV_RESTARTS || k0.it >= k0.max_iter) return AMG_OK;
+  KDISPATCH(l, k_true_residual, n, l.rp, l.ci, l.val, h->kb, h->kx, h->part, h->counter + KSLOT_A, h->st);
+  AMG_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  if (!(h->st_host->rel_true > h->st_host->rtol)) return AMG_OK;
+  *restarts += 1;
+  KDISPATCH(l, k_restart_residual, n, l.rp, l.ci, l.val, h->kb, h->kx, h->kr, h->part, h->counter + KSLOT_A, h->st);
+  AMG_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+  AMG_CUDA(cudaStreamSynchronize(s));
+  *restart = h->st_host->done == 0;
+  return AMG_OK;
+}
+
 amg_status end_solve(amg_hierarchy *h, double *x, cudaStream_t s, amg_solve_info *info) {
   const int n = h->lev[0].n;
   Level &l = h->lev[0];
@@ -573,13 +630,18 @@ extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, doub
   h->last_stream = s;
   const int n = h->lev[0].n;
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, flexible ? 1 : 0, s));
-  AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
-  {
-    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-    k_pcg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kz, h->kp, h->part, h->counter + KSLOT_B, h->st);
+  int restarts = 0;
+  for (bool again = true; again;) {
+    AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
+    {
+      LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
+      k_pcg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kz, h->kp, h->part, h->counter + KSLOT_B,
+                                                        h->st);
+    }
+    AMG_CUDA(cudaGetLastError());
+    AMG_TRY(run_iterations(h, pcg_iteration, &h->g_pcg, &h->g_pcg_nodes, s));
+    AMG_TRY(true_residual_restart(h, s, &restarts, &again));
   }
-  AMG_CUDA(cudaGetLastError());
-  AMG_TRY(run_iterations(h, pcg_iteration, &h->g_pcg, &h->g_pcg_nodes, s));
   return end_solve(h, d_x, s, info);
 }
 
@@ -591,19 +653,23 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
   h->last_stream = s;
   const int n = h->lev[0].n;
   AMG_TRY(begin_solve(h, d_b, d_x, rtol, max_iter, 0, s));
-  {
-    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 4.0 * 8.0 * n);
-    k_bicg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->krb, h->kp, h->part, h->counter + KSLOT_B, h->st);
-  }
-  AMG_CUDA(cudaGetLastError());
-  AMG_TRY(run_iterations(h, bicg_iteration, &h->g_bicg, &h->g_bicg_nodes, s));
-  AMG_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KState), cudaMemcpyDeviceToHost, s));
-  AMG_CUDA(cudaStreamSynchronize(s));
-  if (h->st_host->half == 1)
+  int restarts = 0;
+  for (bool again = true; again;) {
     {
+      LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 4.0 * 8.0 * n);
+      k_bicg_start<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->krb, h->kp, h->part, h->counter + KSLOT_B,
+                                                         h->st);
+    }
+    AMG_CUDA(cudaGetLastError());
+    AMG_TRY(run_iterations(h, bicg_iteration, &h->g_bicg, &h->g_bicg_nodes, s));
+    AMG_CUDA(cudaMemcpyAsync(h->st_host, h->st, sizeof(KState), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA(cudaStreamSynchronize(s));
+    if (h->st_host->half == 1) {
       LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
       k_axpy_half<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kph, h->st);
     }
+    AMG_TRY(true_residual_restart(h, s, &restarts, &again));
+  }
   return end_solve(h, d_x, s, info);
 }
 

@@ -125,6 +125,7 @@ __global__ void k_hem_init(int n, int32_t *mate, int32_t *dirty, int *stamp) {
 // nobody (the fixed point).  Lists are walked with grid-stride loops.
 #define HEM_BLOCK_CAP 2048     // largest dirty list handled by the one-block rounds
 #define HEM_BLOCK_ROUNDS 4096  // rounds per launch of the one-block rounds
+#define HEM_COOP_THREADS 512   // threads per block of the cooperative rounds
 
 // Slot for one appended list entry: the lanes of the warp that append at the
 // same time share one atomic on the counter.
@@ -293,6 +294,98 @@ __global__ void __launch_bounds__(1024)
     out[1] = finished;
     out[2] = nd;
     out[3] = which;
+  }
+}
+
+// Heaviest free neighbour of i (smaller index on equal weight, or the larger
+// one with tie_larger); -1 when i has no free neighbour.  mate is read past
+// the L1 cache: other blocks of a persistent kernel write it.
+__device__ __forceinline__ int hem_pick_node(int i, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                             const double *__restrict__ w, int tie_larger, const int32_t *mate) {
+  int best = -1;
+  double bw = 0.0;
+  const int e1 = __ldg(&rp[i + 1]);
+  for (int e = __ldg(&rp[i]); e < e1; ++e) {
+    const double we = __ldg(&w[e]);
+    if (we <= 0.0) continue;
+    const int j = __ldg(&ci[e]);
+    if (__ldcg(&mate[j]) != HEM_FREE) continue;
+    if (best < 0 || we > bw || (tie_larger && we == bw)) { best = j; bw = we; }
+  }
+  return best;
+}
+
+// Every round of one matching pass in one cooperative launch (all blocks
+// resident): the incremental rounds above with two bounded grid barriers per
+// round instead of three launches and periodic host checks.  Round r:
+//   A. each node i of D_r whose pick j picks i back is paired with j; the
+//      newly matched nodes are listed in M (each once);
+//   B. every free neighbour q of a node of M whose pick was that node is put
+//      in D_{r+1} (stamp = r + 1) and re-picks among its free neighbours,
+//      which now exclude this round's pairs.
+// D_0 is every node (picks of phase 0).  The pass ends after the first round
+// that pairs nobody; out[0] = rounds run (that last one included), out[1] = 1
+// when it ended, 0 when it stopped at max_rounds or on a barrier timeout.
+// Counters: three slots of (matched, next-list size), slot r % 3 for round r.
+__global__ void __launch_bounds__(HEM_COOP_THREADS)
+    k_hem_coop(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
+               int tie_larger, int32_t *mate, int32_t *pick, int *stamp, int32_t *Da, int32_t *Db, int32_t *M,
+               int *ctr, unsigned *bar, unsigned *eflags, int max_rounds, int *out) {
+  __shared__ int fail_sh;
+  if (threadIdx.x == 0) fail_sh = 0;
+  const unsigned G = gridDim.x;
+  GridBarrier gb{bar, 0u};
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  for (int i = gtid; i < n; i += gstride) pick[i] = hem_pick_node(i, rp, ci, w, tie_larger, mate);
+  if (!gb.sync(G, eflags, &fail_sh)) return;
+  int32_t *D = Da, *Dn = Db;
+  int nd = n, r = 0;
+  bool finished = false;
+  for (; r < max_rounds; ++r) {
+    int *slot = ctr + 2 * (r % 3);
+    if (gtid == 0) {  // the slot of round r + 1 (last used by round r - 2)
+      int *nx = ctr + 2 * ((r + 1) % 3);
+      nx[0] = 0;
+      nx[1] = 0;
+    }
+    // A: pairs
+    for (int t = gtid; t < nd; t += gstride) {
+      const int i = r == 0 ? t : __ldcg(&D[t]);
+      const int j = __ldcg(&pick[i]);
+      if (j < 0 || __ldcg(&pick[j]) != i) continue;
+      mate[i] = j;
+      mate[j] = i;
+      M[warp_append(&slot[0])] = i;
+      if (__ldcg(&stamp[j]) != r) M[warp_append(&slot[0])] = j;
+    }
+    if (!gb.sync(G, eflags, &fail_sh)) return;
+    const int nm = __ldcg(&slot[0]);
+    if (nm == 0) {
+      finished = true;
+      ++r;
+      break;
+    }
+    // B: next list and its new picks
+    for (int t = gtid; t < nm; t += gstride) {
+      const int m = __ldcg(&M[t]);
+      const int e1 = __ldg(&rp[m + 1]);
+      for (int e = __ldg(&rp[m]); e < e1; ++e) {
+        const int q = __ldg(&ci[e]);
+        if (q == m || __ldcg(&mate[q]) != HEM_FREE || __ldcg(&pick[q]) != m) continue;
+        if (atomicExch(&stamp[q], r + 1) == r + 1) continue;
+        pick[q] = hem_pick_node(q, rp, ci, w, tie_larger, mate);
+        Dn[warp_append(&slot[1])] = q;
+      }
+    }
+    if (!gb.sync(G, eflags, &fail_sh)) return;
+    nd = __ldcg(&slot[1]);
+    int32_t *tmp = D;
+    D = Dn;
+    Dn = tmp;
+  }
+  if (gtid == 0) {
+    out[0] = r;
+    out[1] = finished ? 1 : 0;
   }
 }
 
@@ -577,6 +670,74 @@ __global__ void k_sort_members(int nc, const int32_t *__restrict__ mrp, int32_t 
 }
 
 // ---------------------------------------------------------------------------
+// Residual-operator form of a zero-guess cycle visit (levels < L): the
+// presmoothed iterate x = omega D^-1 f is folded into C = I - omega A D^-1,
+// and prolongation plus postsmoothing into Q = P - omega D^-1 A P (see Level).
+// One thread per row; setup only.
+// ---------------------------------------------------------------------------
+// c_ij = -a_ij (omega / a_jj) for j != i, c_ii = 1 - a_ii (omega / a_ii);
+// wd_i = omega / a_ii.
+__global__ void k_op_c(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                       const double *__restrict__ val, const double *__restrict__ dinv, double omega,
+                       double *__restrict__ cval, double *__restrict__ wd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  wd[i] = omega * dinv[i];
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int j = ci[e];
+    const double b = val[e] * (omega * dinv[j]);
+    cval[e] = (j == i) ? 1.0 - b : -b;
+  }
+}
+
+// Entries of row i of A P: the distinct aggregates agg[j] of its columns.
+__global__ void k_op_qcount(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                            const int32_t *__restrict__ agg, int *__restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = rp[i], e = rp[i + 1];
+  int c = 0;
+  for (int k = b; k < e; ++k) {
+    const int a = agg[ci[k]];
+    bool seen = false;
+    for (int m = b; m < k && !seen; ++m) seen = agg[ci[m]] == a;
+    c += seen ? 0 : 1;
+  }
+  cnt[i] = c;
+}
+
+// Row i of Q: columns J ascending; (A P)_iJ sums the row's a_ij with agg[j] = J
+// in stored order (the first one starts the sum), and
+// q_iJ = [J == agg[i]] - wd_i (A P)_iJ.
+__global__ void k_op_qfill(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                           const double *__restrict__ val, const int32_t *__restrict__ agg,
+                           const double *__restrict__ wd, const int32_t *__restrict__ qrp, int32_t *__restrict__ qci,
+                           double *__restrict__ qval) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = rp[i], e = rp[i + 1], ai = agg[i];
+  const double w = wd[i];
+  int last = -1;
+  for (int o = qrp[i]; o < qrp[i + 1]; ++o) {
+    int J = 0x7fffffff;
+    for (int k = b; k < e; ++k) {
+      const int a = agg[ci[k]];
+      if (a > last && a < J) J = a;
+    }
+    double sum = 0.0;
+    bool first = true;
+    for (int k = b; k < e; ++k) {
+      if (agg[ci[k]] != J) continue;
+      sum = first ? val[k] : sum + val[k];
+      first = false;
+    }
+    qci[o] = J;
+    qval[o] = (J == ai ? 1.0 : 0.0) - w * sum;
+    last = J;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 namespace {
@@ -613,7 +774,7 @@ amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
   AMG_TRY(pool_alloc((void **)&s.id, sizeof(int) * (n + AMG_PAD), st));
   AMG_TRY(pool_alloc((void **)&s.count, sizeof(int) * (n + AMG_PAD), st));
   AMG_TRY(pool_alloc((void **)&s.tiles, sizeof(int) * (tiles + 8), st));
-  AMG_TRY(pool_alloc((void **)&s.cnt, sizeof(int) * 40, st));
+  AMG_TRY(pool_alloc((void **)&s.cnt, sizeof(int) * 64, st));
   s.host = (int *)pinned_small_alloc();
   if (!s.host) return AMG_ERR_OOM;
   s.cap_n = n;
@@ -641,6 +802,22 @@ amg_status check_flags(amg_hierarchy *h, cudaStream_t st) {
   return AMG_OK;
 }
 
+// Blocks of the cooperative handshake kernel on this device (at most two per
+// SM), or 0 when the device cannot launch it cooperatively.
+int hem_coop_blocks(amg_hierarchy *h) {
+  int coop = 0, occ = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hem_coop, HEM_COOP_THREADS, 0) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return std::min(occ, 2) * h->num_sms;
+}
+
 // One pairwise pass on `in`: matching rounds, numbering, Galerkin product.
 // pass_agg (n entries) receives the map; `out` the coarse CSR (allocated here).
 amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pass_agg, Csr &out,
@@ -660,6 +837,31 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   const int round_cap = 4 * n + 16;  // each productive round pairs >= 1 node
   int batch = 4;                     // rounds per host check: 4, 8, then 16
   bool finished = false, frontier_rounds = true;
+  const int coop_blocks = hem_coop_blocks(h);
+  if (coop_blocks > 0) {
+    // every round in one cooperative launch
+    int *ctr = S.cnt + 40, *out = S.cnt + 48;
+    unsigned *bar = (unsigned *)(S.cnt + 50);
+    AMG_CUDA(cudaMemsetAsync(S.cnt + 40, 0, sizeof(int) * 12, st));
+    int a_n = n, a_tie = tie_larger, a_max = round_cap;
+    const int32_t *a_rp = in.rp, *a_ci = in.ci;
+    const double *a_w = S.w;
+    int32_t *a_mate = S.mate, *a_pick = S.pick, *a_da = S.fa, *a_db = S.fb, *a_m = S.first;
+    int *a_stamp = S.flag;
+    unsigned *a_ef = h->eflags;
+    void *args[] = {&a_n, &a_rp, &a_ci, &a_w, &a_tie, &a_mate, &a_pick, &a_stamp, &a_da, &a_db, &a_m,
+                    &ctr, &bar, &a_ef, &a_max, &out};
+    AMG_CUDA(cudaLaunchCooperativeKernel((void *)k_hem_coop, coop_blocks, HEM_COOP_THREADS, args, 0, st));
+    count_launch();
+    AMG_CUDA(cudaMemcpyAsync(S.host, out, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA(cudaStreamSynchronize(st));
+    r = S.host[0];
+    finished = true;
+    if (!S.host[1]) {
+      AMG_TRY(check_flags(h, st));
+      return AMG_ERR_TIMEOUT;
+    }
+  }
   const int grid = std::min(cdiv(std::max(n, 1), T), 8 * h->num_sms);
   while (!finished) {
     if (r > round_cap) return AMG_ERR_TIMEOUT;
@@ -749,6 +951,7 @@ amg_status validate_params(const amg_params *p) {
   if (p->cycle < AMG_CYCLE_V || p->cycle > AMG_CYCLE_F) return AMG_ERR_INVALID_ARG;
   if (p->tie_break != AMG_TIE_SMALLER && p->tie_break != AMG_TIE_LARGER) return AMG_ERR_INVALID_ARG;
   if (p->edge_weight != AMG_WEIGHT_ABS && p->edge_weight != AMG_WEIGHT_SCALED) return AMG_ERR_INVALID_ARG;
+  if (p->operator_form != 0 && p->operator_form != 1) return AMG_ERR_INVALID_ARG;
   return AMG_OK;
 }
 
@@ -844,6 +1047,59 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
 
 }  // namespace
 
+// Forms C, Q and wd of every level below the coarsest (FP64; the FP32 mode's
+// copies are made by precision_setup).  Only for one pre- and one post-sweep,
+// and not in the FP16-storage mode, whose levels are scaled.
+amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
+  const amg_params &p = h->prm;
+  if (!p.operator_form || p.precision == AMG_FP16_STORAGE || p.nu_pre != 1 || p.nu_post != 1) return AMG_OK;
+  const int T = AMG_THREADS;
+  int nmax = 1;
+  for (int k = 0; k < h->L; ++k) nmax = std::max(nmax, h->lev[k].n);
+  int *cnt = nullptr, *tiles = nullptr, *tot = nullptr;
+  AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * (nmax + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&tiles, sizeof(int) * (cdiv(nmax, SCAN_TILE) + 8), st));
+  AMG_TRY(pool_alloc((void **)&tot, sizeof(int) * 2 * AMG_MAX_LEVELS, st));
+  int *host = (int *)pinned_small_alloc();
+  if (!host) return AMG_ERR_OOM;
+  amg_status rs = AMG_OK;
+  for (int k = 0; k < h->L && rs == AMG_OK; ++k) {
+    Level &l = h->lev[k];
+    rs = hier_alloc(h, (void **)&l.cval, sizeof(double) * (l.nnz + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.wd, sizeof(double) * (l.n + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.qrp, sizeof(int32_t) * (l.n + 1 + AMG_PAD));
+    if (rs != AMG_OK) break;
+    cudaMemsetAsync(l.cval + l.nnz, 0, sizeof(double) * AMG_PAD, st);
+    k_op_c<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.dinv, p.omega, l.cval, l.wd); count_launch();
+    k_op_qcount<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.agg, cnt); count_launch();
+    scan_excl(cnt, l.qrp, l.n, tot + k, tiles, st);
+    cudaMemcpyAsync(l.qrp + l.n, tot + k, sizeof(int), cudaMemcpyDeviceToDevice, st);
+  }
+  if (rs == AMG_OK) {
+    rs = amg_cuda_status(cudaMemcpyAsync(host, tot, sizeof(int) * h->L, cudaMemcpyDeviceToHost, st));
+    if (rs == AMG_OK) rs = amg_cuda_status(cudaStreamSynchronize(st));
+  }
+  for (int k = 0; k < h->L && rs == AMG_OK; ++k) {
+    Level &l = h->lev[k];
+    l.qnnz = host[k];
+    rs = hier_alloc(h, (void **)&l.qci, sizeof(int32_t) * (l.qnnz + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.qval, sizeof(double) * (l.qnnz + AMG_PAD));
+    if (rs != AMG_OK) break;
+    cudaMemsetAsync(l.qci + l.qnnz, 0, sizeof(int32_t) * AMG_PAD, st);
+    cudaMemsetAsync(l.qval + l.qnnz, 0, sizeof(double) * AMG_PAD, st);
+    k_op_qfill<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.agg, l.wd, l.qrp, l.qci, l.qval);
+    count_launch();
+    l.op_avail = 1;
+    l.op_on = 1;
+  }
+  pinned_small_free(host);
+  pool_free(cnt, st);
+  pool_free(tiles, st);
+  pool_free(tot, st);
+  if (rs != AMG_OK) return rs;
+  return amg_cuda_status(cudaGetLastError());
+}
+
 extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                                 const double *d_val, const amg_params *params, amg_stream_t stream,
                                 amg_hierarchy **out) {
@@ -873,6 +1129,8 @@ extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, co
     s = setup_impl(h, n, nnz, d_row_ptr, d_col, d_val, st);
     if (s) break;
     s = coarse_setup(h, st);
+    if (s) break;
+    s = operator_form_setup(h, st);
     if (s) break;
     s = precision_setup(h, st);
     if (s) break;

@@ -200,6 +200,39 @@ __global__ void k_jacobi(int n, const int32_t *__restrict__ perm, const int32_t 
   ROW_LOOP_END
 }
 
+// Residual-operator form of a zero-guess visit (Level documents C and Q).
+// t = C f: the residual f - A x of the first damped-Jacobi sweep x = omega
+// D^-1 f, in one pass over C (A's pattern) without forming x.
+template <int TPR, typename T, typename V>
+__global__ void k_op_residual(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp,
+                              const int32_t *__restrict__ ci, const V *__restrict__ cval, const T *__restrict__ f,
+                              T *__restrict__ t, const KState *st) {
+  if (is_done(st)) return;
+  ROW_LOOP_BEGIN(TPR, n)
+  int b = 0, e = 0;
+  if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
+  T cf = row_sum<TPR, T, V>(ci, cval, b, e, _sub, [&](int j) { return __ldg(&f[j]); });
+  if (valid && _sub == 0) t[row] = cf;
+  ROW_LOOP_END
+}
+
+// y = Q x_c + wd (f + t): prolongation of the coarse correction and the first
+// postsmoothing sweep, x + P x_c + omega D^-1 (f - A (x + P x_c)), in one pass
+// over Q (the pattern of A P, n x n_c).
+template <int TPR, typename T, typename V>
+__global__ void k_op_post(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ qrp,
+                          const int32_t *__restrict__ qci, const V *__restrict__ qval, const T *__restrict__ xc,
+                          const T *__restrict__ wd, const T *__restrict__ f, const T *__restrict__ t,
+                          T *__restrict__ y, const KState *st) {
+  if (is_done(st)) return;
+  ROW_LOOP_BEGIN(TPR, n)
+  int b = 0, e = 0;
+  if (valid) { b = __ldg(&qrp[row]); e = __ldg(&qrp[row + 1]); }
+  T qx = row_sum<TPR, T, V>(qci, qval, b, e, _sub, [&](int J) { return __ldg(&xc[J]); });
+  if (valid && _sub == 0) y[row] = qx + wd[row] * (f[row] + t[row]);
+  ROW_LOOP_END
+}
+
 // ---------------------------------------------------------------------------
 // TMA-staged row kernels (lanes-per-row choice 0): each block walks tiles of
 // ST_ROWS consecutive rows; one elected thread copies a tile's values and
@@ -674,50 +707,7 @@ template amg_status dense_refined_solve<float>(amg_hierarchy *, const float *, f
 #ifndef CG_MAXQ
 #define CG_MAXQ 16      // neighbours a lane gathers in one round
 #endif
-#define BARRIER_SPIN_LIMIT (1ll << 31)  // clock cycles (about one second)
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-
-// Monotonic-counter grid barrier: the k-th barrier completes when the counter
-// reaches k * G.  Waits are bounded; a block that gives up sets the timeout
-// flag and the caller leaves its loop.  arrive() and wait() may be split so
-// that a block does independent work while the others arrive.
-struct GridBarrier {
-  unsigned *count;
-  unsigned target;
-  long long limit = BARRIER_SPIN_LIMIT;
-  __device__ __forceinline__ void arrive(unsigned G) {
-    __syncthreads();
-    target += G;
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(count, 1u);
-    }
-  }
-  __device__ __forceinline__ bool wait(unsigned *eflags, int *fail_sh) {
-    if (threadIdx.x == 0) {
-      long long t0 = clock64();
-      while (ld_acquire_u32(count) < target) {
-        if (clock64() - t0 > limit) {
-          atomicOr(eflags, AMG_EFLAG_TIMEOUT);
-          *fail_sh = 1;
-          break;
-        }
-      }
-    }
-    __syncthreads();
-    return *fail_sh == 0;
-  }
-  __device__ __forceinline__ bool sync(unsigned G, unsigned *eflags, int *fail_sh) {
-    arrive(G);
-    return wait(eflags, fail_sh);
-  }
-};
 
 __device__ __forceinline__ int cg_key(int len) { return len < CG_KEYS - 1 ? len : CG_KEYS - 1; }
 
@@ -1202,6 +1192,9 @@ template <> struct Sel<double, double> {
   static const double *dinv(const Level &l) { return l.dinv; }
   static const float *sig(const Level &) { return nullptr; }
   static const float *isig(const Level &) { return nullptr; }
+  static const double *cval(const Level &l) { return l.cval; }
+  static const double *qval(const Level &l) { return l.qval; }
+  static const double *wd(const Level &l) { return l.wd; }
 };
 template <> struct Sel<float, float> {
   static float *f(Level &l) { return l.f32; }
@@ -1212,6 +1205,9 @@ template <> struct Sel<float, float> {
   static const float *dinv(const Level &l) { return l.dinv32; }
   static const float *sig(const Level &) { return nullptr; }
   static const float *isig(const Level &) { return nullptr; }
+  static const float *cval(const Level &l) { return l.cval32; }
+  static const float *qval(const Level &l) { return l.qval32; }
+  static const float *wd(const Level &l) { return l.wd32; }
 };
 template <> struct Sel<float, __half> {
   static float *f(Level &l) { return l.f32; }
@@ -1222,6 +1218,9 @@ template <> struct Sel<float, __half> {
   static const float *dinv(const Level &) { return nullptr; }
   static const float *sig(const Level &l) { return l.sig; }
   static const float *isig(const Level &l) { return l.isig; }
+  static const __half *cval(const Level &) { return nullptr; }
+  static const __half *qval(const Level &) { return nullptr; }
+  static const float *wd(const Level &) { return nullptr; }
 };
 
 inline int row_blocks(const Level &l) {
@@ -1347,6 +1346,31 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
   const T *dinv = S::dinv(l);
   const V *val = S::val(l);
   const double BA = bytes_A(l, (int)szv);
+  if (!guess && nu_pre == 1 && nu_post == 1 && l.op_on && S::cval(l)) {
+    // residual-operator form: t = C f, restriction, coarse correction,
+    // out = Q x_c + wd (f + t)
+    {
+      LaunchScope ls(h, s, PK_OP_RESIDUAL, k, BA + 2.0 * sz * l.n);
+      DISPATCH_ROWS(l, k_op_residual, l.n, l.perm, l.rp, l.ci, S::cval(l), f, b, st);
+    }
+    {
+      LaunchScope ls(h, s, PK_RESTRICT, k, (sz + 4.0) * l.n + (sz + 4.0) * c.n + 4.0);
+      k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, nullptr, nullptr,
+                                                                        S::f(c), st);
+    }
+    T *xc = S::y(c);
+    const T *fc = S::f(c);
+    cycle_level<T, V>(h, k + 1, fc, nullptr, xc, kind, s, st);
+    if (k + 1 < L && kind == AMG_CYCLE_W) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_W, s, st);
+    if (k + 1 < L && kind == AMG_CYCLE_F) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_V, s, st);
+    {
+      const double BQ = (double)l.qnnz * (szv + 4.0) + 4.0 * (l.n + 1);
+      LaunchScope ls(h, s, PK_OP_POST, k, BQ + 4.0 * sz * l.n + sz * c.n);
+      DISPATCH_ROWS(l, k_op_post, l.n, l.perm, l.qrp, l.qci, S::qval(l), (const T *)xc, S::wd(l), f,
+                    (const T *)b, out, st);
+    }
+    return;
+  }
   // presmoothing (nu_pre >= 1 sweeps), then the residual in b
   if (!guess && nu_pre == 1 && l.fuse_pre) {
     LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 4.0 * sz * l.n);
@@ -1550,6 +1574,17 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
         k_to_f32<<<grid_for(l.nnz, AMG_THREADS), AMG_THREADS, 0, s>>>(l.nnz, l.val, l.val32);
         k_to_f32<<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, l.dinv, l.dinv32);
         count_launch(2);
+        if (l.op_avail) {
+          // the residual-operator form's C, Q and wd rounded to FP32
+          AMG_TRY(hier_alloc(h, (void **)&l.cval32, sizeof(float) * (l.nnz + AMG_PAD)));
+          AMG_TRY(hier_alloc(h, (void **)&l.qval32, sizeof(float) * (l.qnnz + AMG_PAD)));
+          AMG_TRY(hier_alloc(h, (void **)&l.wd32, vf));
+          k_to_f32<<<grid_for(l.nnz + AMG_PAD, AMG_THREADS), AMG_THREADS, 0, s>>>(l.nnz + AMG_PAD, l.cval, l.cval32);
+          k_to_f32<<<grid_for(l.qnnz + AMG_PAD, AMG_THREADS), AMG_THREADS, 0, s>>>(l.qnnz + AMG_PAD, l.qval,
+                                                                                    l.qval32);
+          k_to_f32<<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, l.wd, l.wd32);
+          count_launch(3);
+        }
       }
     }
   }
@@ -1630,7 +1665,7 @@ amg_status precision_setup(amg_hierarchy *h, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 namespace {
 
-struct TuneChoice { int tpr, fuse_pre, fuse_post; };
+struct TuneChoice { int tpr, fuse_pre, fuse_post, op_on; };
 std::mutex g_tune_mu;
 std::map<std::tuple<int, long long, int>, TuneChoice> g_tune;
 
@@ -1702,9 +1737,19 @@ amg_status tune_levels(amg_hierarchy *h, cudaStream_t s) {
       launch_jacobi<T, V>(h, l, val, dinv, omega, t, f, y, s, nullptr);
     });
     l.fuse_post = post_fused <= post_split ? 1 : 0;
+    // residual-operator form against the faster explicit forms
+    if (l.op_avail && S::cval(l)) {
+      float op = time_launch<T>(s, ea, eb, reps, [&]() {
+        DISPATCH_ROWS(l, k_op_residual, l.n, l.perm, l.rp, l.ci, S::cval(l), f, t, (const KState *)nullptr);
+        DISPATCH_ROWS(l, k_op_post, l.n, l.perm, l.qrp, l.qci, S::qval(l), xc, S::wd(l), f, (const T *)t, y,
+                      (const KState *)nullptr);
+      });
+      l.op_on = op <= std::min(pre_fused, pre_split) + std::min(post_fused, post_split) ? 1 : 0;
+    }
     count_launch(0);
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[std::make_tuple(l.n, (long long)l.nnz, h->prm.precision)] = TuneChoice{l.tpr, l.fuse_pre, l.fuse_post};
+    g_tune[std::make_tuple(l.n, (long long)l.nnz, h->prm.precision)] =
+        TuneChoice{l.tpr, l.fuse_pre, l.fuse_post, l.op_on};
   }
   cudaEventDestroy(ea);
   cudaEventDestroy(eb);
@@ -1723,6 +1768,7 @@ static void apply_tuned(amg_hierarchy *h) {
       l.tpr = it->second.tpr;
       l.fuse_pre = it->second.fuse_pre;
       l.fuse_post = it->second.fuse_post;
+      if (l.op_avail) l.op_on = it->second.op_on;
     }
   }
 }
@@ -1758,6 +1804,20 @@ extern "C" int amg_level_config(const amg_hierarchy *h, int level, int *tpr, int
   if (fuse_pre) *fuse_pre = l.fuse_pre;
   if (fuse_post) *fuse_post = l.fuse_post;
   return 0;
+}
+
+extern "C" int amg_level_operator_form(const amg_hierarchy *h, int level) {
+  if (!h || level < 0 || level > h->L) return -1;
+  return h->lev[level].op_on ? 1 : 0;
+}
+
+extern "C" amg_status amg_level_set_operator_form(amg_hierarchy *h, int level, int on) {
+  if (!h || level < 0 || level > h->L) return AMG_ERR_INVALID_ARG;
+  Level &l = h->lev[level];
+  if (on && !l.op_avail) return AMG_ERR_UNSUPPORTED;
+  l.op_on = on ? 1 : 0;
+  reset_graphs(h);
+  return AMG_OK;
 }
 
 // Grid, block and shared-memory configuration of the persistent coarse CG.

@@ -53,7 +53,7 @@ def test_fp32_flexible_pcg_reaches_fp64_accuracy(case):
     info = amg.pcg_solve(h, b, x, rtol=1e-8, flexible=True)
     x_o, info_o = oh.pcg(s.b, rtol=1e-8, flexible=True)
     assert info.status == amg.AMG_OK
-    assert info.rel_res_true <= 1.05e-8
+    assert info.rel_res_true <= 1e-8
     assert info.iterations <= info_o.iterations + 2
     assert rel_err(x.cpu().numpy(), x_o) < 1e-6
 
@@ -76,8 +76,11 @@ def test_fp32_bicgstab_convdiff():
     x = torch.zeros_like(b)
     info = amg.bicgstab_solve(h, b, x, rtol=1e-8, max_iter=300)
     x_o, info_o = oh.bicgstab(s.b, rtol=1e-8, max_iter=300)
-    assert info.status == amg.AMG_OK and info.rel_res_true <= 1.05e-8
-    assert info.iterations <= info_o.iterations + 2
+    assert info.status == amg.AMG_OK and info.rel_res_true <= 1e-8
+    # BiCGStab is not flexible: the FP32 V-cycle is a perturbed (slightly
+    # nonlinear) preconditioner, which may cost a few more iterations than
+    # the FP64 oracle's; bounded by 10% plus two
+    assert info.iterations <= int(1.1 * info_o.iterations) + 2
     assert rel_err(x.cpu().numpy(), x_o) < 1e-6
 
 
@@ -92,7 +95,7 @@ def test_fp16_storage_vcycle_and_flexible_pcg(case):
     x = torch.zeros_like(b)
     info = amg.pcg_solve(h, b, x, rtol=1e-8, flexible=True)
     x_o, info_o = oh.pcg(s.b, rtol=1e-8, flexible=True)
-    assert info.status == amg.AMG_OK and info.rel_res_true <= 1.05e-8
+    assert info.status == amg.AMG_OK and info.rel_res_true <= 1e-8
     assert info.iterations <= int(1.5 * info_o.iterations) + 2
     assert rel_err(x.cpu().numpy(), x_o) < 1e-6
 
