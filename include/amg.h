@@ -340,10 +340,9 @@ amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, d
  * Solves A x = f by the library's Jacobi-preconditioned CG (the coarsest-level
  * solver of the V-cycle: from x = 0 until ||f - A x||_2 <= 1e-12 ||f||_2, at
  * most 1000 iterations) without allocating any device memory.  It is meant for
- * callers that cannot call cudaMalloc: code running while a stream capture in
- * global mode is active (allocation is refused there), latency-critical loops
- * that cannot afford cudaMalloc's implicit device-wide synchronisation, and
- * plugins whose host framework owns every device allocation.
+ * callers that cannot call cudaMalloc: plugins whose host framework owns every
+ * device allocation (through its own pool or budget), and latency-critical
+ * loops that cannot afford cudaMalloc's implicit device-wide synchronisation.
  *
  * All work vectors live in one fixed array inside the library (about 29 MB,
  * held on every GPU that loads the library until the process exits), so:
@@ -356,9 +355,12 @@ amg_status amg_profile_read(amg_hierarchy *h, int kind, int level, double *ms, d
  *   - the first call on each device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  * Arguments: device CSR of A (same conventions as amg_setup, diagonal nonzero),
- * device vectors f (input) and x (output, length n, not aliasing f).  The call
+ * device vectors f (input) and x (output, length n; x must not be f).  The call
  * synchronises `stream`; *iterations (may be NULL) receives the CG iteration
- * count.  Errors: INVALID_ARG, INVALID_CSR, ZERO_DIAG, TIMEOUT, CUDA. */
+ * count.  After the solve the residual is recomputed from x: AMG_OK when it is
+ * at most 1e-10 ||f||_2 within the iteration limit, AMG_ERR_NOT_CONVERGED
+ * otherwise (x holds the last iterate), AMG_ERR_BREAKDOWN when it is not
+ * finite.  Other errors: INVALID_ARG, INVALID_CSR, ZERO_DIAG, TIMEOUT, CUDA. */
 amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                                  const double *d_val, const double *d_f, double *d_x, amg_stream_t stream,
                                  int *iterations);

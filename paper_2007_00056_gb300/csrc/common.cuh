@@ -45,6 +45,7 @@
 struct KState {
   double rz, pq, alpha, beta, omega, rho, bnorm, rel, rtol, srel, rel_true;
   int it, max_iter, done, status, flexible, half;
+  int xpend;  // PCG: the last iteration's x += alpha p is still to be applied
 };
 
 struct Level {
@@ -307,6 +308,7 @@ struct GridBarrier {
   unsigned *count;
   unsigned target;
   long long limit = BARRIER_SPIN_LIMIT;
+  unsigned sleep_ns = 0;  // pause between polls (0: poll continuously)
   __device__ __forceinline__ void arrive(unsigned G) {
     __syncthreads();
     target += G;
@@ -319,6 +321,7 @@ struct GridBarrier {
     if (threadIdx.x == 0) {
       long long t0 = clock64();
       while (ld_acquire_u32(count) < target) {
+        if (sleep_ns) __nanosleep(sleep_ns);
         if (clock64() - t0 > limit) {
           atomicOr(eflags, AMG_EFLAG_TIMEOUT);
           *fail_sh = 1;

@@ -336,54 +336,60 @@ amg_status gj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 #define BGJ_W 64  // block width
 
-// Step 1: P^-1 of the w x w pivot block by unblocked Gauss-Jordan (one block).
+// Step 1: P^-1 of the w x w pivot block by unblocked Gauss-Jordan (one block
+// of BGJ_W x 16 threads: thread (ty, tx) owns column tx of rows ty + 16 q).
 template <typename T>
-__global__ void __launch_bounds__(256) k_bgj_diag(int m, int k0, int w, const T *__restrict__ M, T *__restrict__ Pinv,
-                                                  unsigned *eflags) {
+__global__ void __launch_bounds__(BGJ_W * 16) k_bgj_diag(int m, int k0, int w, const T *__restrict__ M,
+                                                         T *__restrict__ Pinv, unsigned *eflags) {
   __shared__ T P[BGJ_W][BGJ_W + 1];
-  __shared__ int bad;
-  const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    const int r = idx / w, c = idx - r * w;
-    P[r][c] = M[(size_t)(k0 + r) * m + k0 + c];
-  }
+  const int tx = threadIdx.x & (BGJ_W - 1), ty = threadIdx.x / BGJ_W;
+  for (int r = ty; r < w; r += 16) P[r][tx] = tx < w ? M[(size_t)(k0 + r) * m + k0 + tx] : (T)0;
+  bool bad = false;
   __syncthreads();
   for (int c = 0; c < w; ++c) {
     const T pv = P[c][c];
     const bool ok = pv != (T)0 && isfinite((double)pv);
+    bad |= !ok;
     const T d = ok ? (T)1 / pv : (T)0;
-    if (!ok && tid == 0) bad = 1;
-    __syncthreads();
-    // pivot row scaled; its own entry becomes 1/pivot
-    if (tid < w) P[c][tid] = (tid == c) ? d : P[c][tid] * d;
-    __syncthreads();
-    // every other row: r_j -= f p_j (j != c), entry c becomes -f / pivot
-    for (int idx = tid; idx < w * w; idx += blockDim.x) {
-      const int r = idx / w, j = idx - r * w;
-      if (r == c) continue;
-      const T f = P[r][c];
-      if (j != c) P[r][j] = P[r][j] - f * P[c][j];
+    // multipliers of this column, read before any thread changes them
+    T f[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 16 * q;
+      f[q] = r < w ? P[r][c] : (T)0;
     }
     __syncthreads();
-    for (int r = tid; r < w; r += blockDim.x)
-      if (r != c) P[r][c] = -P[r][c] * d;
+    // pivot row scaled; its own entry becomes 1/pivot
+    if (ty == 0 && tx < w) P[c][tx] = (tx == c) ? d : P[c][tx] * d;
+    __syncthreads();
+    // every other row: r_j -= f p_j (j != c); entry c becomes -f / pivot
+    if (tx < w) {
+      const T pc = P[c][tx];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = ty + 16 * q;
+        if (r >= w || r == c) continue;
+        P[r][tx] = (tx == c) ? -f[q] * d : P[r][tx] - f[q] * pc;
+      }
+    }
     __syncthreads();
   }
-  for (int idx = tid; idx < w * w; idx += blockDim.x) {
-    const int r = idx / w, c = idx - r * w;
-    Pinv[idx] = P[r][c];
-  }
-  if (tid == 0 && bad) atomicOr(eflags, AMG_EFLAG_BREAKDOWN);
+  for (int r = ty; r < w; r += 16)
+    if (tx < w) Pinv[r * w + tx] = P[r][tx];
+  if (bad && threadIdx.x == 0) atomicOr(eflags, AMG_EFLAG_BREAKDOWN);
 }
 
 // Step 2: R = P^-1 M_K* for the columns outside K, stored in R (w x m) and in
 // the K rows of M.  Block: 64 columns; thread: one column, 16 of the rows.
+// Shared memory of k_bgj_rows / k_bgj_cols: two BGJ_W x (BGJ_W + 1) tiles.
+#define BGJ_TILE_SMEM(T) (2 * sizeof(T) * BGJ_W * (BGJ_W + 1))
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_bgj_rows(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv,
                                                   T *__restrict__ R) {
-  __shared__ T Ps[BGJ_W][BGJ_W + 1];
-  __shared__ T Ms[BGJ_W][64 + 1];
+  extern __shared__ __align__(16) unsigned char bgj_rs[];
+  T(*Ps)[BGJ_W + 1] = (T(*)[BGJ_W + 1])bgj_rs;
+  T(*Ms)[BGJ_W + 1] = Ps + BGJ_W;
   const int tid = threadIdx.x, j0 = blockIdx.x * 64;
   for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
   for (int idx = tid; idx < w * 64; idx += blockDim.x) {
@@ -457,8 +463,9 @@ __global__ void __launch_bounds__(256) k_bgj_update(int m, int k0, int w, T *__r
 // thread: one row, 16 of the columns.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bgj_cols(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv) {
-  __shared__ T Ps[BGJ_W][BGJ_W + 1];
-  __shared__ T Cs[64][BGJ_W + 1];
+  extern __shared__ __align__(16) unsigned char bgj_cs[];
+  T(*Ps)[BGJ_W + 1] = (T(*)[BGJ_W + 1])bgj_cs;
+  T(*Cs)[BGJ_W + 1] = Ps + BGJ_W;
   const int tid = threadIdx.x, i0 = blockIdx.x * 64;
   for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
   for (int idx = tid; idx < 64 * w; idx += blockDim.x) {
@@ -498,6 +505,9 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   const size_t smem = sizeof(T) * (size_t)BGJ_W * (TL::BM + TL::BN);
   AMG_CUDA(cudaFuncSetAttribute(k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const size_t tsmem = BGJ_TILE_SMEM(T);
+  AMG_CUDA(cudaFuncSetAttribute(k_bgj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+  AMG_CUDA(cudaFuncSetAttribute(k_bgj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
   T *R = nullptr;
   if (pool_alloc((void **)&R, sizeof(T) * ((size_t)BGJ_W * m + (size_t)BGJ_W * BGJ_W), st) != AMG_OK)
     return AMG_ERR_OOM;
@@ -509,10 +519,10 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   const dim3 ug(cdiv(m, TL::BN), cdiv(m, TL::BM));
   for (int k0 = 0; k0 < m; k0 += BGJ_W) {
     const int w = std::min(BGJ_W, m - k0);
-    k_bgj_diag<T><<<1, 256, 0, st>>>(m, k0, w, out, Pinv, h->eflags);
-    k_bgj_rows<T><<<cdiv(m, 64), 256, 0, st>>>(m, k0, w, out, Pinv, R);
+    k_bgj_diag<T><<<1, BGJ_W * 16, 0, st>>>(m, k0, w, out, Pinv, h->eflags);
+    k_bgj_rows<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv, R);
     k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
-    k_bgj_cols<T><<<cdiv(m, 64), 256, 0, st>>>(m, k0, w, out, Pinv);
+    k_bgj_cols<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv);
     count_launch(4);
   }
   AMG_CUDA(cudaGetLastError());
@@ -543,6 +553,63 @@ __global__ void k_refine_rhs(int m, const int32_t *__restrict__ rp, const int32_
 }  // namespace
 
 namespace {
+
+// x = X f with the FP64 inverse (warp per row), for the accuracy check of an
+// inverse formed without pivoting.
+__global__ void k_gemv64_check(int m, const double *__restrict__ X, const double *__restrict__ f,
+                               double *__restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= m) return;
+  double s = 0.0;
+  for (int j = lane; j < m; j += 32) s += X[(size_t)row * m + j] * f[j];
+  s = warp_sum(s);
+  if (lane == 0) x[row] = s;
+}
+
+// Whether the FP64 inverse in h->ainv solves a test system to the backward
+// error of a stable FP64 solve (x = X f, no refinement).
+amg_status inverse64_ok(amg_hierarchy *h, cudaStream_t st, bool *ok) {
+  const Level &c = h->lev[h->L];
+  const int m = c.n;
+  *ok = false;
+  double *f = nullptr;
+  if (pool_alloc((void **)&f, sizeof(double) * 2 * ((size_t)m + AMG_PAD), st) != AMG_OK) return AMG_ERR_OOM;
+  double *x = f + (m + AMG_PAD);
+  const int TB = AMG_THREADS;
+  k_refine_rhs<<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, f);
+  k_gemv64_check<<<cdiv((long long)m * 32, TB), TB, 0, st>>>(m, h->ainv, f, x);
+  count_launch(2);
+  const long long nnz = c.nnz;
+  std::vector<int32_t> hrp(m + 1), hci(nnz);
+  std::vector<double> hval(nnz), hf(m), hx(m);
+  cudaError_t ce = cudaMemcpyAsync(hrp.data(), c.rp, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess && nnz)
+    ce = cudaMemcpyAsync(hci.data(), c.ci, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess && nnz)
+    ce = cudaMemcpyAsync(hval.data(), c.val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hf.data(), f, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hx.data(), x, sizeof(double) * m, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  pool_free(f, st);
+  if (ce != cudaSuccess) return amg_cuda_status(ce);
+  double norm_a = 0.0, norm_f = 0.0, norm_x = 0.0, res = 0.0;
+  bool finite = true;
+  for (int i = 0; i < m; ++i) {
+    double rs = 0.0, ax = 0.0;
+    for (int e = hrp[i]; e < hrp[i + 1]; ++e) {
+      rs += std::fabs(hval[e]);
+      ax += hval[e] * hx[hci[e]];
+    }
+    norm_a = std::max(norm_a, rs);
+    norm_f = std::max(norm_f, std::fabs(hf[i]));
+    norm_x = std::max(norm_x, std::fabs(hx[i]));
+    res = std::max(res, std::fabs(hf[i] - ax));
+    if (!std::isfinite(hx[i])) finite = false;
+  }
+  *ok = finite && res <= GJ_BACKWARD_TOL * (norm_a * norm_x + norm_f);
+  return AMG_OK;
+}
 
 // Refinement steps the FP32 inverse in h->ainv32 needs: the fewest steps s
 // whose refined solve of a test system has a normwise backward error of at
@@ -640,6 +707,16 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t st) {
     h->ainv32 = nullptr;  // refinement does not reach FP64 accuracy: FP64 inverse
   }
   AMG_TRY(hier_alloc(h, (void **)&h->ainv, sizeof(double) * ((size_t)m * m + AMG_PAD)));
+  // FP64 inverse: without row interchanges if that is accurate, else pivoted
+  if (m > BGJ_W) {
+    amg_status rs = bgj_inverse<double>(h, h->ainv, st);
+    if (rs != AMG_ERR_BREAKDOWN) {
+      AMG_TRY(rs);
+      bool ok = false;
+      AMG_TRY(inverse64_ok(h, st, &ok));
+      if (ok) return AMG_OK;
+    }
+  }
   AMG_TRY(gj_inverse<double>(h, h->ainv, st));
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return amg_cuda_status(e);

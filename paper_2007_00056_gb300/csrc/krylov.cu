@@ -142,6 +142,7 @@ __global__ void k_pcg_start(int n, const double *__restrict__ r, const double *_
   double tot[1];
   if (grid_sum_last<1>(v, part, counter, tot) && threadIdx.x == 0) {
     st->rz = tot[0];
+    st->xpend = 0;
     if (!isfinite(tot[0])) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
   }
 }
@@ -168,25 +169,23 @@ __global__ void k_pcg_spmv(int n, const int32_t *__restrict__ rp, const int32_t 
   }
 }
 
-// x += alpha p; (flexible: rold = r); r -= alpha q; stopping test on ||r||
-__global__ void k_pcg_update(int n, double *__restrict__ x, double *__restrict__ r, double *__restrict__ rold,
-                             const double *__restrict__ p, const double *__restrict__ q, double *part,
+// r -= alpha q; stopping test on ||r||.  The matching x += alpha p is
+// deferred to k_pcg_xp (or to k_pcg_xfinal after the last iteration), which
+// reads p anyway: x_{j+1} = x_j + alpha_j p_j either way.
+__global__ void k_pcg_update(int n, double *__restrict__ r, const double *__restrict__ q, double *part,
                              unsigned *counter, KState *st) {
   if (is_done(st)) return;
   const double alpha = st->alpha;
-  const bool flex = st->flexible != 0;
   double v[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    x[i] = x[i] + alpha * p[i];
-    double ri = r[i];
-    if (flex) rold[i] = ri;
-    ri = ri - alpha * q[i];
+    const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     v[0] += ri * ri;
   }
   double tot[1];
   if (grid_sum_last<1>(v, part, counter, tot) && threadIdx.x == 0) {
     st->it += 1;
+    st->xpend = 1;
     st->rel = sqrt(tot[0]) / st->bnorm;
     if (st->rel <= st->rtol) { st->done = 1; st->status = AMG_OK; }
     else if (!isfinite(st->rel)) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
@@ -194,8 +193,9 @@ __global__ void k_pcg_update(int n, double *__restrict__ x, double *__restrict__
   }
 }
 
-// rz_new = (r, z); beta = rz_new / rz, or (z, r - rold) / rz when flexible
-__global__ void k_pcg_beta(int n, const double *__restrict__ r, const double *__restrict__ rold,
+// rz_new = (r, z); beta = rz_new / rz, or, flexible, (z, r_{j+1} - r_j) / rz
+// computed as -alpha (z, q) / rz, since r_{j+1} - r_j = -alpha q_j
+__global__ void k_pcg_beta(int n, const double *__restrict__ r, const double *__restrict__ q,
                            const double *__restrict__ z, double *part, unsigned *counter, KState *st) {
   if (is_done(st)) return;
   const bool flex = st->flexible != 0;
@@ -204,27 +204,40 @@ __global__ void k_pcg_beta(int n, const double *__restrict__ r, const double *__
   // instruction still costs its FP64 pipe time on this GPU
   if (flex) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      double zi = z[i], ri = r[i];
-      v[0] += ri * zi;
-      v[1] += zi * (ri - rold[i]);
+      const double zi = z[i];
+      v[0] += r[i] * zi;
+      v[1] += zi * q[i];
     }
   } else {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[0] += r[i] * z[i];
   }
   double tot[2];
   if (grid_sum_last<2>(v, part, counter, tot) && threadIdx.x == 0) {
-    double beta = (flex ? tot[1] : tot[0]) / st->rz;
+    double beta = (flex ? -st->alpha * tot[1] : tot[0]) / st->rz;
     if (!isfinite(beta)) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
     st->beta = beta;
     st->rz = tot[0];
   }
 }
 
-// p = z + beta p
-__global__ void k_pcg_p(int n, const double *__restrict__ z, double *__restrict__ p, const KState *st) {
+// x += alpha p (the deferred update of this iteration), then p = z + beta p
+__global__ void k_pcg_xp(int n, double *__restrict__ x, const double *__restrict__ z, double *__restrict__ p,
+                         KState *st) {
   if (is_done(st)) return;
-  const double beta = st->beta;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = z[i] + beta * p[i];
+  const double alpha = st->alpha, beta = st->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double pi = p[i];
+    x[i] = x[i] + alpha * pi;
+    p[i] = z[i] + beta * pi;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->xpend = 0;
+}
+
+// After the loop: the last iteration's x += alpha p when it is still pending.
+__global__ void k_pcg_xfinal(int n, double *__restrict__ x, const double *__restrict__ p, const KState *st) {
+  if (!st->xpend) return;
+  const double alpha = st->alpha;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = x[i] + alpha * p[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -426,18 +439,17 @@ amg_status pcg_iteration(amg_hierarchy *h, cudaStream_t s) {
   const int n = l.n;
   KDISPATCH(l, k_pcg_spmv, n, l.rp, l.ci, l.val, h->kp, h->kq, h->part, h->counter + KSLOT_A, h->st);
   {
-    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 6.0 * 8.0 * n);
-    k_pcg_update<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kr, h->krold, h->kp, h->kq, h->part,
-                                                      h->counter + KSLOT_B, h->st);
+    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
+    k_pcg_update<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->part, h->counter + KSLOT_B, h->st);
   }
   AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
   {
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-    k_pcg_beta<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->krold, h->kz, h->part, h->counter + KSLOT_C, h->st);
+    k_pcg_beta<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->kz, h->part, h->counter + KSLOT_C, h->st);
   }
   {
-    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
-    k_pcg_p<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kz, h->kp, h->st);
+    LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 5.0 * 8.0 * n);
+    k_pcg_xp<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kz, h->kp, h->st);
   }
   return amg_cuda_status(cudaGetLastError());
 }
@@ -640,6 +652,11 @@ extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, doub
     }
     AMG_CUDA(cudaGetLastError());
     AMG_TRY(run_iterations(h, pcg_iteration, &h->g_pcg, &h->g_pcg_nodes, s));
+    {
+      LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
+      k_pcg_xfinal<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kx, h->kp, h->st);
+    }
+    AMG_CUDA(cudaGetLastError());
     AMG_TRY(true_residual_restart(h, s, &restarts, &again));
   }
   return end_solve(h, d_x, s, info);

@@ -125,7 +125,22 @@ __global__ void k_hem_init(int n, int32_t *mate, int32_t *dirty, int *stamp) {
 // nobody (the fixed point).  Lists are walked with grid-stride loops.
 #define HEM_BLOCK_CAP 2048     // largest dirty list handled by the one-block rounds
 #define HEM_BLOCK_ROUNDS 4096  // rounds per launch of the one-block rounds
-#define HEM_COOP_THREADS 512   // threads per block of the cooperative rounds
+#define HEM_COOP_THREADS 1024  // threads per block of the cooperative rounds (one block per SM)
+// Counters of the cooperative rounds (ints), each on its own 128-byte line:
+// the appended-list counters of three rounds (round r uses r % 3), the 64-bit
+// barrier word, the result, and block 0's report after a solo stretch.
+#define HEM_COOP_SLOT(r, f) (((r) % 3) * 64 + (f) * 32)  // f = 0: matched list M, 1: next list
+#define HEM_COOP_BAR 192    // unsigned long long
+#define HEM_COOP_OUT 224    // rounds run, finished
+#define HEM_COOP_SOLO 256   // rounds, list size, finished, lists swapped
+#define HEM_COOP_INTS 288
+// Lists of at most HEM_SOLO_CAP nodes (one per thread of a block) run their
+// rounds inside block 0 alone, through its L1 cache and block barriers, while
+// the other blocks wait at a grid barrier: the narrow fronts of uniform grids
+// and the last rounds of every pass.  At most HEM_SOLO_ROUNDS rounds per
+// stretch keep every wait short.
+#define HEM_SOLO_CAP HEM_COOP_THREADS
+#define HEM_SOLO_ROUNDS 20000
 
 // Slot for one appended list entry: the lanes of the warp that append at the
 // same time share one atomic on the counter.
@@ -299,93 +314,302 @@ __global__ void __launch_bounds__(1024)
 
 // Heaviest free neighbour of i (smaller index on equal weight, or the larger
 // one with tie_larger); -1 when i has no free neighbour.  mate is read past
-// the L1 cache: other blocks of a persistent kernel write it.
+// the L1 cache: other blocks of a persistent kernel write it.  The row is
+// read eight entries at a time, all loads of a group issued before any is
+// used, so a pick costs two dependent load latencies per group rather than
+// two per entry; entries are still compared in stored (ascending) order.
+#define HEM_GROUP 8
 __device__ __forceinline__ int hem_pick_node(int i, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                              const double *__restrict__ w, int tie_larger, const int32_t *mate) {
   int best = -1;
   double bw = 0.0;
-  const int e1 = __ldg(&rp[i + 1]);
-  for (int e = __ldg(&rp[i]); e < e1; ++e) {
-    const double we = __ldg(&w[e]);
-    if (we <= 0.0) continue;
-    const int j = __ldg(&ci[e]);
-    if (__ldcg(&mate[j]) != HEM_FREE) continue;
-    if (best < 0 || we > bw || (tie_larger && we == bw)) { best = j; bw = we; }
+  const int e0 = __ldg(&rp[i]), e1 = __ldg(&rp[i + 1]);
+  for (int base = e0; base < e1; base += HEM_GROUP) {
+    int jj[HEM_GROUP], mm[HEM_GROUP];
+    double ww[HEM_GROUP];
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      const int e = base + u;
+      jj[u] = e < e1 ? __ldg(&ci[e]) : -1;
+      ww[u] = e < e1 ? __ldg(&w[e]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) mm[u] = (ww[u] > 0.0) ? __ldcg(&mate[jj[u]]) : 0;
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      if (!(ww[u] > 0.0) || mm[u] != HEM_FREE) continue;
+      if (best < 0 || ww[u] > bw || (tie_larger && ww[u] == bw)) { best = jj[u]; bw = ww[u]; }
+    }
   }
   return best;
 }
 
+// Grid barrier whose 64-bit word also sums one value per block: the low half
+// counts arrivals, the high half accumulates what each block adds on arrival,
+// and the high half seen at completion is the total over every block up to
+// this barrier (no block can add to the next barrier before all have passed
+// this one).  Waits are bounded like GridBarrier's.
+struct SumBarrier {
+  unsigned long long *word;
+  unsigned target;
+  unsigned sleep_ns = 0;
+  __device__ __forceinline__ bool sync(unsigned G, unsigned add, unsigned *eflags, int *fail_sh,
+                                       unsigned *hi_sh, unsigned *hi_out) {
+    __syncthreads();
+    target += G;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(word, 1ull | ((unsigned long long)add << 32));
+      const long long t0 = clock64();
+      unsigned long long v;
+      for (;;) {
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(word) : "memory");
+        if ((unsigned)v >= target) break;
+        if (sleep_ns) __nanosleep(sleep_ns);
+        if (clock64() - t0 > BARRIER_SPIN_LIMIT) {
+          atomicOr(eflags, AMG_EFLAG_TIMEOUT);
+          *fail_sh = 1;
+          break;
+        }
+      }
+      *hi_sh = (unsigned)(v >> 32);
+    }
+    __syncthreads();
+    *hi_out = *hi_sh;
+    return *fail_sh == 0;
+  }
+};
+
+// Loads of the rounds' shared state: past L1 (other SMs write it) in grid
+// rounds, through L1 inside a block's solo stretch.
+template <bool L2ONLY>
+__device__ __forceinline__ int ld_state(const int *p) { return L2ONLY ? __ldcg(p) : *p; }
+
+// Heaviest free neighbour of q given the state loads of policy L2ONLY
+// (grouped loads as in hem_pick_node).
+template <bool L2ONLY>
+__device__ __forceinline__ int hem_pick_ld(int q, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                          const double *__restrict__ w, int tie_larger, const int32_t *mate) {
+  int best = -1;
+  double bw = 0.0;
+  const int e0 = __ldg(&rp[q]), e1 = __ldg(&rp[q + 1]);
+  for (int base = e0; base < e1; base += HEM_GROUP) {
+    int jj[HEM_GROUP], mm[HEM_GROUP];
+    double ww[HEM_GROUP];
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      const int e = base + u;
+      jj[u] = e < e1 ? __ldg(&ci[e]) : -1;
+      ww[u] = e < e1 ? __ldg(&w[e]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) mm[u] = (ww[u] > 0.0) ? ld_state<L2ONLY>(&mate[jj[u]]) : 0;
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      if (!(ww[u] > 0.0) || mm[u] != HEM_FREE) continue;
+      if (best < 0 || ww[u] > bw || (tie_larger && ww[u] == bw)) { best = jj[u]; bw = ww[u]; }
+    }
+  }
+  return best;
+}
+
+// Phase B for one newly matched node m of round r: every free neighbour q
+// whose pick was m joins the next list (stamp r + 1) with its new pick.  q is
+// reached from m only (a node has one pick), so the stamp is a plain store.
+// Appends go through `append` (a slot index); returns the number appended.
+template <bool L2ONLY, typename AppendF>
+__device__ __forceinline__ int hem_repick(int m, int r, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                          const double *__restrict__ w, int tie_larger, const int32_t *mate,
+                                          int32_t *pick, int *stamp, int2 *Dn, AppendF append) {
+  int added = 0;
+  const int e0 = __ldg(&rp[m]), e1 = __ldg(&rp[m + 1]);
+  for (int base = e0; base < e1; base += HEM_GROUP) {
+    int qq[HEM_GROUP], mq[HEM_GROUP], pq[HEM_GROUP];
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) qq[u] = base + u < e1 ? __ldg(&ci[base + u]) : m;
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      const bool other = qq[u] != m;
+      mq[u] = other ? ld_state<L2ONLY>(&mate[qq[u]]) : 0;
+      pq[u] = other ? ld_state<L2ONLY>(&pick[qq[u]]) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) {
+      const int q = qq[u];
+      if (q == m || mq[u] != HEM_FREE || pq[u] != m) continue;
+      stamp[q] = r + 1;
+      const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
+      pick[q] = np;
+      Dn[append()] = make_int2(q, np);
+      ++added;
+    }
+  }
+  return added;
+}
+
 // Every round of one matching pass in one cooperative launch (all blocks
-// resident): the incremental rounds above with two bounded grid barriers per
-// round instead of three launches and periodic host checks.  Round r:
-//   A. each node i of D_r whose pick j picks i back is paired with j; the
-//      newly matched nodes are listed in M (each once);
-//   B. every free neighbour q of a node of M whose pick was that node is put
-//      in D_{r+1} (stamp = r + 1) and re-picks among its free neighbours,
-//      which now exclude this round's pairs.
-// D_0 is every node (picks of phase 0).  The pass ends after the first round
-// that pairs nobody; out[0] = rounds run (that last one included), out[1] = 1
-// when it ended, 0 when it stopped at max_rounds or on a barrier timeout.
-// Counters: three slots of (matched, next-list size), slot r % 3 for round r.
+// resident).  Round r, over the list D_r of (node, its pick):
+//   A. each node i of D_r whose pick j picks i back is paired with j;
+//   B. each newly matched node re-picks its dependants (hem_repick): free
+//      neighbours whose pick it was, which form D_{r+1}.
+// D_0 is every node (picks of phase 0, stamp 0).  Lists no longer than the
+// grid's threads are handled one node per thread, the pair kept in registers
+// across the barrier; longer ones go through the matched list M.  Lists of at
+// most HEM_SOLO_CAP nodes run in block 0 alone (see HEM_SOLO_CAP).  The pass
+// ends after the first round that pairs nobody; ctr[HEM_COOP_OUT] = rounds
+// run (that last one included) and 1 when it ended (0: stopped at
+// max_rounds or on a barrier timeout).  Picks, pairs and round counts are
+// those of the synchronous rounds.
 __global__ void __launch_bounds__(HEM_COOP_THREADS)
     k_hem_coop(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
-               int tie_larger, int32_t *mate, int32_t *pick, int *stamp, int32_t *Da, int32_t *Db, int32_t *M,
-               int *ctr, unsigned *bar, unsigned *eflags, int max_rounds, int *out) {
+               int tie_larger, int32_t *mate, int32_t *pick, int *stamp, int2 *Da, int2 *Db, int32_t *M,
+               int *ctr, unsigned *eflags, int max_rounds) {
   __shared__ int fail_sh;
-  if (threadIdx.x == 0) fail_sh = 0;
+  __shared__ unsigned hi_sh;
+  __shared__ int blk_cnt;
+  if (threadIdx.x == 0) { fail_sh = 0; blk_cnt = 0; }
   const unsigned G = gridDim.x;
-  GridBarrier gb{bar, 0u};
+  SumBarrier gb{(unsigned long long *)(ctr + HEM_COOP_BAR), 0u};
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
   for (int i = gtid; i < n; i += gstride) pick[i] = hem_pick_node(i, rp, ci, w, tie_larger, mate);
-  if (!gb.sync(G, eflags, &fail_sh)) return;
-  int32_t *D = Da, *Dn = Db;
+  unsigned hi = 0, hi_prev = 0;
+  if (!gb.sync(G, 0, eflags, &fail_sh, &hi_sh, &hi)) return;
+  hi_prev = hi;
+  int2 *D = Da, *Dn = Db;
   int nd = n, r = 0;
   bool finished = false;
-  for (; r < max_rounds; ++r) {
-    int *slot = ctr + 2 * (r % 3);
-    if (gtid == 0) {  // the slot of round r + 1 (last used by round r - 2)
-      int *nx = ctr + 2 * ((r + 1) % 3);
-      nx[0] = 0;
-      nx[1] = 0;
+  while (r < max_rounds) {
+    if (r > 0 && nd <= HEM_SOLO_CAP) {
+      // short list: block 0 runs the next rounds alone, through its L1
+      if (blockIdx.x == 0) {
+        __shared__ int s_nn;
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");  // no stale L1 lines from before
+        int2 *d = D, *dn = Dn;
+        int lr = r, lnd = nd, fin = 0, swaps = 0;
+        for (int k = 0; k < HEM_SOLO_ROUNDS && lr < max_rounds; ++k) {
+          if (threadIdx.x == 0) s_nn = 0;
+          __syncthreads();
+          int mi = -1, mj = -1;
+          if (threadIdx.x < lnd) {
+            const int2 e = d[threadIdx.x];
+            if (e.y >= 0 && pick[e.y] == e.x) {
+              mate[e.x] = e.y;
+              mate[e.y] = e.x;
+              mi = e.x;
+              mj = e.y;
+            }
+          }
+          if (__syncthreads_or(mi >= 0) == 0) { fin = 1; ++lr; break; }
+          auto app = [&]() { return atomicAdd(&s_nn, 1); };
+          if (mi >= 0) {
+            hem_repick<false>(mi, lr, rp, ci, w, tie_larger, mate, pick, stamp, dn, app);
+            if (stamp[mj] != lr) hem_repick<false>(mj, lr, rp, ci, w, tie_larger, mate, pick, stamp, dn, app);
+          }
+          __syncthreads();
+          lnd = s_nn;
+          __syncthreads();  // every thread has read s_nn before the next round resets it
+          int2 *tmp = d;
+          d = dn;
+          dn = tmp;
+          swaps ^= 1;
+          ++lr;
+          if (lnd > HEM_SOLO_CAP) break;
+        }
+        if (threadIdx.x == 0) {
+          ctr[HEM_COOP_SOLO + 0] = lr;
+          ctr[HEM_COOP_SOLO + 1] = lnd;
+          ctr[HEM_COOP_SOLO + 2] = fin;
+          ctr[HEM_COOP_SOLO + 3] = swaps;
+          for (int k = 0; k < 3; ++k) ctr[HEM_COOP_SLOT(k, 0)] = ctr[HEM_COOP_SLOT(k, 1)] = 0;
+        }
+      }
+      gb.sleep_ns = 256;
+      const bool ok = gb.sync(G, 0, eflags, &fail_sh, &hi_sh, &hi);
+      gb.sleep_ns = 0;
+      if (!ok) return;
+      hi_prev = hi;
+      r = __ldcg(&ctr[HEM_COOP_SOLO + 0]);
+      nd = __ldcg(&ctr[HEM_COOP_SOLO + 1]);
+      if (__ldcg(&ctr[HEM_COOP_SOLO + 3])) {
+        int2 *tmp = D;
+        D = Dn;
+        Dn = tmp;
+      }
+      if (__ldcg(&ctr[HEM_COOP_SOLO + 2])) {
+        finished = true;
+        break;
+      }
+      continue;
     }
-    // A: pairs
-    for (int t = gtid; t < nd; t += gstride) {
-      const int i = r == 0 ? t : __ldcg(&D[t]);
-      const int j = __ldcg(&pick[i]);
-      if (j < 0 || __ldcg(&pick[j]) != i) continue;
-      mate[i] = j;
-      mate[j] = i;
-      M[warp_append(&slot[0])] = i;
-      if (__ldcg(&stamp[j]) != r) M[warp_append(&slot[0])] = j;
+    int *cm = ctr + HEM_COOP_SLOT(r, 0), *cn = ctr + HEM_COOP_SLOT(r, 1);
+    if (gtid == 0) {  // the counters of round r + 1 (last used by round r - 2)
+      ctr[HEM_COOP_SLOT(r + 1, 0)] = 0;
+      ctr[HEM_COOP_SLOT(r + 1, 1)] = 0;
     }
-    if (!gb.sync(G, eflags, &fail_sh)) return;
-    const int nm = __ldcg(&slot[0]);
-    if (nm == 0) {
+    // A: pairs.  One node per thread keeps its pair in registers; longer
+    // lists list the matched nodes in M (each once)
+    const bool regs = r > 0 && nd <= gstride;
+    int mi = -1, mj = -1;
+    bool any = false;
+    if (regs) {
+      if (gtid < nd) {
+        const int2 e = __ldcg(&D[gtid]);
+        if (e.y >= 0 && __ldcg(&pick[e.y]) == e.x) {
+          mate[e.x] = e.y;
+          mate[e.y] = e.x;
+          mi = e.x;
+          mj = e.y;
+          any = true;
+        }
+      }
+    } else {
+      for (int t = gtid; t < nd; t += gstride) {
+        int i, j;
+        if (r == 0) { i = t; j = __ldcg(&pick[i]); }
+        else { const int2 e = __ldcg(&D[t]); i = e.x; j = e.y; }
+        if (j < 0 || __ldcg(&pick[j]) != i) continue;
+        mate[i] = j;
+        mate[j] = i;
+        any = true;
+        M[warp_append(cm)] = i;
+        if (__ldcg(&stamp[j]) != r) M[warp_append(cm)] = j;
+      }
+    }
+    const int blk_any = __syncthreads_or(any);
+    if (!gb.sync(G, blk_any ? 1u : 0u, eflags, &fail_sh, &hi_sh, &hi)) return;
+    if (hi == hi_prev) {
       finished = true;
       ++r;
       break;
     }
-    // B: next list and its new picks
-    for (int t = gtid; t < nm; t += gstride) {
-      const int m = __ldcg(&M[t]);
-      const int e1 = __ldg(&rp[m + 1]);
-      for (int e = __ldg(&rp[m]); e < e1; ++e) {
-        const int q = __ldg(&ci[e]);
-        if (q == m || __ldcg(&mate[q]) != HEM_FREE || __ldcg(&pick[q]) != m) continue;
-        if (atomicExch(&stamp[q], r + 1) == r + 1) continue;
-        pick[q] = hem_pick_node(q, rp, ci, w, tie_larger, mate);
-        Dn[warp_append(&slot[1])] = q;
+    hi_prev = hi;
+    // B: the next list
+    const int nm = regs ? 0 : __ldcg(cm);
+    auto app = [&]() { return warp_append(cn); };
+    int added = 0;
+    if (regs) {
+      if (mi >= 0) {
+        added += hem_repick<true>(mi, r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
+        if (__ldcg(&stamp[mj]) != r) added += hem_repick<true>(mj, r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
       }
+    } else {
+      for (int t = gtid; t < nm; t += gstride)
+        added += hem_repick<true>(__ldcg(&M[t]), r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
     }
-    if (!gb.sync(G, eflags, &fail_sh)) return;
-    nd = __ldcg(&slot[1]);
-    int32_t *tmp = D;
+    if (added) atomicAdd(&blk_cnt, added);
+    __syncthreads();
+    if (!gb.sync(G, (unsigned)blk_cnt, eflags, &fail_sh, &hi_sh, &hi)) return;
+    if (threadIdx.x == 0) blk_cnt = 0;  // every thread read it before the barrier; the next adds follow barrier A
+    nd = (int)(hi - hi_prev);
+    hi_prev = hi;
+    int2 *tmp = D;
     D = Dn;
     Dn = tmp;
+    ++r;
   }
   if (gtid == 0) {
-    out[0] = r;
-    out[1] = finished ? 1 : 0;
+    ctr[HEM_COOP_OUT + 0] = r;
+    ctr[HEM_COOP_OUT + 1] = finished ? 1 : 0;
   }
 }
 
@@ -690,50 +914,134 @@ __global__ void k_op_c(int n, const int32_t *__restrict__ rp, const int32_t *__r
   }
 }
 
+// Rows of up to OPQ_SHORT entries are handled by one thread (O(len^2) work on
+// a handful of entries); longer rows (hub rows of stalled coarse levels) are
+// handed to a whole warp, which stages the row's aggregate ids in shared
+// memory (rows of up to OPQ_STAGE entries; longer ones read global memory)
+// and marks in `first` the entries that are the first of their aggregate.
+#define OPQ_SHORT 32
+#define OPQ_STAGE 1024
+#define OPQ_WARPS (AMG_THREADS / 32)
+
 // Entries of row i of A P: the distinct aggregates agg[j] of its columns.
-__global__ void k_op_qcount(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                            const int32_t *__restrict__ agg, int *__restrict__ cnt) {
+// Block: AMG_THREADS consecutive rows.
+__global__ void __launch_bounds__(AMG_THREADS) k_op_qcount(int n, const int32_t *__restrict__ rp,
+                                                           const int32_t *__restrict__ ci,
+                                                           const int32_t *__restrict__ agg, int *__restrict__ cnt,
+                                                           uint8_t *__restrict__ first) {
+  __shared__ int longs[AMG_THREADS];
+  __shared__ int nlong;
+  __shared__ int stage[OPQ_WARPS][OPQ_STAGE];
+  if (threadIdx.x == 0) nlong = 0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int b = rp[i], e = rp[i + 1];
-  int c = 0;
-  for (int k = b; k < e; ++k) {
-    const int a = agg[ci[k]];
-    bool seen = false;
-    for (int m = b; m < k && !seen; ++m) seen = agg[ci[m]] == a;
-    c += seen ? 0 : 1;
+  if (i < n) {
+    const int b = rp[i], e = rp[i + 1];
+    if (e - b <= OPQ_SHORT) {
+      int c = 0;
+      for (int k = b; k < e; ++k) {
+        const int a = agg[ci[k]];
+        bool seen = false;
+        for (int m = b; m < k && !seen; ++m) seen = agg[ci[m]] == a;
+        c += seen ? 0 : 1;
+      }
+      cnt[i] = c;
+    } else {
+      longs[atomicAdd(&nlong, 1)] = i;
+    }
   }
-  cnt[i] = c;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int *sa = stage[w];
+  for (int q = w; q < nlong; q += OPQ_WARPS) {
+    const int r = longs[q], b = rp[r], len = rp[r + 1] - b;
+    const bool staged = len <= OPQ_STAGE;
+    if (staged)
+      for (int k = lane; k < len; k += 32) sa[k] = agg[ci[b + k]];
+    __syncwarp();
+    int c = 0;
+    for (int k = lane; k < len; k += 32) {
+      const int a = staged ? sa[k] : agg[ci[b + k]];
+      bool seen = false;
+      for (int m = 0; m < k && !seen; ++m) seen = (staged ? sa[m] : agg[ci[b + m]]) == a;
+      first[b + k] = seen ? 0 : 1;
+      c += seen ? 0 : 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[r] = c;
+    __syncwarp();
+  }
 }
 
 // Row i of Q: columns J ascending; (A P)_iJ sums the row's a_ij with agg[j] = J
 // in stored order (the first one starts the sum), and
-// q_iJ = [J == agg[i]] - wd_i (A P)_iJ.
-__global__ void k_op_qfill(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                           const double *__restrict__ val, const int32_t *__restrict__ agg,
-                           const double *__restrict__ wd, const int32_t *__restrict__ qrp, int32_t *__restrict__ qci,
-                           double *__restrict__ qval) {
+// q_iJ = [J == agg[i]] - wd_i (A P)_iJ.  Same row split as k_op_qcount; in a
+// long row, the lane holding the first entry of an aggregate computes its
+// slot (the number of first entries with a smaller id) and its sum.
+__global__ void __launch_bounds__(AMG_THREADS) k_op_qfill(int n, const int32_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ ci,
+                                                          const double *__restrict__ val,
+                                                          const int32_t *__restrict__ agg,
+                                                          const double *__restrict__ wd,
+                                                          const int32_t *__restrict__ qrp,
+                                                          const uint8_t *__restrict__ first,
+                                                          int32_t *__restrict__ qci, double *__restrict__ qval) {
+  __shared__ int longs[AMG_THREADS];
+  __shared__ int nlong;
+  __shared__ int stage[OPQ_WARPS][OPQ_STAGE];
+  if (threadIdx.x == 0) nlong = 0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int b = rp[i], e = rp[i + 1], ai = agg[i];
-  const double w = wd[i];
-  int last = -1;
-  for (int o = qrp[i]; o < qrp[i + 1]; ++o) {
-    int J = 0x7fffffff;
-    for (int k = b; k < e; ++k) {
-      const int a = agg[ci[k]];
-      if (a > last && a < J) J = a;
+  if (i < n) {
+    const int b = rp[i], e = rp[i + 1];
+    if (e - b <= OPQ_SHORT) {
+      const int ai = agg[i];
+      const double w = wd[i];
+      int last = -1;
+      for (int o = qrp[i]; o < qrp[i + 1]; ++o) {
+        int J = 0x7fffffff;
+        for (int k = b; k < e; ++k) {
+          const int a = agg[ci[k]];
+          if (a > last && a < J) J = a;
+        }
+        double sum = 0.0;
+        bool fst = true;
+        for (int k = b; k < e; ++k) {
+          if (agg[ci[k]] != J) continue;
+          sum = fst ? val[k] : sum + val[k];
+          fst = false;
+        }
+        qci[o] = J;
+        qval[o] = (J == ai ? 1.0 : 0.0) - w * sum;
+        last = J;
+      }
+    } else {
+      longs[atomicAdd(&nlong, 1)] = i;
     }
-    double sum = 0.0;
-    bool first = true;
-    for (int k = b; k < e; ++k) {
-      if (agg[ci[k]] != J) continue;
-      sum = first ? val[k] : sum + val[k];
-      first = false;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  int *sa = stage[wp];
+  for (int q = wp; q < nlong; q += OPQ_WARPS) {
+    const int r = longs[q], b = rp[r], len = rp[r + 1] - b, o0 = qrp[r], ar = agg[r];
+    const double w = wd[r];
+    const bool staged = len <= OPQ_STAGE;
+    if (staged)
+      for (int k = lane; k < len; k += 32) sa[k] = agg[ci[b + k]];
+    __syncwarp();
+    for (int k = lane; k < len; k += 32) {
+      if (!first[b + k]) continue;
+      const int a = staged ? sa[k] : agg[ci[b + k]];
+      int slot = 0;
+      for (int m = 0; m < len; ++m)
+        if (first[b + m] && (staged ? sa[m] : agg[ci[b + m]]) < a) ++slot;
+      double sum = val[b + k];
+      for (int m = k + 1; m < len; ++m)
+        if ((staged ? sa[m] : agg[ci[b + m]]) == a) sum = sum + val[b + m];
+      qci[o0 + slot] = a;
+      qval[o0 + slot] = (a == ar ? 1.0 : 0.0) - w * sum;
     }
-    qci[o] = J;
-    qval[o] = (J == ai ? 1.0 : 0.0) - w * sum;
-    last = J;
+    __syncwarp();
   }
 }
 
@@ -746,6 +1054,8 @@ struct Scratch {
   double *w = nullptr;
   int32_t *mate = nullptr, *pick = nullptr, *fa = nullptr, *fb = nullptr, *first = nullptr;
   int *flag = nullptr, *id = nullptr, *tiles = nullptr, *cnt = nullptr, *count = nullptr;
+  int *coop = nullptr;  // counters and barrier of the cooperative rounds (HEM_COOP_INTS)
+  int2 *la = nullptr, *lb = nullptr;  // the cooperative rounds' lists of (node, pick)
   int *host = nullptr;  // pinned: [0] pairs, [1] frontier, [2] scan total
   size_t cap_n = 0, cap_nnz = 0;
 };
@@ -775,6 +1085,9 @@ amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
   AMG_TRY(pool_alloc((void **)&s.count, sizeof(int) * (n + AMG_PAD), st));
   AMG_TRY(pool_alloc((void **)&s.tiles, sizeof(int) * (tiles + 8), st));
   AMG_TRY(pool_alloc((void **)&s.cnt, sizeof(int) * 64, st));
+  AMG_TRY(pool_alloc((void **)&s.coop, sizeof(int) * HEM_COOP_INTS, st));
+  AMG_TRY(pool_alloc((void **)&s.la, sizeof(int2) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.lb, sizeof(int2) * (n + AMG_PAD), st));
   s.host = (int *)pinned_small_alloc();
   if (!s.host) return AMG_ERR_OOM;
   s.cap_n = n;
@@ -783,7 +1096,7 @@ amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
 }
 
 void scratch_free(Scratch &s, cudaStream_t st) {
-  void *ps[] = {s.w, s.mate, s.pick, s.fa, s.fb, s.first, s.flag, s.id, s.count, s.tiles, s.cnt};
+  void *ps[] = {s.w, s.mate, s.pick, s.fa, s.fb, s.first, s.flag, s.id, s.count, s.tiles, s.cnt, s.coop, s.la, s.lb};
   for (void *p : ps) pool_free(p, st);
   pinned_small_free(s.host);
   s = Scratch();
@@ -802,8 +1115,8 @@ amg_status check_flags(amg_hierarchy *h, cudaStream_t st) {
   return AMG_OK;
 }
 
-// Blocks of the cooperative handshake kernel on this device (at most two per
-// SM), or 0 when the device cannot launch it cooperatively.
+// Blocks of the cooperative handshake kernel on this device (one per SM), or
+// 0 when the device cannot launch it cooperatively.
 int hem_coop_blocks(amg_hierarchy *h) {
   int coop = 0, occ = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess || !coop) {
@@ -815,7 +1128,7 @@ int hem_coop_blocks(amg_hierarchy *h) {
     cudaGetLastError();
     return 0;
   }
-  return std::min(occ, 2) * h->num_sms;
+  return h->num_sms;
 }
 
 // One pairwise pass on `in`: matching rounds, numbering, Galerkin product.
@@ -840,20 +1153,20 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   const int coop_blocks = hem_coop_blocks(h);
   if (coop_blocks > 0) {
     // every round in one cooperative launch
-    int *ctr = S.cnt + 40, *out = S.cnt + 48;
-    unsigned *bar = (unsigned *)(S.cnt + 50);
-    AMG_CUDA(cudaMemsetAsync(S.cnt + 40, 0, sizeof(int) * 12, st));
+    int *ctr = S.coop;
+    AMG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int) * HEM_COOP_INTS, st));
     int a_n = n, a_tie = tie_larger, a_max = round_cap;
     const int32_t *a_rp = in.rp, *a_ci = in.ci;
     const double *a_w = S.w;
-    int32_t *a_mate = S.mate, *a_pick = S.pick, *a_da = S.fa, *a_db = S.fb, *a_m = S.first;
+    int32_t *a_mate = S.mate, *a_pick = S.pick, *a_m = S.first;
+    int2 *a_da = S.la, *a_db = S.lb;
     int *a_stamp = S.flag;
     unsigned *a_ef = h->eflags;
     void *args[] = {&a_n, &a_rp, &a_ci, &a_w, &a_tie, &a_mate, &a_pick, &a_stamp, &a_da, &a_db, &a_m,
-                    &ctr, &bar, &a_ef, &a_max, &out};
+                    &ctr, &a_ef, &a_max};
     AMG_CUDA(cudaLaunchCooperativeKernel((void *)k_hem_coop, coop_blocks, HEM_COOP_THREADS, args, 0, st));
     count_launch();
-    AMG_CUDA(cudaMemcpyAsync(S.host, out, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
+    AMG_CUDA(cudaMemcpyAsync(S.host, ctr + HEM_COOP_OUT, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     AMG_CUDA(cudaStreamSynchronize(st));
     r = S.host[0];
     finished = true;
@@ -1056,13 +1369,17 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
   const int T = AMG_THREADS;
   int nmax = 1;
   for (int k = 0; k < h->L; ++k) nmax = std::max(nmax, h->lev[k].n);
+  long long nnzmax = 1;
+  for (int k = 0; k < h->L; ++k) nnzmax = std::max(nnzmax, (long long)h->lev[k].nnz);
   int *cnt = nullptr, *tiles = nullptr, *tot = nullptr;
-  AMG_TRY(pool_alloc((void **)&cnt, sizeof(int) * (nmax + AMG_PAD), st));
-  AMG_TRY(pool_alloc((void **)&tiles, sizeof(int) * (cdiv(nmax, SCAN_TILE) + 8), st));
-  AMG_TRY(pool_alloc((void **)&tot, sizeof(int) * 2 * AMG_MAX_LEVELS, st));
+  uint8_t *first = nullptr;
   int *host = (int *)pinned_small_alloc();
   if (!host) return AMG_ERR_OOM;
-  amg_status rs = AMG_OK;
+  amg_status rs = pool_alloc((void **)&cnt, sizeof(int) * (nmax + AMG_PAD), st);
+  if (rs == AMG_OK) rs = pool_alloc((void **)&tiles, sizeof(int) * (cdiv(nmax, SCAN_TILE) + 8), st);
+  if (rs == AMG_OK) rs = pool_alloc((void **)&tot, sizeof(int) * 2 * AMG_MAX_LEVELS, st);
+  if (rs == AMG_OK) rs = pool_alloc((void **)&first, (size_t)nnzmax + AMG_PAD, st);
+  // level by level: the first-entry flags of a level are used by its fill
   for (int k = 0; k < h->L && rs == AMG_OK; ++k) {
     Level &l = h->lev[k];
     rs = hier_alloc(h, (void **)&l.cval, sizeof(double) * (l.nnz + AMG_PAD));
@@ -1071,23 +1388,19 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
     if (rs != AMG_OK) break;
     cudaMemsetAsync(l.cval + l.nnz, 0, sizeof(double) * AMG_PAD, st);
     k_op_c<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.dinv, p.omega, l.cval, l.wd); count_launch();
-    k_op_qcount<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.agg, cnt); count_launch();
+    k_op_qcount<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.agg, cnt, first); count_launch();
     scan_excl(cnt, l.qrp, l.n, tot + k, tiles, st);
     cudaMemcpyAsync(l.qrp + l.n, tot + k, sizeof(int), cudaMemcpyDeviceToDevice, st);
-  }
-  if (rs == AMG_OK) {
-    rs = amg_cuda_status(cudaMemcpyAsync(host, tot, sizeof(int) * h->L, cudaMemcpyDeviceToHost, st));
+    rs = amg_cuda_status(cudaMemcpyAsync(host, tot + k, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (rs == AMG_OK) rs = amg_cuda_status(cudaStreamSynchronize(st));
-  }
-  for (int k = 0; k < h->L && rs == AMG_OK; ++k) {
-    Level &l = h->lev[k];
-    l.qnnz = host[k];
+    if (rs != AMG_OK) break;
+    l.qnnz = host[0];
     rs = hier_alloc(h, (void **)&l.qci, sizeof(int32_t) * (l.qnnz + AMG_PAD));
     if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.qval, sizeof(double) * (l.qnnz + AMG_PAD));
     if (rs != AMG_OK) break;
     cudaMemsetAsync(l.qci + l.qnnz, 0, sizeof(int32_t) * AMG_PAD, st);
     cudaMemsetAsync(l.qval + l.qnnz, 0, sizeof(double) * AMG_PAD, st);
-    k_op_qfill<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.agg, l.wd, l.qrp, l.qci, l.qval);
+    k_op_qfill<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.agg, l.wd, l.qrp, first, l.qci, l.qval);
     count_launch();
     l.op_avail = 1;
     l.op_on = 1;
@@ -1096,6 +1409,7 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
   pool_free(cnt, st);
   pool_free(tiles, st);
   pool_free(tot, st);
+  pool_free(first, st);
   if (rs != AMG_OK) return rs;
   return amg_cuda_status(cudaGetLastError());
 }

