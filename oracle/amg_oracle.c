@@ -307,10 +307,11 @@ int orc_match_rounds(int n, const int *rp, const int *ci, const double *val, int
  * |a_ij|, and on equal weights the last one met in the row (the test
  * max(k,|a_ij|) = |a_ij| accepts equality).  The printed listing scans row i
  * only.  agg receives the coarse numbers in visit order.  Returns N_c. */
-int orc_nhem(int n, const int *rp, const int *ci, const double *val, int *agg) {
+int orc_nhem_dir(int n, const int *rp, const int *ci, const double *val, int descending, int *agg) {
   for (int i = 0; i < n; ++i) agg[i] = -1;
   int C = 0;
-  for (int i = 0; i < n; ++i) {
+  for (int s = 0; s < n; ++s) {
+    const int i = descending ? n - 1 - s : s;
     if (agg[i] >= 0) continue;
     double k = -1.0;
     int match = -1;
@@ -325,6 +326,10 @@ int orc_nhem(int n, const int *rp, const int *ci, const double *val, int *agg) {
     ++C;
   }
   return C;
+}
+
+int orc_nhem(int n, const int *rp, const int *ci, const double *val, int *agg) {
+  return orc_nhem_dir(n, rp, ci, val, 0, agg);
 }
 
 /* Aggregate numbering (Sec. 2.1.1, Algorithm 2's coarse counter C): every
@@ -407,7 +412,8 @@ typedef struct {
   int passes, max_levels, coarse_max;
   double stall_ratio, omega;
   int nu_pre, nu_post, coarse_solver; /* 0 auto, 1 dense LU, 2 CG */
-  int matcher;                        /* 0 greedy EHEM order, 1 literal rounds */
+  int matcher;                        /* 0 greedy EHEM order, 1 literal rounds, 2 node-based HEM
+                                         (Algorithm 2) with alternating scan direction */
   int cycle;                          /* 0 V, 1 W, 2 F (Sec. 2 names all three) */
   int tie_break;                      /* 0 smaller index, 1 larger (Algorithm 3's order) */
   int edge_weight;                    /* 0 max(|a_ij|,|a_ji|), 1 / sqrt(|a_ii a_jj|) */
@@ -440,19 +446,28 @@ static void level_free(orc_level *l) {
 }
 
 /* One pairwise pass: match, number, and form the Galerkin product. */
-static int coarsen_pass(const orc_params *prm, int n, const int *rp, const int *ci, const double *val,
-                        int *agg, int *nc_out, int **rp_c, int **ci_c, double **val_c,
+static int coarsen_pass(const orc_params *prm, int pass_index, int n, const int *rp, const int *ci,
+                        const double *val, int *agg, int *nc_out, int **rp_c, int **ci_c, double **val_c,
                         long long *nnz_c, int *rounds) {
-  int *mate = (int *)malloc((size_t)(n ? n : 1) * sizeof(int));
-  if (!mate) return ORC_ERR_OOM;
-  int r = 0;
-  int pairs = prm->matcher == 1
-                  ? orc_match_rounds_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate, &r)
-                  : orc_match_greedy_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate);
-  if (pairs < 0) { free(mate); return ORC_ERR_OOM; }
-  *rounds = r;
-  int nc = orc_aggregates(n, mate, agg);
-  free(mate);
+  int nc;
+  if (prm->matcher == 2) {
+    /* node-based HEM (Algorithm 2), its scan direction alternating from one
+     * pass to the next: from the first index in passes 0, 2, 4, ..., from the
+     * last index in passes 1, 3, 5, ... (counted over the whole hierarchy) */
+    *rounds = 0;
+    nc = orc_nhem_dir(n, rp, ci, val, pass_index % 2, agg);
+  } else {
+    int *mate = (int *)malloc((size_t)(n ? n : 1) * sizeof(int));
+    if (!mate) return ORC_ERR_OOM;
+    int r = 0;
+    int pairs = prm->matcher == 1
+                    ? orc_match_rounds_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate, &r)
+                    : orc_match_greedy_opt(n, rp, ci, val, prm->tie_break, prm->edge_weight, mate);
+    if (pairs < 0) { free(mate); return ORC_ERR_OOM; }
+    *rounds = r;
+    nc = orc_aggregates(n, mate, agg);
+    free(mate);
+  }
   long long nnz = rp[n];
   *rp_c = (int *)malloc(((size_t)nc + 1) * sizeof(int));
   *ci_c = (int *)malloc((size_t)(nnz ? nnz : 1) * sizeof(int));
@@ -583,7 +598,8 @@ int orc_setup(int n, const int *rp, const int *ci, const double *val, const orc_
       int nc, *rpc, *cic;
       double *valc;
       long long nnzc;
-      st = coarsen_pass(prm, cur_n, cur_rp, cur_ci, cur_val, pagg, &nc, &rpc, &cic, &valc, &nnzc, &rounds[p]);
+      st = coarsen_pass(prm, k * prm->passes + p, cur_n, cur_rp, cur_ci, cur_val, pagg, &nc, &rpc, &cic, &valc,
+                        &nnzc, &rounds[p]);
       if (st) { free(pagg); free(agg); orc_destroy(h); return st; }
       for (int i = 0; i < f->n; ++i) agg[i] = pagg[agg[i]];
       free(pagg);

@@ -40,7 +40,10 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     """Oracle parameters; defaults follow the method's configuration (2 pairwise
     passes, damped Jacobi omega = 2/3 with one pre and one post sweep, V-cycle;
-    cycle = 1 selects the W-cycle, 2 the F-cycle)."""
+    cycle = 1 selects the W-cycle, 2 the F-cycle).  matcher: 0 the greedy
+    edge-order matching (Algorithm 3), 1 its literal handshake rounds, 2 the
+    node-based matching of Algorithm 2 with the scan direction alternating
+    between passes (Sec. 2.1.1)."""
 
     _fields_ = [
         ("passes", C.c_int),
@@ -92,6 +95,7 @@ def lib():
             l.orc_match_rounds_opt.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, C.c_int, _i32p,
                                                C.POINTER(C.c_int)]
             l.orc_nhem.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p]
+            l.orc_nhem_dir.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_int, _i32p]
             l.orc_aggregates.argtypes = [C.c_int, _i32p, _i32p]
             l.orc_galerkin.argtypes = [C.c_int, _i32p, _i32p, _f64p, _i32p, C.c_int, _i32p, _i32p, _f64p]
             l.orc_galerkin.restype = C.c_longlong
@@ -158,12 +162,14 @@ def match_rounds(rp, ci, val, tie_break=0, edge_weight=0):
     return mate, r.value
 
 
-def nhem(rp, ci, val):
-    """Literal node-based HEM of Algorithm 2: (agg, n_c)."""
+def nhem(rp, ci, val, descending=False):
+    """Literal node-based HEM of Algorithm 2: (agg, n_c).  descending scans
+    the nodes from the last index down (the alternate direction of Sec. 2.1.1);
+    aggregates are numbered in visit order either way."""
     rp, ci, val = _csr(rp, ci, val)
     n = len(rp) - 1
     agg = np.empty(n, dtype=np.int32)
-    nc = lib().orc_nhem(n, rp, ci, val, agg)
+    nc = lib().orc_nhem_dir(n, rp, ci, val, int(bool(descending)), agg)
     return agg, nc
 
 

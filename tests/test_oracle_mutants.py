@@ -39,6 +39,10 @@ MUTANTS = [
      "test_flexible_beta_keeps_consecutive_directions_a_conjugate"),
     ("flexible_beta_is_fletcher_reeves", "s += z[i] * (r[i] - rold[i]);", "s += z[i] * r[i];",
      "test_flexible_beta_keeps_consecutive_directions_a_conjugate"),
+    ("nhem_never_descending", "nc = orc_nhem_dir(n, rp, ci, val, pass_index % 2, agg);",
+     "nc = orc_nhem_dir(n, rp, ci, val, 0, agg);", "test_alternating_node_based_hierarchy"),
+    ("nhem_descending_scan_wrong", "const int i = descending ? n - 1 - s : s;", "const int i = s;",
+     "test_node_based_matching_scans_both_ways_by_hand"),
     ("stall_rule_not_strict", "if ((double)cur_n / (double)f->n > prm->stall_ratio) {",
      "if ((double)cur_n / (double)f->n >= prm->stall_ratio) {", "test_hierarchy_stops_before_a_stalled_level"),
     ("stall_ratio_against_finest", "if ((double)cur_n / (double)f->n > prm->stall_ratio) {",

@@ -296,6 +296,71 @@ def test_hierarchy_stops_before_a_stalled_level():
     assert h.sizes() == cand[:first_stall]
 
 
+def _path(m):
+    a = np.diag([2.0] * m) + np.diag([-1.0] * (m - 1), 1) + np.diag([-1.0] * (m - 1), -1)
+    return W.from_dense(a)
+
+
+def test_node_based_matching_scans_both_ways_by_hand():
+    """Algorithm 2 on a 5-node path with equal weights, worked by hand.  From
+    the first index: 0 takes 1, 2 takes 3 (1 is taken), 4 stays single; ids in
+    visit order.  From the last index (the alternate direction of Sec. 2.1.1):
+    4 takes 3, 2 takes 1, 0 stays single, ids again in visit order.  A node
+    with two equally heavy free neighbours keeps the last one in stored order
+    (Algorithm 2's max(k, |a_ij|) = |a_ij| test)."""
+    s = _path(5)
+    agg, nc = O.nhem(s.rp, s.ci, s.val)
+    assert nc == 3 and agg.tolist() == [0, 0, 1, 1, 2]
+    agg, nc = O.nhem(s.rp, s.ci, s.val, descending=True)
+    assert nc == 3 and agg.tolist() == [2, 1, 1, 0, 0]
+    # a 3-node path: from the first index 0 takes 1; from the last, 2 takes 1
+    p3 = _path(3)
+    assert O.nhem(p3.rp, p3.ci, p3.val)[0].tolist() == [0, 0, 1]
+    assert O.nhem(p3.rp, p3.ci, p3.val, descending=True)[0].tolist() == [1, 0, 0]
+    # node 0 with two equally heavy free neighbours 1 and 2 keeps the last (2)
+    s3 = W.from_dense(np.array([[3.0, -1.0, -1.0], [-1.0, 2.0, 0.0], [-1.0, 0.0, 2.0]]))
+    assert O.nhem(s3.rp, s3.ci, s3.val)[0].tolist() == [0, 1, 0]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_node_based_matching_is_maximal_both_ways(seed):
+    s = W.random_spd(40, 0.15, seed, int_weights=True)
+    a = s.dense()
+    for desc in (False, True):
+        agg, nc = O.nhem(s.rp, s.ci, s.val, descending=desc)
+        sizes = np.bincount(agg, minlength=nc)
+        assert sizes.min() >= 1 and sizes.max() <= 2
+        single = np.flatnonzero(sizes[agg] == 1)
+        for i in single:  # no edge joins two singletons
+            for j in single:
+                assert i == j or a[i, j] == 0.0
+
+
+def test_alternating_node_based_hierarchy():
+    """matcher = 2: pass p of the hierarchy (counted over all levels) scans from
+    the first index when p is even and from the last when p is odd; every
+    level is the Galerkin product of its composed aggregates."""
+    s = W.lognormal3d(10, seed=5)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=30, matcher=2)
+    assert h.num_levels >= 3
+    rp, ci, val = s.rp, s.ci, s.val
+    p = 0
+    for k in range(h.num_levels - 1):
+        n = len(rp) - 1
+        comp = np.arange(n)
+        for _ in range(2):
+            agg, nc = O.nhem(rp, ci, val, descending=(p % 2 == 1))
+            comp = agg[comp]
+            rp, ci, val = O.galerkin(rp, ci, val, agg, nc)
+            p += 1
+        _, _, _, agg_h = h.level(k)
+        np.testing.assert_array_equal(agg_h, comp)
+        rpc, cic, vc, _ = h.level(k + 1)
+        np.testing.assert_array_equal(rpc, rp)
+        np.testing.assert_array_equal(cic, ci)
+        np.testing.assert_array_equal(vc, val)
+
+
 # --------------------------------------------------------------------------
 # Coarse solve, V-cycle, Krylov
 # --------------------------------------------------------------------------
