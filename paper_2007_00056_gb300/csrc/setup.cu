@@ -413,15 +413,47 @@ __device__ __forceinline__ int hem_pick_ld(int q, const int32_t *__restrict__ rp
   return best;
 }
 
-// Phase B for one newly matched node m of round r: every free neighbour q
-// whose pick was m joins the next list (stamp r + 1) with its new pick.  q is
-// reached from m only (a node has one pick), so the stamp is a plain store.
-// Appends go through `append` (a slot index); returns the number appended.
-template <bool L2ONLY, typename AppendF>
-__device__ __forceinline__ int hem_repick(int m, int r, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                          const double *__restrict__ w, int tie_larger, const int32_t *mate,
-                                          int32_t *pick, int *stamp, int2 *Dn, AppendF append) {
-  int added = 0;
+// List appends staged in shared memory: a push takes a slot from a block
+// counter; flush() reserves the block's range of the global list with one
+// atomic and copies the staged entries out, so the global counter sees one
+// atomic per block and flush instead of one per warp (thousands of atomics
+// on one address serialise at its L2 slice).  Pushes beyond CAP between two
+// flushes go straight to the global list.  Every thread of the block calls
+// flush(); it returns the number of entries pushed since the last flush.
+template <typename T, int CAP>
+struct StagedList {
+  T *buf;
+  int *cnt, *base;
+  T *out;
+  int *gctr;
+  __device__ __forceinline__ void push(T v) {
+    const int k = atomicAdd(cnt, 1);
+    if (k < CAP) buf[k] = v;
+    else out[atomicAdd(gctr, 1)] = v;
+  }
+  __device__ __forceinline__ int flush() {
+    __syncthreads();
+    const int c = *cnt, m = c < CAP ? c : CAP;
+    if (threadIdx.x == 0 && m) *base = atomicAdd(gctr, m);
+    __syncthreads();
+    const int b = *base;
+    for (int k = threadIdx.x; k < m; k += blockDim.x) out[b + k] = buf[k];
+    __syncthreads();
+    if (threadIdx.x == 0) *cnt = 0;
+    __syncthreads();
+    return c;
+  }
+};
+#define HEM_STAGE 3072  // staged entries per block between flushes
+
+// Phase B, first half, for one newly matched node m of round r: every free
+// neighbour q whose pick was m depends on m and must re-pick.  q is reached
+// from m only (a node has one pick), so its stamp (r + 1: member of the next
+// list) is a plain store.  Each dependant goes to `found`.
+template <bool L2ONLY, typename FoundF>
+__device__ __forceinline__ void hem_dependants(int m, int r, const int32_t *__restrict__ rp,
+                                               const int32_t *__restrict__ ci, const int32_t *mate,
+                                               const int32_t *pick, int *stamp, FoundF found) {
   const int e0 = __ldg(&rp[m]), e1 = __ldg(&rp[m + 1]);
   for (int base = e0; base < e1; base += HEM_GROUP) {
     int qq[HEM_GROUP], mq[HEM_GROUP], pq[HEM_GROUP];
@@ -438,13 +470,45 @@ __device__ __forceinline__ int hem_repick(int m, int r, const int32_t *__restric
       const int q = qq[u];
       if (q == m || mq[u] != HEM_FREE || pq[u] != m) continue;
       stamp[q] = r + 1;
-      const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
-      pick[q] = np;
-      Dn[append()] = make_int2(q, np);
-      ++added;
+      found(q);
     }
   }
-  return added;
+}
+
+// Phase B of a block: the dependants of the matched nodes `nodes` (each
+// thread passes the ones it holds; -1 for none) are collected in shared
+// memory, then re-picked one per thread, so a thread's chain of dependent
+// loads is one row scan and one pick rather than a scan and a pick per
+// dependant.  Dependants beyond the shared list are re-picked where found.
+// Every (q, new pick) goes to `emit`.  All threads of the block call it.
+#define HEM_CAND 4096
+template <bool L2ONLY, typename EmitF>
+__device__ __forceinline__ void hem_phase_b(int m0, int m1, int r, const int32_t *__restrict__ rp,
+                                            const int32_t *__restrict__ ci, const double *__restrict__ w,
+                                            int tie_larger, const int32_t *mate, int32_t *pick, int *stamp,
+                                            int *cand, int *ncand, EmitF emit) {
+  if (threadIdx.x == 0) *ncand = 0;
+  __syncthreads();
+  auto found = [&](int q) {
+    const int k = atomicAdd(ncand, 1);
+    if (k < HEM_CAND) {
+      cand[k] = q;
+    } else {
+      const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
+      pick[q] = np;
+      emit(make_int2(q, np));
+    }
+  };
+  if (m0 >= 0) hem_dependants<L2ONLY>(m0, r, rp, ci, mate, pick, stamp, found);
+  if (m1 >= 0) hem_dependants<L2ONLY>(m1, r, rp, ci, mate, pick, stamp, found);
+  __syncthreads();
+  const int nc = min(*ncand, HEM_CAND);
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+    const int q = cand[k];
+    const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
+    pick[q] = np;
+    emit(make_int2(q, np));
+  }
 }
 
 // Every round of one matching pass in one cooperative launch (all blocks
@@ -466,8 +530,11 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
                int *ctr, unsigned *eflags, int max_rounds) {
   __shared__ int fail_sh;
   __shared__ unsigned hi_sh;
-  __shared__ int blk_cnt;
-  if (threadIdx.x == 0) { fail_sh = 0; blk_cnt = 0; }
+  __shared__ int s_cnt, s_base, s_nc;
+  __shared__ int2 s_d[HEM_STAGE];  // staged next-list entries (the matched list uses its first half as ints)
+  __shared__ int s_c[HEM_CAND];    // dependants waiting for their new pick
+  int *s_m = (int *)s_d;
+  if (threadIdx.x == 0) { fail_sh = 0; s_cnt = 0; }
   const unsigned G = gridDim.x;
   SumBarrier gb{(unsigned long long *)(ctr + HEM_COOP_BAR), 0u};
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
@@ -500,11 +567,9 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
             }
           }
           if (__syncthreads_or(mi >= 0) == 0) { fin = 1; ++lr; break; }
-          auto app = [&]() { return atomicAdd(&s_nn, 1); };
-          if (mi >= 0) {
-            hem_repick<false>(mi, lr, rp, ci, w, tie_larger, mate, pick, stamp, dn, app);
-            if (stamp[mj] != lr) hem_repick<false>(mj, lr, rp, ci, w, tie_larger, mate, pick, stamp, dn, app);
-          }
+          auto app = [&](int2 v) { dn[atomicAdd(&s_nn, 1)] = v; };
+          const int m1 = (mi >= 0 && stamp[mj] != lr) ? mj : -1;
+          hem_phase_b<false>(mi, m1, lr, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc, app);
           __syncthreads();
           lnd = s_nn;
           __syncthreads();  // every thread has read s_nn before the next round resets it
@@ -563,16 +628,23 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
         }
       }
     } else {
-      for (int t = gtid; t < nd; t += gstride) {
-        int i, j;
-        if (r == 0) { i = t; j = __ldcg(&pick[i]); }
-        else { const int2 e = __ldcg(&D[t]); i = e.x; j = e.y; }
-        if (j < 0 || __ldcg(&pick[j]) != i) continue;
-        mate[i] = j;
-        mate[j] = i;
-        any = true;
-        M[warp_append(cm)] = i;
-        if (__ldcg(&stamp[j]) != r) M[warp_append(cm)] = j;
+      // chunks of one item per thread, the matched list staged per chunk
+      StagedList<int, HEM_STAGE> ml{s_m, &s_cnt, &s_base, M, cm};
+      for (int t0 = blockIdx.x * blockDim.x; t0 < nd; t0 += gstride) {
+        const int t = t0 + threadIdx.x;
+        if (t < nd) {
+          int i, j;
+          if (r == 0) { i = t; j = __ldcg(&pick[i]); }
+          else { const int2 e = __ldcg(&D[t]); i = e.x; j = e.y; }
+          if (j >= 0 && __ldcg(&pick[j]) == i) {
+            mate[i] = j;
+            mate[j] = i;
+            any = true;
+            ml.push(i);
+            if (__ldcg(&stamp[j]) != r) ml.push(j);
+          }
+        }
+        ml.flush();
       }
     }
     const int blk_any = __syncthreads_or(any);
@@ -583,23 +655,24 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
       break;
     }
     hi_prev = hi;
-    // B: the next list
+    // B: the next list, staged per block
     const int nm = regs ? 0 : __ldcg(cm);
-    auto app = [&]() { return warp_append(cn); };
+    StagedList<int2, HEM_STAGE> nl{s_d, &s_cnt, &s_base, Dn, cn};
+    auto app = [&](int2 v) { nl.push(v); };
     int added = 0;
     if (regs) {
-      if (mi >= 0) {
-        added += hem_repick<true>(mi, r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
-        if (__ldcg(&stamp[mj]) != r) added += hem_repick<true>(mj, r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
-      }
+      const int m1 = (mi >= 0 && __ldcg(&stamp[mj]) != r) ? mj : -1;
+      hem_phase_b<true>(mi, m1, r, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc, app);
+      added = nl.flush();
     } else {
-      for (int t = gtid; t < nm; t += gstride)
-        added += hem_repick<true>(__ldcg(&M[t]), r, rp, ci, w, tie_larger, mate, pick, stamp, Dn, app);
+      for (int t0 = blockIdx.x * blockDim.x; t0 < nm; t0 += gstride) {
+        const int t = t0 + threadIdx.x;
+        hem_phase_b<true>(t < nm ? __ldcg(&M[t]) : -1, -1, r, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc,
+                          app);
+        added += nl.flush();
+      }
     }
-    if (added) atomicAdd(&blk_cnt, added);
-    __syncthreads();
-    if (!gb.sync(G, (unsigned)blk_cnt, eflags, &fail_sh, &hi_sh, &hi)) return;
-    if (threadIdx.x == 0) blk_cnt = 0;  // every thread read it before the barrier; the next adds follow barrier A
+    if (!gb.sync(G, (unsigned)added, eflags, &fail_sh, &hi_sh, &hi)) return;
     nd = (int)(hi - hi_prev);
     hi_prev = hi;
     int2 *tmp = D;
