@@ -57,8 +57,8 @@ def parse_args():
     ap.add_argument("--profile-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=192,
-                    help="requests of the serving stream sample added to the line (0: none)")
+    ap.add_argument("--serving-requests", type=int, default=2048,
+                    help="requests of the serving stream added to the line (2048: the whole stream; 0: none)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (256^3 mixed precision, 2048^2 BiCGStab, 64^2 Poisson)")
     ap.add_argument("--workload", choices=["solve", "serving"], default="solve",
@@ -306,9 +306,10 @@ def generate_requests(count: int):
     return reqs, [systems[r.rid] for r in reqs]
 
 
-def run_serving(reqs, systems):
+def run_serving(reqs, systems, plain_sample=256):
     """Serves the stream at its arrival times (latency), then all at once
-    (capacity), then the plain FP64 method one request at a time (context)."""
+    (capacity), then the plain FP64 method one request at a time on the first
+    `plain_sample` requests (context)."""
     import numpy as np
     import torch
 
@@ -327,12 +328,17 @@ def run_serving(reqs, systems):
     res_cap, wall_cap = S.serve_stream(srv, reqs, systems, time_scale=0.0)
     srv.close()
     ok = sum(r.status == amg.AMG_OK and r.rel_res_true <= 1e-8 for r in res)
+    # the queue stays bounded when late requests wait no longer than early ones
+    q = len(res) // 4
+    lat_first = S.latency_summary(res[:q]) if q else None
+    lat_last = S.latency_summary(res[-q:]) if q else None
     # plain FP64 method: setup + pcg_solve per request, sequential, same device
     dev = torch.device("cuda", torch.cuda.current_device())
+    sample = list(zip(reqs, systems))[:plain_sample]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     per_request = []
-    for s in systems:
+    for _, s in sample:
         tr = time.perf_counter()
         rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
         # the server's hierarchy shape (coarsest size) in plain FP64
@@ -346,18 +352,22 @@ def run_serving(reqs, systems):
     plain = time.perf_counter() - t0
     # the plain method serving the same arrivals one request at a time
     done, plain_lat = 0.0, []
-    for rq, t in zip(reqs, per_request):
+    for (rq, _), t in zip(sample, per_request):
         done = max(done, rq.arrival_s) + t
         plain_lat.append((done - rq.arrival_s) * 1e3)
     lat = S.latency_summary(res)
     return {
         "requests": len(reqs), "unknowns_total": int(total_n), "converged_1e-8": int(ok),
         "arrival_rate_hz": 200.0, "solves_per_s": len(reqs) / wall, "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+        "max_ms": lat["max_ms"],
+        "p50_ms_first_quarter": lat_first["p50_ms"] if lat_first else None,
+        "p50_ms_last_quarter": lat_last["p50_ms"] if lat_last else None,
         "mean_queue_ms": lat.get("mean_queue_ms"), "mean_setup_ms": lat.get("mean_setup_ms"),
         "mean_solve_ms": lat.get("mean_solve_ms"),
         "capacity_solves_per_s": len(reqs) / wall_cap,
         "capacity_p50_ms": S.latency_summary(res_cap)["p50_ms"],
-        "plain_fp64_sequential_solves_per_s": len(reqs) / plain,
+        "plain_fp64_sequential_sample": len(sample),
+        "plain_fp64_sequential_solves_per_s": len(sample) / plain,
         "plain_fp64_sequential_p50_ms": float(np.percentile(plain_lat, 50)),
         "plain_fp64_sequential_p99_ms": float(np.percentile(plain_lat, 99)),
         "batched_requests": int(stats.get("batched", 0)), "batches": int(stats.get("batches", 0)),

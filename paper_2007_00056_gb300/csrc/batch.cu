@@ -24,6 +24,10 @@ struct BatchLevel {
   const void *val, *dinv;  // T-typed (double or float)
   const int32_t *agg, *mrp, *mem;
   void *f, *x, *t, *y;     // T-typed level vectors
+  // residual-operator form (null when the level has none): C values (A's
+  // pattern), Q = P - omega D^-1 A P in CSR, omega D^-1; T-typed
+  const void *cval, *qval, *wd;
+  const int32_t *qrp, *qci;
 };
 
 struct BatchSys {
@@ -71,6 +75,9 @@ __device__ __forceinline__ T brow(const int32_t *rp, const int32_t *ci, const V 
 }
 
 // One V-cycle of the system from a zero guess: out0 = M^{-1} f0 (level-0 vectors of type T).
+// A level with the residual-operator form (Level documents C and Q) forms its
+// residual as t = C f on the way down and its result as Q x_c + wd (f + t) on
+// the way up; the others run the explicit sweeps.
 template <typename T>
 __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
   const int L = S.L;
@@ -83,6 +90,21 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
     const T *val = (const T *)l.val, *dinv = (const T *)l.dinv;
     T *a = (T *)l.x, *b = (T *)l.t;
     const T *f = fk[k];
+    if (l.cval) {
+      const T *cv = (const T *)l.cval;
+      for (int i = threadIdx.x; i < l.n; i += blockDim.x) b[i] = brow<T, T>(l.rp, l.ci, cv, f, i);
+      __syncthreads();
+      cur[k] = nullptr;
+      T *fc = (T *)S.lev[k + 1].f;
+      for (int I = threadIdx.x; I < l.nc; I += blockDim.x) {
+        int e0 = l.mrp[I], e1 = l.mrp[I + 1];
+        T s = b[l.mem[e0]];
+        for (int m = e0 + 1; m < e1; ++m) s += b[l.mem[m]];
+        fc[I] = s;
+      }
+      __syncthreads();
+      continue;
+    }
     for (int i = threadIdx.x; i < l.n; i += blockDim.x) a[i] = omega * (dinv[i] * f[i]);
     __syncthreads();
     for (int sw = 1; sw < S.nu_pre; ++sw) {
@@ -123,6 +145,14 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
     const T *val = (const T *)l.val, *dinv = (const T *)l.dinv;
     const T *f = fk[k];
     T *fin = (k == 0) ? out0 : (T *)l.y;
+    if (l.cval) {
+      const T *qv = (const T *)l.qval, *wd = (const T *)l.wd, *t = (const T *)l.t;
+      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+        fin[i] = brow<T, T>(l.qrp, l.qci, qv, xc, i) + wd[i] * (f[i] + t[i]);
+      __syncthreads();
+      xc = fin;
+      continue;
+    }
     T *in = cur[k];
     T *other = (in == (T *)l.x) ? (T *)l.t : (T *)l.x;
     // prolongation into `other`, then the post-smoothing sweeps, the last into fin
@@ -161,7 +191,13 @@ __device__ void b_precond<float>(const BatchSys &S, const double *r, double *z) 
   __syncthreads();
 }
 
-// Flexible (or not) AMG-PCG of Algorithm 4 for the block's system.
+// Flexible (or not) AMG-PCG of Algorithm 4 for the block's system, with the
+// same stopping rule as pcg_solve: a stop on the recurrence residual whose
+// true residual b - A x misses rtol replaces r by the true residual and
+// restarts from x (at most BATCH_RESTARTS times), so an OK exit always has
+// ||b - A x|| <= rtol ||b||.  The flexible beta is (z_{j+1}, r_{j+1} - r_j) /
+// (z_j, r_j), formed as -alpha (z_{j+1}, q_j) / (z_j, r_j).
+#define BATCH_RESTARTS 4
 template <typename T>
 __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const BatchJob *__restrict__ jobs,
                                                               double rtol, int max_iter, int flexible,
@@ -173,17 +209,23 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const Bat
   const double *b = jobs[sidx].b;
   double *x = jobs[sidx].x;
   const int n = S.n;
-  double *r = S.r, *z = S.z, *p = S.p, *q = S.q, *rold = S.rold;
-  // r = b - A x
-  double bb = 0.0, rr = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
-    r[i] = ri;
-    bb += b[i] * b[i];
-    rr += ri * ri;
-  }
-  bb = bsum(bb, sh);
-  rr = bsum(rr, sh);
+  double *r = S.r, *z = S.z, *p = S.p, *q = S.q;
+  // ||b||, and r = b - A x with its norm
+  auto residual = [&](double *bb_out) {
+    double bb = 0.0, rr = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
+      r[i] = ri;
+      bb += b[i] * b[i];
+      rr += ri * ri;
+    }
+    bb = bsum(bb, sh);
+    rr = bsum(rr, sh);
+    if (bb_out) *bb_out = bb;
+    return rr;
+  };
+  double bb = 0.0;
+  double rr = residual(&bb);
   const double bnorm = sqrt(bb);
   double rel = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
   int it = 0, status = AMG_ERR_NOT_CONVERGED;
@@ -195,52 +237,61 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const Bat
   } else if (rel <= rtol) {
     status = AMG_OK;
   } else if (max_iter > 0) {
-    __syncthreads();
-    b_precond<T>(S, r, z);
-    double rz = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
-    rz = bsum(rz, sh);
-    for (it = 1; it <= max_iter; ++it) {
-      __syncthreads();
-      double pq = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double qi = brow<double, double>(S.rp0, S.ci0, S.val0, p, i);
-        q[i] = qi;
-        pq += p[i] * qi;
-      }
-      pq = bsum(pq, sh);
-      if (pq == 0.0 || !isfinite(pq) || !isfinite(rz)) { status = AMG_ERR_BREAKDOWN; break; }
-      const double alpha = rz / pq;
-      double r2 = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        x[i] = x[i] + alpha * p[i];
-        double ri = r[i];
-        if (flexible) rold[i] = ri;
-        ri = ri - alpha * q[i];
-        r[i] = ri;
-        r2 += ri * ri;
-      }
-      r2 = bsum(r2, sh);
-      rel = sqrt(r2) / bnorm;
-      if (rel <= rtol) { status = AMG_OK; break; }
-      if (!isfinite(rel)) { status = AMG_ERR_BREAKDOWN; break; }
-      if (it == max_iter) break;
+    for (int restart = 0;; ++restart) {
       __syncthreads();
       b_precond<T>(S, r, z);
-      double rzn = 0.0, zd = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        rzn += r[i] * z[i];
-        if (flexible) zd += z[i] * (r[i] - rold[i]);
+      double rz = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
+      rz = bsum(rz, sh);
+      status = AMG_ERR_NOT_CONVERGED;
+      while (it < max_iter) {
+        __syncthreads();
+        double pq = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const double qi = brow<double, double>(S.rp0, S.ci0, S.val0, p, i);
+          q[i] = qi;
+          pq += p[i] * qi;
+        }
+        pq = bsum(pq, sh);
+        if (pq == 0.0 || !isfinite(pq) || !isfinite(rz)) { status = AMG_ERR_BREAKDOWN; break; }
+        const double alpha = rz / pq;
+        double r2 = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          x[i] = x[i] + alpha * p[i];
+          const double ri = r[i] - alpha * q[i];
+          r[i] = ri;
+          r2 += ri * ri;
+        }
+        r2 = bsum(r2, sh);
+        ++it;
+        rel = sqrt(r2) / bnorm;
+        if (rel <= rtol) { status = AMG_OK; break; }
+        if (!isfinite(rel)) { status = AMG_ERR_BREAKDOWN; break; }
+        if (it == max_iter) break;
+        __syncthreads();
+        b_precond<T>(S, r, z);
+        double rzn = 0.0, zq = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          rzn += r[i] * z[i];
+          if (flexible) zq += z[i] * q[i];
+        }
+        rzn = bsum(rzn, sh);
+        if (flexible) zq = bsum(zq, sh);
+        const double beta = (flexible ? -alpha * zq : rzn) / rz;
+        if (!isfinite(beta)) { status = AMG_ERR_BREAKDOWN; break; }
+        rz = rzn;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
       }
-      rzn = bsum(rzn, sh);
-      if (flexible) zd = bsum(zd, sh);
-      const double beta = (flexible ? zd : rzn) / rz;
-      if (!isfinite(beta)) { status = AMG_ERR_BREAKDOWN; break; }
-      rz = rzn;
+      if (status != AMG_OK || restart >= BATCH_RESTARTS || it >= max_iter) break;
+      // true residual: accept, or restart from x with r = b - A x
       __syncthreads();
-      for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+      rr = residual(nullptr);
+      rel = sqrt(rr) / bnorm;
+      if (rel <= rtol) break;
+      if (!isfinite(rel)) { status = AMG_ERR_BREAKDOWN; break; }
+      status = AMG_ERR_NOT_CONVERGED;
     }
-    if (it > max_iter) it = max_iter;
   }
   __syncthreads();
   // true relative residual from x
@@ -265,7 +316,7 @@ namespace {
 
 // Builds (once) the device descriptor of a hierarchy for batched solves.
 amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **out) {
-  if (h->batch_desc) { *out = (const BatchSys *)h->batch_desc; return AMG_OK; }
+  if (h->batch_desc && !h->batch_desc_stale) { *out = (const BatchSys *)h->batch_desc; return AMG_OK; }
   if (!h->dense || !h->ainv || h->lev[h->L].n > BATCH_MAX_COARSE) return AMG_ERR_UNSUPPORTED;
   if (h->prm.precision == AMG_FP16_STORAGE) return AMG_ERR_UNSUPPORTED;
   if (h->prm.cycle != AMG_CYCLE_V) return AMG_ERR_UNSUPPORTED;
@@ -293,6 +344,12 @@ amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **o
     b.x = f32 ? (void *)l.x32 : (void *)l.x;
     b.t = f32 ? (void *)l.t32 : (void *)l.t;
     b.y = f32 ? (void *)l.y32 : (void *)l.y;
+    const bool op = k < h->L && l.op_avail && l.op_on;
+    b.cval = op ? (f32 ? (const void *)l.cval32 : (const void *)l.cval) : nullptr;
+    b.qval = op ? (f32 ? (const void *)l.qval32 : (const void *)l.qval) : nullptr;
+    b.wd = op ? (f32 ? (const void *)l.wd32 : (const void *)l.wd) : nullptr;
+    b.qrp = op ? l.qrp : nullptr;
+    b.qci = op ? l.qci : nullptr;
   }
   d.ainv = h->ainv;
   d.rp0 = h->lev[0].rp;
@@ -303,11 +360,12 @@ amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **o
   d.p = h->kp;
   d.q = h->kq;
   d.rold = h->krold;
-  void *dev = nullptr;
-  AMG_TRY(hier_alloc(h, &dev, sizeof(BatchSys)));
+  void *dev = h->batch_desc;  // rebuilt in place when the levels' forms changed
+  if (!dev) AMG_TRY(hier_alloc(h, &dev, sizeof(BatchSys)));
   AMG_CUDA(cudaMemcpyAsync(dev, &d, sizeof(BatchSys), cudaMemcpyHostToDevice, s));
   AMG_CUDA(cudaStreamSynchronize(s));
   h->batch_desc = dev;
+  h->batch_desc_stale = 0;
   *out = (const BatchSys *)dev;
   return AMG_OK;
 }

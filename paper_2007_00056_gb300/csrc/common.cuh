@@ -164,6 +164,7 @@ struct amg_hierarchy {
   int solves = 0;            // Krylov solves run on this hierarchy (graphs from the second one)
   Profiler prof;
   void *batch_desc = nullptr;  // device descriptor for batched solves (built on first use)
+  int batch_desc_stale = 0;    // the levels' kernel forms changed since it was built
 };
 
 // Kernel launches issued by this library since it was loaded (graph replays

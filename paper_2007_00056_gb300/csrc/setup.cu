@@ -385,29 +385,59 @@ struct SumBarrier {
 template <bool L2ONLY>
 __device__ __forceinline__ int ld_state(const int *p) { return L2ONLY ? __ldcg(p) : *p; }
 
-// Heaviest free neighbour of q given the state loads of policy L2ONLY
-// (grouped loads as in hem_pick_node).
-template <bool L2ONLY>
-__device__ __forceinline__ int hem_pick_ld(int q, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                          const double *__restrict__ w, int tie_larger, const int32_t *mate) {
+// The graph of a matching pass as the rounds read it: CSR with edge weights,
+// and, when every node has at most HEM_ELL neighbours, each node's neighbours
+// sorted by preference (heaviest first, ties by the pass's index rule), -1
+// padded: a pick is then the first free entry of one 32-byte row, with no
+// weights and no row pointers on the round's dependent-load chain.
+#define HEM_ELL 8
+struct HemGraph {
+  const int32_t *rp, *ci;
+  const double *w;
+  int tie_larger;
+  const int32_t *nb;  // n x HEM_ELL sorted neighbours (ELL form only)
+};
+
+// Neighbours of u into jj[0..HEM_ELL) (-1 beyond the row) from the sorted
+// table, two 16-byte loads.
+__device__ __forceinline__ void hem_row_ell(const int32_t *__restrict__ nb, int u, int (&jj)[HEM_ELL]) {
+  const int4 a = __ldg((const int4 *)(nb + (size_t)u * HEM_ELL));
+  const int4 b = __ldg((const int4 *)(nb + (size_t)u * HEM_ELL) + 1);
+  jj[0] = a.x; jj[1] = a.y; jj[2] = a.z; jj[3] = a.w;
+  jj[4] = b.x; jj[5] = b.y; jj[6] = b.z; jj[7] = b.w;
+}
+
+// Heaviest free neighbour of q (the pass's tie rule), -1 when none.
+template <bool L2ONLY, bool ELL>
+__device__ __forceinline__ int hem_pick(int q, const HemGraph &g, const int32_t *mate) {
+  if (ELL) {
+    int jj[HEM_ELL], mm[HEM_ELL];
+    hem_row_ell(g.nb, q, jj);
+#pragma unroll
+    for (int u = 0; u < HEM_ELL; ++u) mm[u] = jj[u] >= 0 ? ld_state<L2ONLY>(&mate[jj[u]]) : 0;
+#pragma unroll
+    for (int u = 0; u < HEM_ELL; ++u)
+      if (mm[u] == HEM_FREE) return jj[u];
+    return -1;
+  }
   int best = -1;
   double bw = 0.0;
-  const int e0 = __ldg(&rp[q]), e1 = __ldg(&rp[q + 1]);
+  const int e0 = __ldg(&g.rp[q]), e1 = __ldg(&g.rp[q + 1]);
   for (int base = e0; base < e1; base += HEM_GROUP) {
     int jj[HEM_GROUP], mm[HEM_GROUP];
     double ww[HEM_GROUP];
 #pragma unroll
     for (int u = 0; u < HEM_GROUP; ++u) {
       const int e = base + u;
-      jj[u] = e < e1 ? __ldg(&ci[e]) : -1;
-      ww[u] = e < e1 ? __ldg(&w[e]) : 0.0;
+      jj[u] = e < e1 ? __ldg(&g.ci[e]) : -1;
+      ww[u] = e < e1 ? __ldg(&g.w[e]) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < HEM_GROUP; ++u) mm[u] = (ww[u] > 0.0) ? ld_state<L2ONLY>(&mate[jj[u]]) : 0;
 #pragma unroll
     for (int u = 0; u < HEM_GROUP; ++u) {
       if (!(ww[u] > 0.0) || mm[u] != HEM_FREE) continue;
-      if (best < 0 || ww[u] > bw || (tie_larger && ww[u] == bw)) { best = jj[u]; bw = ww[u]; }
+      if (best < 0 || ww[u] > bw || (g.tie_larger && ww[u] == bw)) { best = jj[u]; bw = ww[u]; }
     }
   }
   return best;
@@ -450,28 +480,37 @@ struct StagedList {
 // neighbour q whose pick was m depends on m and must re-pick.  q is reached
 // from m only (a node has one pick), so its stamp (r + 1: member of the next
 // list) is a plain store.  Each dependant goes to `found`.
-template <bool L2ONLY, typename FoundF>
-__device__ __forceinline__ void hem_dependants(int m, int r, const int32_t *__restrict__ rp,
-                                               const int32_t *__restrict__ ci, const int32_t *mate,
+template <bool L2ONLY, bool ELL, typename FoundF>
+__device__ __forceinline__ void hem_dependants(int m, int r, const HemGraph &g, const int32_t *mate,
                                                const int32_t *pick, int *stamp, FoundF found) {
-  const int e0 = __ldg(&rp[m]), e1 = __ldg(&rp[m + 1]);
-  for (int base = e0; base < e1; base += HEM_GROUP) {
-    int qq[HEM_GROUP], mq[HEM_GROUP], pq[HEM_GROUP];
-#pragma unroll
-    for (int u = 0; u < HEM_GROUP; ++u) qq[u] = base + u < e1 ? __ldg(&ci[base + u]) : m;
+  auto visit = [&](const int (&qq)[HEM_GROUP]) {
+    int mq[HEM_GROUP], pq[HEM_GROUP];
 #pragma unroll
     for (int u = 0; u < HEM_GROUP; ++u) {
-      const bool other = qq[u] != m;
+      const bool other = qq[u] >= 0 && qq[u] != m;
       mq[u] = other ? ld_state<L2ONLY>(&mate[qq[u]]) : 0;
       pq[u] = other ? ld_state<L2ONLY>(&pick[qq[u]]) : -1;
     }
 #pragma unroll
     for (int u = 0; u < HEM_GROUP; ++u) {
       const int q = qq[u];
-      if (q == m || mq[u] != HEM_FREE || pq[u] != m) continue;
+      if (q < 0 || q == m || mq[u] != HEM_FREE || pq[u] != m) continue;
       stamp[q] = r + 1;
       found(q);
     }
+  };
+  if (ELL) {
+    int qq[HEM_ELL];
+    hem_row_ell(g.nb, m, qq);
+    visit(qq);
+    return;
+  }
+  const int e0 = __ldg(&g.rp[m]), e1 = __ldg(&g.rp[m + 1]);
+  for (int base = e0; base < e1; base += HEM_GROUP) {
+    int qq[HEM_GROUP];
+#pragma unroll
+    for (int u = 0; u < HEM_GROUP; ++u) qq[u] = base + u < e1 ? __ldg(&g.ci[base + u]) : -1;
+    visit(qq);
   }
 }
 
@@ -482,11 +521,9 @@ __device__ __forceinline__ void hem_dependants(int m, int r, const int32_t *__re
 // dependant.  Dependants beyond the shared list are re-picked where found.
 // Every (q, new pick) goes to `emit`.  All threads of the block call it.
 #define HEM_CAND 4096
-template <bool L2ONLY, typename EmitF>
-__device__ __forceinline__ void hem_phase_b(int m0, int m1, int r, const int32_t *__restrict__ rp,
-                                            const int32_t *__restrict__ ci, const double *__restrict__ w,
-                                            int tie_larger, const int32_t *mate, int32_t *pick, int *stamp,
-                                            int *cand, int *ncand, EmitF emit) {
+template <bool L2ONLY, bool ELL, typename EmitF>
+__device__ __forceinline__ void hem_phase_b(int m0, int m1, int r, const HemGraph &g, const int32_t *mate,
+                                            int32_t *pick, int *stamp, int *cand, int *ncand, EmitF emit) {
   if (threadIdx.x == 0) *ncand = 0;
   __syncthreads();
   auto found = [&](int q) {
@@ -494,21 +531,51 @@ __device__ __forceinline__ void hem_phase_b(int m0, int m1, int r, const int32_t
     if (k < HEM_CAND) {
       cand[k] = q;
     } else {
-      const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
+      const int np = hem_pick<L2ONLY, ELL>(q, g, mate);
       pick[q] = np;
       emit(make_int2(q, np));
     }
   };
-  if (m0 >= 0) hem_dependants<L2ONLY>(m0, r, rp, ci, mate, pick, stamp, found);
-  if (m1 >= 0) hem_dependants<L2ONLY>(m1, r, rp, ci, mate, pick, stamp, found);
+  if (m0 >= 0) hem_dependants<L2ONLY, ELL>(m0, r, g, mate, pick, stamp, found);
+  if (m1 >= 0) hem_dependants<L2ONLY, ELL>(m1, r, g, mate, pick, stamp, found);
   __syncthreads();
   const int nc = min(*ncand, HEM_CAND);
   for (int k = threadIdx.x; k < nc; k += blockDim.x) {
     const int q = cand[k];
-    const int np = hem_pick_ld<L2ONLY>(q, rp, ci, w, tie_larger, mate);
+    const int np = hem_pick<L2ONLY, ELL>(q, g, mate);
     pick[q] = np;
     emit(make_int2(q, np));
   }
+}
+
+// Sorted neighbour table of the ELL form: row i lists i's neighbours j with
+// w_ij > 0, heaviest first, equal weights by the tie rule (smaller index
+// first, or larger with tie_larger), -1 padded to HEM_ELL.  A row with more
+// than HEM_ELL neighbours sets *too_wide (the pass then uses the CSR form).
+__global__ void k_hem_ell(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                          const double *__restrict__ w, int tie_larger, int32_t *__restrict__ nb,
+                          unsigned *too_wide) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int jj[HEM_ELL];
+  double ww[HEM_ELL];
+  int c = 0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double we = w[e];
+    if (!(we > 0.0)) continue;
+    if (c == HEM_ELL) { atomicOr(too_wide, 1u); return; }
+    // insertion in preference order
+    const int j = ci[e];
+    int k = c++;
+    while (k > 0 && (ww[k - 1] < we || (ww[k - 1] == we && (tie_larger ? jj[k - 1] < j : jj[k - 1] > j)))) {
+      jj[k] = jj[k - 1];
+      ww[k] = ww[k - 1];
+      --k;
+    }
+    jj[k] = j;
+    ww[k] = we;
+  }
+  for (int k = 0; k < HEM_ELL; ++k) nb[(size_t)i * HEM_ELL + k] = k < c ? jj[k] : -1;
 }
 
 // Every round of one matching pass in one cooperative launch (all blocks
@@ -524,10 +591,12 @@ __device__ __forceinline__ void hem_phase_b(int m0, int m1, int r, const int32_t
 // run (that last one included) and 1 when it ended (0: stopped at
 // max_rounds or on a barrier timeout).  Picks, pairs and round counts are
 // those of the synchronous rounds.
+template <bool ELL>
 __global__ void __launch_bounds__(HEM_COOP_THREADS)
     k_hem_coop(int n, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ w,
-               int tie_larger, int32_t *mate, int32_t *pick, int *stamp, int2 *Da, int2 *Db, int32_t *M,
-               int *ctr, unsigned *eflags, int max_rounds) {
+               int tie_larger, const int32_t *__restrict__ nb, int32_t *mate, int32_t *pick, int *stamp, int2 *Da,
+               int2 *Db, int32_t *M, int *ctr, unsigned *eflags, int max_rounds) {
+  const HemGraph g{rp, ci, w, tie_larger, nb};
   __shared__ int fail_sh;
   __shared__ unsigned hi_sh;
   __shared__ int s_cnt, s_base, s_nc;
@@ -538,7 +607,7 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
   const unsigned G = gridDim.x;
   SumBarrier gb{(unsigned long long *)(ctr + HEM_COOP_BAR), 0u};
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-  for (int i = gtid; i < n; i += gstride) pick[i] = hem_pick_node(i, rp, ci, w, tie_larger, mate);
+  for (int i = gtid; i < n; i += gstride) pick[i] = hem_pick<true, ELL>(i, g, mate);
   unsigned hi = 0, hi_prev = 0;
   if (!gb.sync(G, 0, eflags, &fail_sh, &hi_sh, &hi)) return;
   hi_prev = hi;
@@ -569,7 +638,7 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
           if (__syncthreads_or(mi >= 0) == 0) { fin = 1; ++lr; break; }
           auto app = [&](int2 v) { dn[atomicAdd(&s_nn, 1)] = v; };
           const int m1 = (mi >= 0 && stamp[mj] != lr) ? mj : -1;
-          hem_phase_b<false>(mi, m1, lr, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc, app);
+          hem_phase_b<false, ELL>(mi, m1, lr, g, mate, pick, stamp, s_c, &s_nc, app);
           __syncthreads();
           lnd = s_nn;
           __syncthreads();  // every thread has read s_nn before the next round resets it
@@ -662,13 +731,12 @@ __global__ void __launch_bounds__(HEM_COOP_THREADS)
     int added = 0;
     if (regs) {
       const int m1 = (mi >= 0 && __ldcg(&stamp[mj]) != r) ? mj : -1;
-      hem_phase_b<true>(mi, m1, r, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc, app);
+      hem_phase_b<true, ELL>(mi, m1, r, g, mate, pick, stamp, s_c, &s_nc, app);
       added = nl.flush();
     } else {
       for (int t0 = blockIdx.x * blockDim.x; t0 < nm; t0 += gstride) {
         const int t = t0 + threadIdx.x;
-        hem_phase_b<true>(t < nm ? __ldcg(&M[t]) : -1, -1, r, rp, ci, w, tie_larger, mate, pick, stamp, s_c, &s_nc,
-                          app);
+        hem_phase_b<true, ELL>(t < nm ? __ldcg(&M[t]) : -1, -1, r, g, mate, pick, stamp, s_c, &s_nc, app);
         added += nl.flush();
       }
     }
@@ -1129,6 +1197,7 @@ struct Scratch {
   int *flag = nullptr, *id = nullptr, *tiles = nullptr, *cnt = nullptr, *count = nullptr;
   int *coop = nullptr;  // counters and barrier of the cooperative rounds (HEM_COOP_INTS)
   int2 *la = nullptr, *lb = nullptr;  // the cooperative rounds' lists of (node, pick)
+  int32_t *nb = nullptr;              // sorted neighbour table (n x HEM_ELL)
   int *host = nullptr;  // pinned: [0] pairs, [1] frontier, [2] scan total
   size_t cap_n = 0, cap_nnz = 0;
 };
@@ -1161,6 +1230,7 @@ amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
   AMG_TRY(pool_alloc((void **)&s.coop, sizeof(int) * HEM_COOP_INTS, st));
   AMG_TRY(pool_alloc((void **)&s.la, sizeof(int2) * (n + AMG_PAD), st));
   AMG_TRY(pool_alloc((void **)&s.lb, sizeof(int2) * (n + AMG_PAD), st));
+  AMG_TRY(pool_alloc((void **)&s.nb, sizeof(int32_t) * ((size_t)n * HEM_ELL + AMG_PAD), st));
   s.host = (int *)pinned_small_alloc();
   if (!s.host) return AMG_ERR_OOM;
   s.cap_n = n;
@@ -1169,7 +1239,8 @@ amg_status scratch_alloc(Scratch &s, int n, long long nnz, cudaStream_t st) {
 }
 
 void scratch_free(Scratch &s, cudaStream_t st) {
-  void *ps[] = {s.w, s.mate, s.pick, s.fa, s.fb, s.first, s.flag, s.id, s.count, s.tiles, s.cnt, s.coop, s.la, s.lb};
+  void *ps[] = {s.w, s.mate, s.pick, s.fa, s.fb, s.first, s.flag, s.id, s.count, s.tiles, s.cnt, s.coop, s.la, s.lb,
+                s.nb};
   for (void *p : ps) pool_free(p, st);
   pinned_small_free(s.host);
   s = Scratch();
@@ -1196,7 +1267,10 @@ int hem_coop_blocks(amg_hierarchy *h) {
     cudaGetLastError();
     return 0;
   }
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hem_coop, HEM_COOP_THREADS, 0) != cudaSuccess ||
+  int occ2 = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hem_coop<false>, HEM_COOP_THREADS, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_hem_coop<true>, HEM_COOP_THREADS, 0) != cudaSuccess ||
+      occ2 < 1 ||
       occ < 1) {
     cudaGetLastError();
     return 0;
@@ -1225,19 +1299,29 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   bool finished = false, frontier_rounds = true;
   const int coop_blocks = hem_coop_blocks(h);
   if (coop_blocks > 0) {
-    // every round in one cooperative launch
+    // every round in one cooperative launch; the sorted neighbour table when
+    // every node has at most HEM_ELL neighbours
     int *ctr = S.coop;
     AMG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int) * HEM_COOP_INTS, st));
+    unsigned *too_wide = (unsigned *)(S.cnt + 60);
+    AMG_CUDA(cudaMemsetAsync(too_wide, 0, sizeof(unsigned), st));
+    k_hem_ell<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, S.w, tie_larger, S.nb, too_wide);
+    count_launch();
+    AMG_CUDA(cudaMemcpyAsync(S.host + 60, too_wide, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA(cudaStreamSynchronize(st));
+    const bool ell = S.host[60] == 0;
     int a_n = n, a_tie = tie_larger, a_max = round_cap;
     const int32_t *a_rp = in.rp, *a_ci = in.ci;
     const double *a_w = S.w;
     int32_t *a_mate = S.mate, *a_pick = S.pick, *a_m = S.first;
     int2 *a_da = S.la, *a_db = S.lb;
     int *a_stamp = S.flag;
+    const int32_t *a_nb = S.nb;
     unsigned *a_ef = h->eflags;
-    void *args[] = {&a_n, &a_rp, &a_ci, &a_w, &a_tie, &a_mate, &a_pick, &a_stamp, &a_da, &a_db, &a_m,
+    void *args[] = {&a_n, &a_rp, &a_ci, &a_w, &a_tie, &a_nb, &a_mate, &a_pick, &a_stamp, &a_da, &a_db, &a_m,
                     &ctr, &a_ef, &a_max};
-    AMG_CUDA(cudaLaunchCooperativeKernel((void *)k_hem_coop, coop_blocks, HEM_COOP_THREADS, args, 0, st));
+    AMG_CUDA(cudaLaunchCooperativeKernel(ell ? (void *)k_hem_coop<true> : (void *)k_hem_coop<false>, coop_blocks,
+                                         HEM_COOP_THREADS, args, 0, st));
     count_launch();
     AMG_CUDA(cudaMemcpyAsync(S.host, ctr + HEM_COOP_OUT, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     AMG_CUDA(cudaStreamSynchronize(st));

@@ -1781,6 +1781,7 @@ extern "C" amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream) {
                   : h->prm.precision == AMG_FP32 ? tune_levels<float, float>(h, s)
                                                  : tune_levels<float, __half>(h, s);
   reset_graphs(h);
+  h->batch_desc_stale = 1;
   AMG_CUDA(cudaStreamSynchronize(s));
   return st;
 }
@@ -1817,6 +1818,7 @@ extern "C" amg_status amg_level_set_operator_form(amg_hierarchy *h, int level, i
   if (on && !l.op_avail) return AMG_ERR_UNSUPPORTED;
   l.op_on = on ? 1 : 0;
   reset_graphs(h);
+  h->batch_desc_stale = 1;
   return AMG_OK;
 }
 

@@ -1,6 +1,14 @@
-"""Continuous-batching server: every request converges, each result is the same
-(bitwise) alone and in the mix, admission respects the memory budget, and the
-hierarchy cache is reused."""
+"""Continuous-batching server: every request converges to a true relative
+residual of at most 1e-8, its solution agrees with the FP64 oracle's, each
+result is the same (bitwise) alone and in the mix, admission respects the
+memory budget, and the hierarchy cache is reused.
+
+Error against the oracle: the server runs an FP32 V-cycle inside FP64
+flexible PCG and stops at ||b - A x|| <= 1e-8 ||b||, so its error against
+the exact solution is at most cond(A) 1e-8; for these systems (up to 60,000
+unknowns, cond(A) up to a few 1e4) that is a few 1e-4 at worst, and the
+observed errors against the oracle's solution to 1e-12 are far smaller.  The
+test asserts 1e-5."""
 import numpy as np
 import pytest
 
@@ -8,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 from paper_2007_00056_gb300 import amg  # noqa: E402
 from paper_2007_00056_gb300 import serving as S  # noqa: E402
 from paper_2007_00056_gb300 import workloads as W  # noqa: E402
@@ -20,14 +29,20 @@ def _stream(count=24, n_hi=6e4):
 
 def test_server_mix_equals_alone_and_converges():
     reqs, systems = _stream()
-    srv = S.SolveServer(workers=4, small_max_n=20000)
+    srv = S.SolveServer(workers=4, small_max_n=20000, batch_classes=(5000,))
     mixed, wall = S.serve_stream(srv, reqs, systems)
     srv.close()
     assert {r.path for r in mixed} == {"batch", "single"}, "the stream should exercise both paths"
-    for r in mixed:
-        assert r.status == amg.AMG_OK and r.rel_res_true <= 1.05e-8, r
+    worst = 0.0
+    for req, s, r in zip(reqs, systems, mixed):
+        assert r.status == amg.AMG_OK and r.rel_res_true <= 1e-8, r
+        x_o, info_o = O.Hierarchy(s.rp, s.ci, s.val).pcg(s.b, rtol=1e-12, flexible=True)
+        err = np.linalg.norm(r.x - x_o) / np.linalg.norm(x_o)
+        worst = max(worst, err)
+        assert err < 1e-5, (req.rid, s.n, err)
+    print(f"largest relative error of a served solution against the FP64 oracle: {worst:.2e}")
     # each request alone, through a fresh server
-    alone = S.SolveServer(workers=1, small_max_n=20000)
+    alone = S.SolveServer(workers=1, small_max_n=20000, batch_classes=(5000,))
     for req, s, r in zip(reqs, systems, mixed):
         alone.submit(req.rid, s.rp, s.ci, s.val, s.b, arrival=0.0)
         a = alone.wait([req.rid])[0]
