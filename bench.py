@@ -39,7 +39,12 @@ HBM_SPEC_GBS = 7900.0  # GB300 HBM3e nominal; the measured copy bandwidth is the
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel, keyed by profiler kind at level 0 of the 256^3 system (scaled from
 # the capture named in profiles/ by rows); absent once the kernel changes
-DRAM_BYTES_PER_LAUNCH = {}
+DRAM_BYTES_PER_LAUNCH = {
+    # k_op_residual<1, double, double> at level 0 of anisotropic3d_128: 213,434,624 bytes
+    # (profiles/level_kernels_anisotropic3d_128.md), times 8.0217, the ratio of the
+    # launch's algorithmic bytes at 256^3 and at 128^3
+    ("op_residual", 0): 213434624 * 8.0217,
+}
 # DRAM bytes per launch of the coarse CG on the 128^3 lognormal coarsest
 # level (profiles/coarse_cg_lognormal3d_128.md): its matrix and vectors live
 # in shared memory, so these bytes stand for the solve's HBM traffic
@@ -504,6 +509,58 @@ def coarse_cg_roofline(table, level_nnz):
             "us_per_iteration": ms * 1e3 / iters}
 
 
+def run_residency(dev, x64_main=None):
+    """The hybrid CPU/GPU-CI placement of Sec. 3.1.1 on the 256^3 system (FP64
+    flexible PCG): the level matrices in pinned host memory, read over the
+    host-device link (mapped) or copied one cycle visit ahead into two device
+    buffers (staged), against the resident hierarchy.  Per mode: device and
+    host bytes of the hierarchy, the solve time (setup excluded: the
+    placement changes after setup), iterations, whether x equals the resident
+    solution bit for bit, and the bytes the staging copied per solve."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    s3 = W.config_anisotropic3d_256()
+    rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s3.rp, s3.ci, s3.val, s3.b))
+    h = amg.amg_setup(rp, ci, val, amg.amg_default_params())
+    del rp, ci, val
+    stream = torch.cuda.current_stream()
+    lines = []
+    x_res = None
+    for mode, first in ((amg.AMG_RESIDENT, 0), (amg.AMG_HOST_STAGED, 1), (amg.AMG_HOST_STAGED, 0),
+                        (amg.AMG_HOST_MAPPED, 1), (amg.AMG_HOST_MAPPED, 0)):
+        amg.amg_set_residency(h, mode, first)
+        x = torch.zeros_like(b)
+        amg.pcg_solve(h, b, x, rtol=RTOL, flexible=True)  # warm-up (prefetch state, page mappings)
+        mem0 = amg.amg_memory_info(h)
+        x.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info = amg.pcg_solve(h, b, x, rtol=RTOL, flexible=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mem = amg.amg_memory_info(h)
+        if x_res is None:
+            x_res = x.clone()
+        ms = e0.elapsed_time(e1)
+        copied = mem["copied_bytes"] - mem0["copied_bytes"]
+        lines.append({"mode": ["resident", "host_mapped", "host_staged"][mode], "first_level": first,
+                      "device_bytes": mem["device_bytes"], "host_bytes": mem["host_bytes"],
+                      "staging_bytes": mem["staging_bytes"], "solve_ms": ms, "iterations": info.iterations,
+                      "status": amg.status_string(info.status), "rel_res_true": info.rel_res_true,
+                      "x_bitwise_equal_resident": bool(torch.equal(x.view(torch.int64), x_res.view(torch.int64))),
+                      "staged_bytes_per_solve": copied,
+                      "staged_gbs": copied / (ms * 1e-3) / 1e9 if copied else None})
+    amg.amg_set_residency(h, amg.AMG_RESIDENT)
+    h.close()
+    del b
+    torch.cuda.empty_cache()
+    return {"system": "anisotropic3d_256 FP64 flexible PCG", "lines": lines}
+
+
 def run_configs(dev, peak, x64_main=None):
     """The other workloads of the method, measured on this GPU: the 256^3
     anisotropic system in both mixed-precision forms (flexible PCG; error
@@ -846,7 +903,9 @@ def main():
     for r in table:
         if r["level"] == 0 and r["kind"] in HBM_KERNEL_KINDS and r["ms"] > 0:
             g = r["bytes"] / (r["ms"] * 1e-3) / 1e9
-            hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak, "frac_of_spec": g / HBM_SPEC_GBS})
+            hbm_level0.append({"kernel": f"{r['kind']}@0", "gbs": g, "frac": g / peak, "frac_of_spec": g / HBM_SPEC_GBS,
+                               "bytes_per_launch": r["bytes"] / r["launches"],
+                               "traffic": DRAM_BYTES_PER_LAUNCH.get((r["kind"], 0))})
     kernels = [dict(kernel=f"{r['kind']}@{r['level']}", ms_per_step=r["ms"] / args.profile_steps,
                     launches_per_step=r["launches"] / args.profile_steps,
                     gbs=(r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else 0.0) for r in table[:14]]
@@ -881,9 +940,10 @@ def main():
     e2e_value = job_throughput(e2e_steps, world, e2e_ms)
     del d_rp, d_ci, d_val, d_b, h_rp, h_ci, h_val
 
-    configs = cycles = complexity = scaled = None
+    configs = cycles = complexity = scaled = residency = None
     if rank == 0 and world == 1 and not args.no_configs:
         configs = run_configs(dev, peak, x_main)
+        residency = run_residency(dev)
         s2 = W.config_lognormal3d_128()
         cycles = run_cycles(dev, s2)
         complexity = run_complexity(dev)
@@ -918,7 +978,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
             "configs_measured": configs, "cycles": cycles, "complexity": complexity,
-            "option_scaled_weight": scaled, "serving": serving,
+            "option_scaled_weight": scaled, "host_resident_levels": residency, "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

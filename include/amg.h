@@ -116,7 +116,12 @@ typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
  *                Algorithm 1 (x = omega D^-1 f is never stored), in two
  *                matrix passes of which the second is over the smaller A P.
  *                Costs about one more copy of the level matrices in device
- *                memory.  0: only the explicit sweeps. */
+ *                memory.  0: only the explicit sweeps.
+ *   dense_max    largest coarsest level that AMG_COARSE_AUTO solves with the
+ *                dense inverse (0, the default: coarse_max).  A value above
+ *                coarse_max keeps the stop size small while a hierarchy whose
+ *                coarsening stalled a little above it still gets the direct
+ *                coarsest solve instead of the CG. */
 typedef struct {
   int passes;
   int max_levels;
@@ -131,6 +136,7 @@ typedef struct {
   int tie_break;
   int edge_weight;
   int operator_form;
+  int dense_max;
 } amg_params;
 
 /* Result of a Krylov solve.  iterations counts completed iterations (a
@@ -365,12 +371,50 @@ amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, c
                                  const double *d_val, const double *d_f, double *d_x, amg_stream_t stream,
                                  int *iterations);
 
+/* Where the level matrices live during the solve phase (Sec. 3.1.1, the hybrid
+ * CPU/GPU-CI algorithm: a cycle works on one level at a time, so the matrices
+ * of the other levels can wait in host memory and be copied to the GPU when
+ * the cycle reaches them, the copy overlapping the current level's kernels).
+ *   AMG_RESIDENT     everything in device memory (the state after amg_setup).
+ *   AMG_HOST_MAPPED  for levels first_level..L-1, every array whose length is
+ *                    the level's number of nonzeros (column indices and values
+ *                    of A, of its FP32 / FP16 copies, of C and of Q) moves to
+ *                    pinned host memory and the kernels read it there, over
+ *                    the host-device link (NVLink-C2C on GB300).
+ *   AMG_HOST_STAGED  the same arrays in pinned host memory, but each cycle
+ *                    visit of such a level reads its matrix from one of two
+ *                    device buffers that a second stream fills with
+ *                    cudaMemcpyAsync; the copy for the visit predicted next
+ *                    (V-cycle order) runs while the current visit computes,
+ *                    and an unpredicted visit (W- and F-cycles) waits for its
+ *                    own copy.  Level 0's A stays in device memory (the outer
+ *                    Krylov method multiplies by it every iteration).  Solves
+ *                    run without CUDA graphs in this mode.
+ * Arrays of length n (row pointers, diagonals, aggregate maps, vectors) and
+ * the coarsest level never move.  Results are bitwise the same in every mode.
+ * first_level must be in [0, L) for the host modes (ignored for
+ * AMG_RESIDENT).  Synchronises the hierarchy's latest stream and `stream`;
+ * errors: INVALID_ARG, OOM (pinned host or device memory; the hierarchy is
+ * left resident), UNSUPPORTED (no unified addressing), CUDA.  amg_autotune
+ * returns UNSUPPORTED while levels are in host memory: tune first. */
+typedef enum { AMG_RESIDENT = 0, AMG_HOST_MAPPED = 1, AMG_HOST_STAGED = 2 } amg_residency;
+amg_status amg_set_residency(amg_hierarchy *h, int residency, int first_level, amg_stream_t stream);
+
+/* Memory of h (any output may be NULL): device bytes it owns (staging buffers
+ * included), pinned host bytes of its host-resident arrays, bytes of the two
+ * staging buffers, and bytes copied host-to-device by the staging since the
+ * last amg_set_residency. */
+amg_status amg_memory_info(const amg_hierarchy *h, uint64_t *device_bytes, uint64_t *host_bytes,
+                           uint64_t *staging_bytes, uint64_t *copied_bytes);
+
 /* Frees every device allocation of h (NULL is a no-op).  Synchronises the
  * device work of h first. */
 void amg_destroy(amg_hierarchy *h);
 
 /* Text of the last CUDA runtime error behind an AMG_ERR_CUDA or AMG_ERR_OOM
- * returned to the calling thread ("no CUDA error" if none). */
+ * returned to the calling thread, with the library source file and line of
+ * the call that reported it where known ("no CUDA error" if none).  The text
+ * stays valid until the thread's next call into the library. */
 const char *amg_last_cuda_error(void);
 
 /* Static English text for a status code. */

@@ -30,6 +30,7 @@ AMG_COARSE_AUTO, AMG_COARSE_DENSE, AMG_COARSE_CG = 0, 1, 2
 AMG_CYCLE_V, AMG_CYCLE_W, AMG_CYCLE_F = 0, 1, 2
 AMG_TIE_SMALLER, AMG_TIE_LARGER = 0, 1
 AMG_WEIGHT_ABS, AMG_WEIGHT_SCALED = 0, 1
+AMG_RESIDENT, AMG_HOST_MAPPED, AMG_HOST_STAGED = 0, 1, 2
 
 # every symbol include/amg.h declares
 EXPORTS = (
@@ -38,7 +39,7 @@ EXPORTS = (
     "amg_kernel_launches", "amg_profile_enable", "amg_profile_reset", "amg_profile_read",
     "amg_coarse_cg_noalloc", "amg_autotune", "amg_level_config", "amg_level_set_config", "amg_batch_pcg",
     "amg_selftest_wait_timeout", "amg_selftest_convert", "amg_last_cuda_error", "amg_coarse_cg_cluster_size",
-    "amg_level_operator_form", "amg_level_set_operator_form",
+    "amg_level_operator_form", "amg_level_set_operator_form", "amg_set_residency", "amg_memory_info",
 )
 KERNEL_KINDS = ("jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
                 "coarse_cg", "cast", "krylov_spmv", "krylov_vec", "op_residual", "op_post")
@@ -71,6 +72,7 @@ class amg_params(C.Structure):
         ("tie_break", C.c_int),
         ("edge_weight", C.c_int),
         ("operator_form", C.c_int),
+        ("dense_max", C.c_int),
     ]
 
 
@@ -137,6 +139,9 @@ def lib(build_if_missing: bool = False):
             l.amg_coarse_cg_cluster_size.argtypes = [vp]
             l.amg_level_operator_form.argtypes = [vp, i32]
             l.amg_level_set_operator_form.argtypes = [vp, i32, i32]
+            l.amg_set_residency.argtypes = [vp, i32, i32, vp]
+            u64p = C.POINTER(C.c_uint64)
+            l.amg_memory_info.argtypes = [vp, u64p, u64p, u64p, u64p]
             _lib = l
     return _lib
 
@@ -400,6 +405,23 @@ def amg_level_set_operator_form(h: Hierarchy, level: int, on: bool) -> None:
     st = lib().amg_level_set_operator_form(h.handle, int(level), int(bool(on)))
     if st != AMG_OK:
         raise AmgError(st, "amg_level_set_operator_form")
+
+
+def amg_set_residency(h: Hierarchy, residency: int, first_level: int = 0, stream=None) -> None:
+    """Moves the matrix arrays of levels first_level..L-1 to pinned host memory
+    (AMG_HOST_MAPPED, AMG_HOST_STAGED) or everything back (AMG_RESIDENT)."""
+    st = lib().amg_set_residency(h.handle, int(residency), int(first_level), _stream(stream))
+    if st != AMG_OK:
+        raise AmgError(st, "amg_set_residency")
+
+
+def amg_memory_info(h: Hierarchy) -> dict:
+    """Device bytes, pinned host bytes, staging bytes and bytes copied by the staging."""
+    v = [C.c_uint64() for _ in range(4)]
+    st = lib().amg_memory_info(h.handle, *[C.byref(x) for x in v])
+    if st != AMG_OK:
+        raise AmgError(st, "amg_memory_info")
+    return dict(zip(("device_bytes", "host_bytes", "staging_bytes", "copied_bytes"), (x.value for x in v)))
 
 
 def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible: bool = False, stream=None):

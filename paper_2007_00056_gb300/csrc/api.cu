@@ -1,5 +1,6 @@
 // api.cu -- small C-ABI entry points and host helpers shared by the library.
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -51,11 +52,25 @@ amg_status prof_flush(amg_hierarchy *h) {
 
 static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
 
+static thread_local const char *g_last_cuda_file = nullptr;
+static thread_local int g_last_cuda_line = 0;
+
 amg_status amg_cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return AMG_OK;
   g_last_cuda_error = e;
+  g_last_cuda_file = nullptr;
   if (e == cudaErrorMemoryAllocation) return AMG_ERR_OOM;
   return AMG_ERR_CUDA;
+}
+
+amg_status amg_cuda_status_at(cudaError_t e, const char *file, int line) {
+  const amg_status s = amg_cuda_status(e);
+  if (s != AMG_OK) {
+    const char *base = strrchr(file, '/');
+    g_last_cuda_file = base ? base + 1 : file;
+    g_last_cuda_line = line;
+  }
+  return s;
 }
 
 namespace {
@@ -77,6 +92,11 @@ cudaMemPool_t lib_pool() {
     if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) { cudaGetLastError(); return nullptr; }
     uint64_t keep = UINT64_MAX;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // a block freed on one stream is not handed to another stream by making
+    // that stream wait for the first: setups on different streams stay
+    // independent (the pool takes fresh memory instead)
+    int no = 0;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     g_pool[dev] = pool;
   }
   return g_pool[dev];
@@ -96,6 +116,11 @@ amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s) {
 
 void pool_free(void *p, cudaStream_t s) {
   if (p && cudaFreeAsync(p, s) != cudaSuccess) cudaGetLastError();
+}
+
+void pool_trim() {
+  cudaMemPool_t pool = lib_pool();
+  if (pool && cudaMemPoolTrimTo(pool, 0) != cudaSuccess) cudaGetLastError();
 }
 
 // Small pinned host buffers (<= 256 bytes) for device-to-host status reads,
@@ -127,7 +152,7 @@ void pinned_small_free(void *p) {
 
 amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes) {
   AMG_TRY(pool_alloc(p, bytes, h->stream));
-  h->allocs.push_back(*p);
+  h->allocs.push_back({*p, bytes});
   return AMG_OK;
 }
 
@@ -155,11 +180,17 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->tie_break = AMG_TIE_SMALLER;
   p->edge_weight = AMG_WEIGHT_ABS;
   p->operator_form = 1;
+  p->dense_max = 0;
   return AMG_OK;
 }
 
 extern "C" const char *amg_last_cuda_error(void) {
-  return g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(g_last_cuda_error);
+  static thread_local char text[256];
+  if (g_last_cuda_error == cudaSuccess) return "no CUDA error";
+  if (!g_last_cuda_file) return cudaGetErrorString(g_last_cuda_error);
+  snprintf(text, sizeof(text), "%s (at %s:%d)", cudaGetErrorString(g_last_cuda_error), g_last_cuda_file,
+           g_last_cuda_line);
+  return text;
 }
 
 extern "C" const char *amg_status_string(amg_status s) {
@@ -182,6 +213,7 @@ extern "C" int amg_num_levels(const amg_hierarchy *h) { return h ? h->L + 1 : -1
 
 extern "C" amg_status amg_level_info(const amg_hierarchy *h, int level, int *n, int64_t *nnz, int32_t *d_agg_out,
                                      amg_stream_t stream) {
+  clear_stale_cuda_error();
   if (!h || level < 0 || level > h->L) return AMG_ERR_INVALID_ARG;
   if (d_agg_out && level == h->L) return AMG_ERR_INVALID_ARG;
   const Level &l = h->lev[level];
@@ -197,14 +229,15 @@ extern "C" amg_status amg_level_info(const amg_hierarchy *h, int level, int *n, 
 
 extern "C" amg_status amg_export_level(const amg_hierarchy *h, int level, int32_t *d_row_ptr, int32_t *d_col,
                                        double *d_val, amg_stream_t stream) {
+  clear_stale_cuda_error();
   if (!h || level < 0 || level > h->L || !d_row_ptr) return AMG_ERR_INVALID_ARG;
   const Level &l = h->lev[level];
   if (l.nnz > 0 && (!d_col || !d_val)) return AMG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   AMG_CUDA(cudaMemcpyAsync(d_row_ptr, l.rp, sizeof(int32_t) * (l.n + 1), cudaMemcpyDeviceToDevice, s));
   if (l.nnz > 0) {
-    AMG_CUDA(cudaMemcpyAsync(d_col, l.ci, sizeof(int32_t) * l.nnz, cudaMemcpyDeviceToDevice, s));
-    AMG_CUDA(cudaMemcpyAsync(d_val, l.val, sizeof(double) * l.nnz, cudaMemcpyDeviceToDevice, s));
+    AMG_CUDA(cudaMemcpyAsync(d_col, l.ci, sizeof(int32_t) * l.nnz, cudaMemcpyDefault, s));
+    AMG_CUDA(cudaMemcpyAsync(d_val, l.val, sizeof(double) * l.nnz, cudaMemcpyDefault, s));
   }
   AMG_CUDA(cudaStreamSynchronize(s));
   return AMG_OK;
@@ -223,7 +256,8 @@ extern "C" void amg_destroy(amg_hierarchy *h) {
   prof_flush(h);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   // stream-ordered frees back into the library pool, on the hierarchy's own stream
-  for (void *p : h->allocs) pool_free(p, h->cap_stream);
+  residency_release(h);
+  for (auto &a : h->allocs) pool_free(a.first, h->cap_stream);
   pinned_small_free(h->st_host);
   pinned_small_free(h->eflags_host);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);

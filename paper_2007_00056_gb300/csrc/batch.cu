@@ -375,6 +375,7 @@ amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **o
 extern "C" amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const double *const *d_b,
                                     double *const *d_x, double rtol, int max_iter, int flexible,
                                     amg_stream_t stream, amg_solve_info *infos) {
+  clear_stale_cuda_error();
   if (nsys <= 0 || !hs || !d_b || !d_x || !(rtol >= 0.0) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   int prec = -1;

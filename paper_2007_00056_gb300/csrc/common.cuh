@@ -11,6 +11,8 @@
 //             vectors.
 //   Krylov:   level-0 FP64 work vectors and a device-resident scalar block
 //             (KState) so an iteration runs without host round trips.
+// After amg_set_residency, the matrix arrays (column indices and values) of
+// the chosen levels live in pinned host memory instead (residency.cu).
 // Every CSR array is padded by AMG_PAD elements so that vector loads of a
 // tile never leave the allocation.
 #pragma once
@@ -83,6 +85,8 @@ struct Level {
   int64_t qnnz = 0;
   int op_avail = 0;          // C, Q and wd exist for this level
   int op_on = 0;             // zero-guess visits use them
+  int host = 0;              // its matrix arrays are in pinned host memory (residency.cu)
+  int st_cap_dev = 0;        // st_cap while the level was in device memory
 };
 
 // Kernel kinds of the per-kernel profiler (id = kind * AMG_MAX_LEVELS + level).
@@ -154,7 +158,11 @@ struct amg_hierarchy {
   KState *st_host = nullptr; // pinned host mirror
   unsigned *eflags = nullptr;   // device error bits
   unsigned *eflags_host = nullptr;
-  std::vector<void *> allocs;
+  std::vector<std::pair<void *, size_t>> allocs;       // device memory owned, with sizes
+  std::vector<std::pair<void *, size_t>> host_allocs;  // pinned host memory owned (moved level arrays)
+  int residency = 0;         // amg_residency
+  int res_first = 0;         // first level whose matrix arrays are in host memory
+  struct Stager *stg = nullptr;  // two-slot staging of host-resident levels (AMG_HOST_STAGED)
   cudaStream_t stream = nullptr;       // stream of amg_setup (stream-ordered allocations)
   cudaStream_t last_stream = nullptr;  // stream of the latest call that used the hierarchy
   cudaStream_t cap_stream = nullptr;
@@ -194,11 +202,22 @@ struct LaunchScope {
 // Host helpers (defined in api.cu)
 // ---------------------------------------------------------------------------
 amg_status amg_cuda_status(cudaError_t e);
+// Clears the calling thread's last CUDA error at a public entry point, so that
+// the checks after this call's own launches report this call's errors and not
+// an error some other code of the thread left behind.
+static inline void clear_stale_cuda_error() { (void)cudaGetLastError(); }
+// The same, recording the library source location of the failing call for
+// amg_last_cuda_error.
+amg_status amg_cuda_status_at(cudaError_t e, const char *file, int line);
 amg_status hier_alloc(amg_hierarchy *h, void **p, size_t bytes);
+// Records device memory allocated from the pool as owned by the hierarchy.
+static inline void hier_adopt(amg_hierarchy *h, void *p, size_t bytes) { h->allocs.push_back({p, bytes}); }
 // Stream-ordered allocation from the library's own device memory pool (freed
 // memory stays in the pool for the next setup; no implicit device sync).
 amg_status pool_alloc(void **p, size_t bytes, cudaStream_t s);
 void pool_free(void *p, cudaStream_t s);
+// Returns the pool's unused blocks to the device.
+void pool_trim();
 // Recycled pinned host buffers of 256 bytes (status and counter read-backs).
 void *pinned_small_alloc();
 void pinned_small_free(void *p);
@@ -210,8 +229,21 @@ void pinned_small_free(void *p);
 #define AMG_CUDA(x)                             \
   do {                                          \
     cudaError_t _e = (x);                       \
-    if (_e != cudaSuccess) return amg_cuda_status(_e); \
+    if (_e != cudaSuccess) return amg_cuda_status_at(_e, __FILE__, __LINE__); \
   } while (0)
+
+// Host-resident levels (residency.cu).  A cycle visit of level k reads one
+// matrix: A (explicit sweeps), C (residual-operator form, descending) or Q
+// (residual-operator form, ascending).  With AMG_HOST_STAGED, stage_acquire
+// returns the level with that matrix's host-resident arrays replaced by a
+// device staging buffer (the stream waits for the copy), and stage_release,
+// called once the visit's kernels are enqueued, frees the buffer for the
+// copy of a later visit and starts the copy of the predicted next one.
+enum StageSet { SET_A = 0, SET_C = 1, SET_Q = 2, SET_NONE = 3 };
+static inline bool stage_on(const amg_hierarchy *h, int k) { return h->stg != nullptr && h->lev[k].host; }
+Level stage_acquire(amg_hierarchy *h, int k, int set, cudaStream_t s);
+void stage_release(amg_hierarchy *h, int k, bool descending, cudaStream_t s);
+void residency_release(amg_hierarchy *h);  // frees host memory and the stager (amg_destroy)
 
 static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline int grid_for(long long n, int per_block, int max_blocks = AMG_MAX_BLOCKS) {

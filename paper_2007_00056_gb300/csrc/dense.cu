@@ -459,6 +459,78 @@ __global__ void __launch_bounds__(256) k_bgj_update(int m, int k0, int w, T *__r
   }
 }
 
+// Step 3 in FP32 for m a multiple of 4: the same products in the same order
+// per entry (c = 0..w-1, one FMA each), with the operands read from shared
+// memory four at a time.  Block: 128 x 128 outputs; thread (ty, tx) of 16 x 16
+// owns rows {4 ty + a, 64 + 4 ty + a} and columns {4 tx + b, 64 + 4 tx + b}
+// (a, b = 0..3), so each k step reads two float4 of M_IK and two of R_KJ for
+// 64 FMAs.  Rows of the shared tiles are 132 floats apart: 16-byte aligned,
+// and the transposing stores of M_IK (lanes on consecutive rows) hit distinct
+// banks.
+#define BGJ4_S 132
+#define BGJ4_SMEM (2 * sizeof(float) * BGJ_W * BGJ4_S)
+
+__global__ void __launch_bounds__(256) k_bgj_update4(int m, int k0, int w, float *__restrict__ M,
+                                                     const float *__restrict__ R) {
+  extern __shared__ __align__(16) unsigned char bgj4_smem[];
+  float *As = (float *)bgj4_smem;     // [c][r]: M_IK transposed
+  float *Bs = As + BGJ_W * BGJ4_S;    // [c][j]: R_KJ
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 128;
+  const int wq = w >> 2;  // w is a multiple of 4 (k0 and m are)
+  for (int idx = tid; idx < 128 * wq; idx += 256) {
+    const int r = idx & 127, cq = idx >> 7, i = i0 + r;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < m) v = *reinterpret_cast<const float4 *>(M + (size_t)i * m + k0 + 4 * cq);
+    As[(4 * cq + 0) * BGJ4_S + r] = v.x;
+    As[(4 * cq + 1) * BGJ4_S + r] = v.y;
+    As[(4 * cq + 2) * BGJ4_S + r] = v.z;
+    As[(4 * cq + 3) * BGJ4_S + r] = v.w;
+  }
+  for (int idx = tid; idx < w * 32; idx += 256) {
+    const int c = idx >> 5, jq = idx & 31, j = j0 + 4 * jq;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (j < m) v = *reinterpret_cast<const float4 *>(R + (size_t)c * m + j);
+    *reinterpret_cast<float4 *>(Bs + c * BGJ4_S + 4 * jq) = v;
+  }
+  __syncthreads();
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  for (int c = 0; c < w; ++c) {
+    const float4 a0 = *reinterpret_cast<const float4 *>(As + c * BGJ4_S + 4 * ty);
+    const float4 a1 = *reinterpret_cast<const float4 *>(As + c * BGJ4_S + 64 + 4 * ty);
+    const float4 b0 = *reinterpret_cast<const float4 *>(Bs + c * BGJ4_S + 4 * tx);
+    const float4 b1 = *reinterpret_cast<const float4 *>(Bs + c * BGJ4_S + 64 + 4 * tx);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + (a < 4 ? 4 * ty + a : 64 + 4 * ty + (a - 4));
+    if (i >= m || (i >= k0 && i < k0 + w)) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = j0 + 64 * h + 4 * tx;  // four columns, all inside or all outside K
+      if (j >= m || (j >= k0 && j < k0 + w)) continue;
+      float4 *p = reinterpret_cast<float4 *>(M + (size_t)i * m + j);
+      float4 v = *p;
+      v.x = v.x - acc[a][4 * h + 0];
+      v.y = v.y - acc[a][4 * h + 1];
+      v.z = v.z - acc[a][4 * h + 2];
+      v.w = v.w - acc[a][4 * h + 3];
+      *p = v;
+    }
+  }
+}
+
 // Step 4: M_IK <- -M_IK P^-1 for I outside K, M_KK <- P^-1.  Block: 64 rows;
 // thread: one row, 16 of the columns.
 template <typename T>
@@ -505,6 +577,10 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   const size_t smem = sizeof(T) * (size_t)BGJ_W * (TL::BM + TL::BN);
   AMG_CUDA(cudaFuncSetAttribute(k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the float4 form of the update when rows are 16-byte aligned
+  const bool vec4 = sizeof(T) == sizeof(float) && m % 4 == 0;
+  if (vec4)
+    AMG_CUDA(cudaFuncSetAttribute(k_bgj_update4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BGJ4_SMEM));
   const size_t tsmem = BGJ_TILE_SMEM(T);
   AMG_CUDA(cudaFuncSetAttribute(k_bgj_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
   AMG_CUDA(cudaFuncSetAttribute(k_bgj_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
@@ -521,7 +597,10 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
     const int w = std::min(BGJ_W, m - k0);
     k_bgj_diag<T><<<1, BGJ_W * 16, 0, st>>>(m, k0, w, out, Pinv, h->eflags);
     k_bgj_rows<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv, R);
-    k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
+    if (vec4)
+      k_bgj_update4<<<ug, 256, BGJ4_SMEM, st>>>(m, k0, w, (float *)out, (const float *)R);
+    else
+      k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
     k_bgj_cols<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv);
     count_launch(4);
   }

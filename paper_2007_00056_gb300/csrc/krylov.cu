@@ -529,7 +529,9 @@ amg_status get_graph(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long l
 amg_status run_iterations(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long long *nodes, cudaStream_t s) {
   // a graph is captured once the hierarchy is reused: for a single solve the
   // capture and instantiation cost more than the launches they save
-  const bool use_graph = !h->prof.on && (*exec != nullptr || h->solves >= 1);
+  // (not while host-resident levels are staged: each visit's copies are
+  // issued from the host with the prediction of the next one)
+  const bool use_graph = !h->prof.on && h->stg == nullptr && (*exec != nullptr || h->solves >= 1);
   h->solves += 1;
   if (use_graph) AMG_TRY(get_graph(h, fn, exec, nodes));
   // enqueue a few iterations between host checks; kernels after convergence are no-ops
@@ -636,6 +638,7 @@ void reset_graphs(amg_hierarchy *h) {
 
 extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol, int max_iter,
                                 int flexible, amg_stream_t stream, amg_solve_info *info) {
+  clear_stale_cuda_error();
   if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;
@@ -664,6 +667,7 @@ extern "C" amg_status pcg_solve(const amg_hierarchy *hc, const double *d_b, doub
 
 extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol,
                                      int max_iter, amg_stream_t stream, amg_solve_info *info) {
+  clear_stale_cuda_error();
   if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;
@@ -692,6 +696,7 @@ extern "C" amg_status bicgstab_solve(const amg_hierarchy *hc, const double *d_b,
 
 extern "C" amg_status amg_solve(const amg_hierarchy *hc, const double *d_b, double *d_x, double rtol, int max_iter,
                                 amg_stream_t stream, amg_solve_info *info) {
+  clear_stale_cuda_error();
   if (!hc || !d_b || !d_x || bad_scalar(rtol) || max_iter < 0) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;

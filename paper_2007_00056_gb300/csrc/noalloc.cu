@@ -111,6 +111,7 @@ __global__ void k_noalloc_total(int blocks, const double *__restrict__ part, dou
 extern "C" amg_status amg_coarse_cg_noalloc(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                                             const double *d_val, const double *d_f, double *d_x,
                                             amg_stream_t stream, int *iterations) {
+  clear_stale_cuda_error();
   if (iterations) *iterations = 0;
   if (n <= 0 || n > NOALLOC_MAX_N || nnz < 0 || nnz >= (1ll << 31) || !d_row_ptr || !d_f || !d_x ||
       (const void *)d_f == (const void *)d_x || (nnz > 0 && (!d_col || !d_val)))

@@ -1261,7 +1261,7 @@ amg_status check_flags(amg_hierarchy *h, cudaStream_t st) {
 
 // Blocks of the cooperative handshake kernel on this device (one per SM), or
 // 0 when the device cannot launch it cooperatively.
-int hem_coop_blocks(amg_hierarchy *h) {
+int hem_coop_blocks(amg_hierarchy *h, int n) {
   int coop = 0, occ = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) != cudaSuccess || !coop) {
     cudaGetLastError();
@@ -1275,7 +1275,10 @@ int hem_coop_blocks(amg_hierarchy *h) {
     cudaGetLastError();
     return 0;
   }
-  return h->num_sms;
+  // one block per 4096 nodes up to one per SM: a small graph's rounds take a
+  // few blocks (a cheaper grid barrier) and leave the other SMs to the work
+  // of other streams
+  return (int)std::min<long long>(h->num_sms, std::max<long long>(1, cdiv(n, 4096)));
 }
 
 // One pairwise pass on `in`: matching rounds, numbering, Galerkin product.
@@ -1297,7 +1300,7 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   const int round_cap = 4 * n + 16;  // each productive round pairs >= 1 node
   int batch = 4;                     // rounds per host check: 4, 8, then 16
   bool finished = false, frontier_rounds = true;
-  const int coop_blocks = hem_coop_blocks(h);
+  const int coop_blocks = hem_coop_blocks(h, n);
   if (coop_blocks > 0) {
     // every round in one cooperative launch; the sorted neighbour table when
     // every node has at most HEM_ELL neighbours
@@ -1422,6 +1425,7 @@ amg_status validate_params(const amg_params *p) {
   if (p->tie_break != AMG_TIE_SMALLER && p->tie_break != AMG_TIE_LARGER) return AMG_ERR_INVALID_ARG;
   if (p->edge_weight != AMG_WEIGHT_ABS && p->edge_weight != AMG_WEIGHT_SCALED) return AMG_ERR_INVALID_ARG;
   if (p->operator_form != 0 && p->operator_form != 1) return AMG_ERR_INVALID_ARG;
+  if (p->dense_max < 0) return AMG_ERR_INVALID_ARG;
   return AMG_OK;
 }
 
@@ -1486,9 +1490,11 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
     c.n = cur.n;
     c.nnz = cur.nnz;
     c.rp = cur.rp; c.ci = cur.ci; c.val = cur.val;
-    h->allocs.push_back(cur.rp); h->allocs.push_back(cur.ci); h->allocs.push_back(cur.val);
+    hier_adopt(h, cur.rp, sizeof(int32_t) * (cur.n + 1 + AMG_PAD));
+    hier_adopt(h, cur.ci, sizeof(int32_t) * (cur.nnz + AMG_PAD));
+    hier_adopt(h, cur.val, sizeof(double) * (cur.nnz + AMG_PAD));
     f.agg = agg;
-    h->allocs.push_back(agg);
+    hier_adopt(h, agg, sizeof(int32_t) * (f.n + AMG_PAD));
     memcpy(f.rounds, rounds, sizeof(rounds));
     // member lists of the level's aggregates
     AMG_TRY(hier_alloc(h, (void **)&f.mrp, sizeof(int32_t) * (c.n + 1 + AMG_PAD)));
@@ -1574,6 +1580,7 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
 extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, const int32_t *d_col,
                                 const double *d_val, const amg_params *params, amg_stream_t stream,
                                 amg_hierarchy **out) {
+  clear_stale_cuda_error();
   if (!out) return AMG_ERR_INVALID_ARG;
   *out = nullptr;
   if (n <= 0 || nnz < 0 || nnz >= (1ll << 31) - AMG_PAD || !d_row_ptr || (nnz > 0 && (!d_col || !d_val)))

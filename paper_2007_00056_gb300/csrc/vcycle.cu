@@ -1340,7 +1340,10 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
   const T omega = (T)h->prm.omega;
   const int nu_pre = h->prm.nu_pre, nu_post = h->prm.nu_post;
   const double sz = sizeof(T), szv = sizeof(V);
-  Level &l = h->lev[k];
+  // matrix arrays of a host-resident level come through a staging buffer,
+  // one visit (descending or ascending) at a time
+  const bool staged = stage_on(h, k);
+  Level l = h->lev[k];
   Level &c = h->lev[k + 1];
   T *a = S::x(l), *b = S::t(l);
   const T *dinv = S::dinv(l);
@@ -1349,10 +1352,12 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
   if (!guess && nu_pre == 1 && nu_post == 1 && l.op_on && S::cval(l)) {
     // residual-operator form: t = C f, restriction, coarse correction,
     // out = Q x_c + wd (f + t)
+    if (staged) l = stage_acquire(h, k, SET_C, s);
     {
       LaunchScope ls(h, s, PK_OP_RESIDUAL, k, BA + 2.0 * sz * l.n);
       DISPATCH_ROWS(l, k_op_residual, l.n, l.perm, l.rp, l.ci, S::cval(l), f, b, st);
     }
+    if (staged) stage_release(h, k, true, s);
     {
       LaunchScope ls(h, s, PK_RESTRICT, k, (sz + 4.0) * l.n + (sz + 4.0) * c.n + 4.0);
       k_restrict<T><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, nullptr, nullptr,
@@ -1363,13 +1368,19 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
     cycle_level<T, V>(h, k + 1, fc, nullptr, xc, kind, s, st);
     if (k + 1 < L && kind == AMG_CYCLE_W) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_W, s, st);
     if (k + 1 < L && kind == AMG_CYCLE_F) cycle_level<T, V>(h, k + 1, fc, xc, xc, AMG_CYCLE_V, s, st);
+    if (staged) l = stage_acquire(h, k, SET_Q, s);
     {
       const double BQ = (double)l.qnnz * (szv + 4.0) + 4.0 * (l.n + 1);
       LaunchScope ls(h, s, PK_OP_POST, k, BQ + 4.0 * sz * l.n + sz * c.n);
       DISPATCH_ROWS(l, k_op_post, l.n, l.perm, l.qrp, l.qci, S::qval(l), (const T *)xc, S::wd(l), f,
                     (const T *)b, out, st);
     }
+    if (staged) stage_release(h, k, false, s);
     return;
+  }
+  if (staged) {
+    l = stage_acquire(h, k, SET_A, s);
+    val = S::val(l);
   }
   // presmoothing (nu_pre >= 1 sweeps), then the residual in b
   if (!guess && nu_pre == 1 && l.fuse_pre) {
@@ -1391,6 +1402,7 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
     LaunchScope ls(h, s, PK_RESIDUAL, k, BA + 3.0 * sz * l.n);
     launch_residual<T, V>(h, l, val, a, f, b, s, st);
   }
+  if (staged) stage_release(h, k, true, s);
   // restriction f_{k+1} = P^T r
   const float *isig_c = (k + 1 < L) ? S::isig(c) : nullptr;
   {
@@ -1416,6 +1428,10 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
     k_prolong<T><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, in, l.agg, xc, sig, isig_c, out, st);
     return;
   }
+  if (staged) {
+    l = stage_acquire(h, k, SET_A, s);
+    val = S::val(l);
+  }
   // curb: current iterate; spare: a free buffer distinct from out
   T *curb, *spare;
   int sweeps = nu_post;
@@ -1440,6 +1456,7 @@ void cycle_level(amg_hierarchy *h, int k, const T *f, const T *guess, T *out, in
     spare = curb;
     curb = dst;
   }
+  if (staged) stage_release(h, k, false, s);
 }
 
 template <typename T, typename V>
@@ -1478,7 +1495,8 @@ amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t
 amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s) {
   const Level &c = h->lev[h->L];
   const amg_params &p = h->prm;
-  h->dense = (p.coarse_solver == AMG_COARSE_DENSE) || (p.coarse_solver == AMG_COARSE_AUTO && c.n <= p.coarse_max);
+  const int dense_max = p.dense_max > 0 ? p.dense_max : p.coarse_max;
+  h->dense = (p.coarse_solver == AMG_COARSE_DENSE) || (p.coarse_solver == AMG_COARSE_AUTO && c.n <= dense_max);
   if (h->dense) {
     if ((long long)c.n * c.n * 8 > (8ll << 30)) return AMG_ERR_UNSUPPORTED;  // > 8 GB dense factor
     return dense_inverse(h, s);
@@ -1774,7 +1792,10 @@ static void apply_tuned(amg_hierarchy *h) {
 }
 
 extern "C" amg_status amg_autotune(amg_hierarchy *h, amg_stream_t stream) {
+  clear_stale_cuda_error();
   if (!h) return AMG_ERR_INVALID_ARG;
+  // the tuner times device-resident kernels; tune before moving levels to the host
+  if (h->residency != AMG_RESIDENT) return AMG_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   AMG_CUDA(cudaStreamSynchronize(s));
   amg_status st = h->prm.precision == AMG_FP64   ? tune_levels<double, double>(h, s)
@@ -1933,6 +1954,7 @@ extern "C" amg_status amg_selftest_wait_timeout(int blocks, amg_stream_t stream)
 }
 
 extern "C" amg_status amg_vcycle(const amg_hierarchy *hc, const double *d_r, double *d_z, amg_stream_t stream) {
+  clear_stale_cuda_error();
   if (!hc || !d_r || !d_z || d_r == d_z) return AMG_ERR_INVALID_ARG;
   amg_hierarchy *h = const_cast<amg_hierarchy *>(hc);
   cudaStream_t s = (cudaStream_t)stream;

@@ -19,14 +19,23 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    different classes overlap with each other and with the large solves on
    the worker streams.  Classes keep a batch's systems of similar size: a
    batch returns when its slowest system converges.  One thread block per
-   system outruns the whole-GPU solve in throughput up to these sizes
-   (measured: 60,000-row systems 635 solves/s batched against 255/s one at a
-   time; 8,100 rows 13,400/s against 430/s).  Larger requests run
-   ``pcg_solve`` on their worker's stream, with the whole GPU.  Their
+   system outruns the whole-GPU solve in throughput once enough systems of a
+   class are ready together (measured: 32 systems of 60,000 rows 715
+   solves/s batched against 254/s one at a time; 64 of 8,100 rows 12,950/s
+   against 424/s), but a lone mid-size system is several times slower on one
+   block than on the whole GPU; so a class launches the batched kernel only
+   with at least ``batch_min`` systems and otherwise hands them back to
+   their workers.  Under a backlog the batches fill; at a light load the
+   requests take the whole-GPU path.  Requests whose matrix is already
+   cached share its hierarchy and take turns on it (its work vectors serve
+   one solve at a time).  Larger requests run ``pcg_solve`` on their worker's
+   stream, with the whole GPU.  Their
    hierarchies stop at 1024 rows (``big_coarse_max``) rather than the
    library's 4096: the dense inverse of the coarsest level costs 2 N_L^3
-   FP64 operations on a GPU with a small FP64 rate, while one more level
-   costs far less;
+   operations, while one more level costs far less.  A hierarchy whose
+   coarsening stalls above that (the P1 systems near 10^6 rows stop at a few
+   thousand rows) still gets the dense inverse up to ``big_dense_max`` rows:
+   a coarse CG would run hundreds of grid-wide iterations in every cycle;
 4. completion: the solution is copied to host memory; the latency is
    completion time minus arrival time.
 
@@ -86,20 +95,25 @@ def estimate_bytes(n: int, nnz: int, precision: int) -> int:
 
 
 class _Entry:
-    __slots__ = ("h", "bytes", "users", "key")
+    __slots__ = ("h", "bytes", "users", "key", "lock")
 
     def __init__(self, h, nbytes, key):
         self.h = h
         self.bytes = nbytes
         self.users = 0
         self.key = key
+        # a hierarchy's work vectors serve one solve at a time: requests with
+        # the same matrix (a cache hit) take turns
+        self.lock = threading.Lock()
 
 
 class SolveServer:
     def __init__(self, device: int = 0, memory_budget: int | None = None, precision: int = amg.AMG_FP32,
                  rtol: float = 1e-8, max_iter: int = 1000, workers: int = 12, small_max_n: int = 60000,
-                 batch_coarse_max: int = 256, big_coarse_max: int = 1024, max_batch: int = 256,
-                 cache_entries: int = 64, batch_classes=(5000, 20000, 60000), batch_window_s: float = 0.001):
+                 batch_coarse_max: int = 256, big_coarse_max: int = 1024, big_dense_max: int = 8192,
+                 max_batch: int = 256,
+                 cache_entries: int = 64, batch_classes=(5000, 20000, 60000), batch_window_s: float = 0.001,
+                 batch_min=(1, 3, 8)):
         self.dev = torch.device("cuda", device)
         torch.cuda.set_device(self.dev)
         amg.lib()
@@ -113,6 +127,7 @@ class SolveServer:
         self.small_max_n = small_max_n
         self.batch_coarse_max = batch_coarse_max
         self.big_coarse_max = big_coarse_max
+        self.big_dense_max = big_dense_max
         self.max_batch = max_batch
         self.cache_entries = cache_entries
         self.batch_window_s = batch_window_s
@@ -122,20 +137,27 @@ class SolveServer:
         self._cache_bytes = 0
         self._pending: "collections.deque" = collections.deque()  # admitted, waiting for a worker
         self.batch_classes = tuple(sorted(c for c in batch_classes if c < small_max_n)) + (small_max_n,)
+        # fewest systems a batch of each class needs to beat solving them one
+        # by one on the worker streams (the batched kernel gives a system one
+        # thread block, so a lone mid-size system is faster on the whole GPU)
+        bm = tuple(batch_min) + (batch_min[-1],) * len(self.batch_classes)
+        self.batch_min = bm[:len(self.batch_classes)]
         self._batchqs = [queue.Queue() for _ in self.batch_classes]
         self._results: dict[int, ServeResult] = {}
         self._stop = False
         self.stats = collections.Counter()
         self._workers = [threading.Thread(target=self._worker, daemon=True) for _ in range(workers)]
-        self._batchers = [threading.Thread(target=self._batch_loop, args=(q,), daemon=True) for q in self._batchqs]
+        self._batchers = [threading.Thread(target=self._batch_loop, args=(q, m), daemon=True)
+                          for q, m in zip(self._batchqs, self.batch_min)]
         for t in self._workers + self._batchers:
             t.start()
 
     # ------------------------------------------------------------------ admission
     def _params_for(self, n: int):
-        small = n <= self.small_max_n
-        return amg.amg_default_params(precision=self.precision,
-                                      coarse_max=self.batch_coarse_max if small else self.big_coarse_max)
+        if n <= self.small_max_n:
+            return amg.amg_default_params(precision=self.precision, coarse_max=self.batch_coarse_max)
+        return amg.amg_default_params(precision=self.precision, coarse_max=self.big_coarse_max,
+                                      dense_max=self.big_dense_max)
 
     def _evict_for(self, need: int) -> bool:
         """Evicts idle cached hierarchies (least recent first) until `need` fits."""
@@ -225,21 +247,23 @@ class SolveServer:
             setup_done = time.perf_counter()
             batchable = (n <= self.small_max_n and h.sizes()[-1] <= self.batch_coarse_max
                          and self._dense_coarse(h))
-            if batchable:
-                done = threading.Event()
-                slot = {}
-                stream.synchronize()
-                cls = next(k for k, c in enumerate(self.batch_classes) if n <= c)
-                self._batchqs[cls].put((h, d_b, x, done, slot))
-                done.wait()
-                info = slot["info"]
-                path = "batch"
-            else:
-                info = amg.pcg_solve(h, d_b, x, rtol=self.rtol, max_iter=self.max_iter, flexible=True,
-                                     stream=stream)
+            with entry.lock:
+                info = None
                 path = "single"
-            hx = x.to("cpu", non_blocking=True)
-            stream.synchronize()
+                if batchable:
+                    done = threading.Event()
+                    slot = {}
+                    cls = next(k for k, c in enumerate(self.batch_classes) if n <= c)
+                    self._batchqs[cls].put((h, d_b, x, done, slot))
+                    done.wait()
+                    info = slot["info"]  # None: too few systems of the class were ready to batch
+                    if info is not None:
+                        path = "batch"
+                if info is None:
+                    info = amg.pcg_solve(h, d_b, x, rtol=self.rtol, max_iter=self.max_iter, flexible=True,
+                                         stream=stream)
+                hx = x.to("cpu", non_blocking=True)
+                stream.synchronize()
         fin = time.perf_counter()
         with self._lock:
             entry.users -= 1
@@ -260,11 +284,11 @@ class SolveServer:
 
     @staticmethod
     def _dense_coarse(h) -> bool:
-        # a hierarchy whose coarsest level is small enough for the dense inverse
-        return h.sizes()[-1] <= h.params.coarse_max or h.params.coarse_solver == amg.AMG_COARSE_DENSE
+        # the coarsest level is solved with the dense inverse
+        return amg.amg_coarse_cg_cluster_size(h) < 0
 
     # ------------------------------------------------------------------ batcher
-    def _batch_loop(self, bq):
+    def _batch_loop(self, bq, min_batch):
         torch.cuda.set_device(self.dev)
         stream = torch.cuda.Stream(device=self.dev)
         while True:
@@ -283,6 +307,13 @@ class SolveServer:
                     group.append(bq.get(timeout=left) if left > 0 else bq.get_nowait())
                 except queue.Empty:
                     break
+            if len(group) < min_batch:
+                # hand the systems back: each runs the whole-GPU solve on its worker's stream
+                for g in group:
+                    g[4]["info"] = None
+                    g[3].set()
+                self.stats["unbatched"] += len(group)
+                continue
             try:
                 infos = amg.amg_batch_pcg([g[0] for g in group], [g[1] for g in group], [g[2] for g in group],
                                           rtol=self.rtol, max_iter=self.max_iter, flexible=True, stream=stream)

@@ -92,3 +92,29 @@ def test_batched_solver_requires_fp64_inverse():
     x = torch.zeros_like(b)
     with pytest.raises(amg.AmgError):
         amg.amg_batch_pcg([h], [b], [x], rtol=1e-8)
+
+
+def test_dense_max_gives_a_stalled_coarsest_level_the_direct_solve():
+    """A lognormal hierarchy stalls well above a stop size of 100 rows; with
+    dense_max above its coarsest size the coarsest level is inverted instead
+    of solved by CG, and the V-cycle is the oracle's dense-coarse cycle."""
+    s = W.lognormal3d(24, seed=2)
+    p = amg.amg_default_params(coarse_max=100)
+    rp, ci, val, b = to_cuda(s)
+    h_cg = amg.amg_setup(rp, ci, val, p)
+    n_l = h_cg.sizes()[-1]
+    assert n_l > 100 and amg.amg_coarse_cg_cluster_size(h_cg) >= 0
+    h_cg.close()
+    h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=100, dense_max=n_l))
+    assert h.sizes()[-1] == n_l and amg.amg_coarse_cg_cluster_size(h) == -1
+    import oracle as O
+    oh = O.Hierarchy(s.rp, s.ci, s.val, params=O.Params(coarse_max=100, coarse_solver=1))
+    assert oh.sizes() == h.sizes()
+    z = torch.empty_like(b)
+    amg.amg_vcycle(h, b, z)
+    assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < 1e-12
+    h.close()
+    # below the coarsest size the CG stays
+    h2 = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=100, dense_max=n_l - 1))
+    assert amg.amg_coarse_cg_cluster_size(h2) >= 0
+    h2.close()

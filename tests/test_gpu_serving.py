@@ -70,3 +70,21 @@ def test_admission_budget_and_cache():
         big = W.poisson2d(300)
         srv.submit(2000, big.rp, big.ci, big.val, big.b, arrival=0.0)
     srv.close()
+
+
+def test_identical_matrices_take_turns_on_a_cached_hierarchy():
+    """Requests with the same matrix and different right-hand sides share the
+    cached hierarchy; solved concurrently they must not share its work vectors."""
+    systems = [W.poisson2d(70, seed=30 + i) for i in range(12)]
+    assert all(np.array_equal(s.val, systems[0].val) for s in systems)
+    srv = S.SolveServer(workers=6, small_max_n=20000, batch_classes=(5000,))
+    for i, s in enumerate(systems):
+        srv.submit(i, s.rp, s.ci, s.val, s.b, arrival=0.0)
+    res = srv.wait(list(range(len(systems))))
+    assert srv.stats["cache_hit"] >= 1
+    srv.close()
+    oh = O.Hierarchy(systems[0].rp, systems[0].ci, systems[0].val)
+    for s, r in zip(systems, res):
+        assert r.status == amg.AMG_OK and r.rel_res_true <= 1e-8, r
+        x_o, _ = oh.pcg(s.b, rtol=1e-12, flexible=True)
+        assert np.linalg.norm(r.x - x_o) / np.linalg.norm(x_o) < 1e-5

@@ -48,6 +48,7 @@ def _bare_server(budget):
     srv.small_max_n = 5000
     srv.batch_coarse_max = 256
     srv.big_coarse_max = 1024
+    srv.big_dense_max = 8192
     srv._lock = threading.Condition()
     srv._in_use = 0
     srv._cache = collections.OrderedDict()
@@ -92,5 +93,7 @@ def test_small_and_large_requests_get_their_coarse_limits():
     small = srv._params_for(4000)
     large = srv._params_for(6000)
     assert small.coarse_max == 256 and large.coarse_max == 1024
+    # a large hierarchy that stalls above its stop size keeps the dense coarsest solve
+    assert small.dense_max == 0 and large.dense_max == 8192
     assert small.precision == large.precision == amg.AMG_FP32
     assert small.cycle == amg.AMG_CYCLE_V  # the batched kernel runs V-cycles
