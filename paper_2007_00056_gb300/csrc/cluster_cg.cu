@@ -244,11 +244,17 @@ cudaError_t ccg_launch_t(const ClusterCG &cc, int n, const int32_t *rp, const in
                             iters_total, st);
 }
 
+// The kernel's attributes are process-wide, so they are set to fixed values
+// (the largest shared memory any configuration uses), never to one
+// hierarchy's size: a setup on another thread must not lower the limit under
+// a launch that needs more.
+#define CCG_SMEM_CAP (200 * 1024)
+
 template <typename T>
-cudaError_t ccg_prepare_kernel(size_t smem) {
+cudaError_t ccg_prepare_kernel() {
   cudaError_t e = cudaFuncSetAttribute(k_coarse_cg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_coarse_cg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_coarse_cg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, CCG_SMEM_CAP);
   return e;
 }
 
@@ -285,8 +291,8 @@ amg_status cluster_cg_config(int n, ClusterCG *cc) {
   for (int size : {16, 8}) {
     const int rows_per = cdiv(n, size);
     const size_t smem = sizeof(double) * (size_t)CCG_VECS * rows_per;
-    if (smem > 200 * 1024) continue;
-    if (ccg_prepare_kernel<double>(smem) != cudaSuccess || ccg_prepare_kernel<float>(smem) != cudaSuccess) {
+    if (smem > CCG_SMEM_CAP) continue;
+    if (ccg_prepare_kernel<double>() != cudaSuccess || ccg_prepare_kernel<float>() != cudaSuccess) {
       cudaGetLastError();
       continue;
     }

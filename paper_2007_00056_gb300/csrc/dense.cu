@@ -34,6 +34,7 @@
 #define GJ_TJ 256                // update kernel: columns per block (one per thread)
 #define GJ_TI 32                 // update kernel: rows per block
 #define GJ_REFINE_MAX 12         // refinement steps tried at setup
+#define GJ_COLMAP_SMEM (4 * 32768)  // shared memory of k_gj_colmap (one int per column)
 #define GJ_BACKWARD_TOL (16.0 * 2.220446049250313e-16)  // accepted backward error of the refined solve
 
 namespace {
@@ -44,12 +45,26 @@ __global__ void k_dense_zero(long long mm, T *__restrict__ M) {
     M[t] = (T)0;
 }
 
+// A (m x m CSR) into the dense row-major M with row stride ld >= m; rows and
+// columns m..ld-1 (a padding) get the identity.
 template <typename T>
-__global__ void k_dense_scatter(int m, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+__global__ void k_dense_scatter(int m, int ld, const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
                                 const double *__restrict__ val, T *__restrict__ M) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  for (int e = rp[i]; e < rp[i + 1]; ++e) M[(size_t)i * m + ci[e]] = (T)val[e];
+  if (i >= ld) return;
+  if (i >= m) {
+    M[(size_t)i * ld + i] = (T)1;
+    return;
+  }
+  for (int e = rp[i]; e < rp[i + 1]; ++e) M[(size_t)i * ld + ci[e]] = (T)val[e];
+}
+
+// out (m x m) = the leading m x m block of W (row stride ld).
+template <typename T>
+__global__ void k_dense_crop(int m, int ld, const T *__restrict__ W, T *__restrict__ out) {
+  const long long mm = (long long)m * m;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < mm; t += (long long)gridDim.x * blockDim.x)
+    out[t] = W[(t / m) * ld + t % m];
 }
 
 // Step 1: factor columns k0 .. k0+nb-1 of the m x m array M in place (one
@@ -292,7 +307,7 @@ amg_status gj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   const int TB = AMG_THREADS;
   k_dense_zero<T><<<grid_for(mm, TB), TB, 0, st>>>(mm, M);
   count_launch();
-  k_dense_scatter<T><<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, M);
+  k_dense_scatter<T><<<cdiv(m, TB), TB, 0, st>>>(m, m, c.rp, c.ci, c.val, M);
   count_launch();
   for (int k0 = 0; k0 < m;) {
     // widest instantiated width within the panel width and the columns left
@@ -310,8 +325,11 @@ amg_status gj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
     gj_update_dispatch<T>(w, m, k0, M, R, st);
     k0 += w;
   }
-  if (sizeof(int) * (size_t)m > 48 * 1024)
-    AMG_CUDA(cudaFuncSetAttribute(k_gj_colmap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * m)));
+  // a fixed limit for every m up to the largest dense level (32768 rows): the
+  // attribute is process-wide, and a setup on another thread must not lower it
+  // under this launch
+  if (sizeof(int) * (size_t)m > GJ_COLMAP_SMEM) return AMG_ERR_UNSUPPORTED;
+  AMG_CUDA(cudaFuncSetAttribute(k_gj_colmap, cudaFuncAttributeMaxDynamicSharedMemorySize, GJ_COLMAP_SMEM));
   k_gj_colmap<<<1, 256, sizeof(int) * m, st>>>(m, piv, cm);
   count_launch();
   k_gj_unpermute<T><<<grid_for(mm, TB), TB, 0, st>>>(m, M, cm, out);
@@ -572,13 +590,17 @@ template <typename T>
 amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   using TL = BgjTile<T>;
   const Level &c = h->lev[h->L];
-  const int m = c.n;
+  const int n = c.n;
+  // FP32: eliminate on an order rounded up to a multiple of 4 whose extra rows
+  // and columns are an identity block (the inverse of diag(A, I) is
+  // diag(A^-1, I), and the padding meets A's entries only through exact
+  // zeros), so that every row is 16-byte aligned for the float4 update
+  const int m = sizeof(T) == sizeof(float) ? (n + 3) / 4 * 4 : n;
   const long long mm = (long long)m * m;
   const size_t smem = sizeof(T) * (size_t)BGJ_W * (TL::BM + TL::BN);
   AMG_CUDA(cudaFuncSetAttribute(k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // the float4 form of the update when rows are 16-byte aligned
-  const bool vec4 = sizeof(T) == sizeof(float) && m % 4 == 0;
+  const bool vec4 = sizeof(T) == sizeof(float);
   if (vec4)
     AMG_CUDA(cudaFuncSetAttribute(k_bgj_update4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)BGJ4_SMEM));
   const size_t tsmem = BGJ_TILE_SMEM(T);
@@ -588,9 +610,14 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   if (pool_alloc((void **)&R, sizeof(T) * ((size_t)BGJ_W * m + (size_t)BGJ_W * BGJ_W), st) != AMG_OK)
     return AMG_ERR_OOM;
   T *Pinv = R + (size_t)BGJ_W * m;
+  T *const dst = out;
+  if (m != n && pool_alloc((void **)&out, sizeof(T) * (size_t)mm, st) != AMG_OK) {
+    pool_free(R, st);
+    return AMG_ERR_OOM;
+  }
   const int TB = AMG_THREADS;
   k_dense_zero<T><<<grid_for(mm, TB), TB, 0, st>>>(mm, out);
-  k_dense_scatter<T><<<cdiv(m, TB), TB, 0, st>>>(m, c.rp, c.ci, c.val, out);
+  k_dense_scatter<T><<<cdiv(m, TB), TB, 0, st>>>(n, m, c.rp, c.ci, c.val, out);
   count_launch(2);
   const dim3 ug(cdiv(m, TL::BN), cdiv(m, TL::BM));
   for (int k0 = 0; k0 < m; k0 += BGJ_W) {
@@ -603,6 +630,11 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
       k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
     k_bgj_cols<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv);
     count_launch(4);
+  }
+  if (m != n) {
+    k_dense_crop<T><<<grid_for((long long)n * n, TB), TB, 0, st>>>(n, m, out, dst);
+    count_launch();
+    pool_free(out, st);
   }
   AMG_CUDA(cudaGetLastError());
   unsigned flags = 0;

@@ -882,15 +882,32 @@ __device__ __forceinline__ PairRow pair_row(int I, const int32_t *first, const i
   return r;
 }
 
+// The product's operands gathered first, by independent threads: each coarse
+// row's member row bounds (b0, n0, b1, n1) and each fine entry's coarse column
+// agg[ci[e]].  The product then waits on two dependent loads per coarse row
+// instead of five (first, mate, rp, ci, agg), which bound its time.
+__global__ void k_pair_meta(int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ mate,
+                            const int32_t *__restrict__ rp, int4 *__restrict__ meta) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nc) return;
+  const PairRow r = pair_row(I, first, mate, rp);
+  meta[I] = make_int4(r.b0, r.n0, r.b1, r.n1);
+}
+
+__global__ void k_coarse_cols(long long nnz, const int32_t *__restrict__ ci, const int32_t *__restrict__ agg,
+                              int32_t *__restrict__ Jf) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz; e += (long long)gridDim.x * blockDim.x)
+    Jf[e] = agg[ci[e]];
+}
+
 #define GAL_WARPS (AMG_THREADS / 32)
 #define GAL_CAP 256  // contributions per coarse row staged in shared memory
 
 template <bool FILL>
 __global__ void __launch_bounds__(AMG_THREADS)
-    k_galerkin(int nc, const int32_t *__restrict__ first, const int32_t *__restrict__ mate,
-               const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ val,
-               const int32_t *__restrict__ agg, int *__restrict__ count, const int32_t *__restrict__ rpc,
-               int32_t *__restrict__ cic, double *__restrict__ valc) {
+    k_galerkin(int nc, const int4 *__restrict__ meta, const double *__restrict__ val, const int32_t *__restrict__ Jf,
+               int *__restrict__ count, const int32_t *__restrict__ rpc, int32_t *__restrict__ cic,
+               double *__restrict__ valc) {
   __shared__ int sJ[GAL_WARPS][GAL_CAP];
   __shared__ double sV[GAL_WARPS][GAL_CAP];
   __shared__ unsigned char sF[GAL_WARPS][GAL_CAP];
@@ -898,7 +915,12 @@ __global__ void __launch_bounds__(AMG_THREADS)
   const int wib = threadIdx.x >> 5;
   const int warps = (gridDim.x * blockDim.x) >> 5;
   for (int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += warps) {
-    PairRow r = pair_row(I, first, mate, rp);
+    const int4 mt = meta[I];
+    PairRow r;
+    r.b0 = mt.x;
+    r.n0 = mt.y;
+    r.b1 = mt.z;
+    r.n1 = mt.w;
     const int m = r.m();
     int distinct = 0;
     const int out0 = FILL ? rpc[I] : 0;
@@ -907,7 +929,7 @@ __global__ void __launch_bounds__(AMG_THREADS)
       // keys); lanes with the same coarse column form a match group, the
       // group's lowest lane (first in stored order) sums its values in lane
       // order -- FP64 adds only for real duplicates
-      const int J = lane < m ? agg[ci[r.pos(lane)]] : -1 - lane;
+      const int J = lane < m ? Jf[r.pos(lane)] : -1 - lane;
       const double v = lane < m ? val[r.pos(lane)] : 0.0;
       sV[wib][lane] = v;
       const unsigned grp = __match_any_sync(0xffffffffu, J);
@@ -936,7 +958,7 @@ __global__ void __launch_bounds__(AMG_THREADS)
       int *J = sJ[wib];
       double *V = sV[wib];
       unsigned char *F = sF[wib];
-      for (int k = lane; k < m; k += 32) { J[k] = agg[ci[r.pos(k)]]; V[k] = val[r.pos(k)]; }
+      for (int k = lane; k < m; k += 32) { J[k] = Jf[r.pos(k)]; V[k] = val[r.pos(k)]; }
       __syncwarp();
       int cnt = 0;
       for (int k = lane; k < m; k += 32) {
@@ -969,21 +991,21 @@ __global__ void __launch_bounds__(AMG_THREADS)
     } else {
       // very long rows: the same definition with operands re-read from memory
       for (int k = lane; k < m; k += 32) {
-        int J = agg[ci[r.pos(k)]];
+        int J = Jf[r.pos(k)];
         bool firstJ = true;
         for (int q = 0; q < k && firstJ; ++q)
-          if (agg[ci[r.pos(q)]] == J) firstJ = false;
+          if (Jf[r.pos(q)] == J) firstJ = false;
         if (!firstJ) continue;
         ++distinct;
         if (FILL) {
           int rank = 0;
           double sum = val[r.pos(k)];
           for (int q = 0; q < m; ++q) {
-            int Jq = agg[ci[r.pos(q)]];
+            int Jq = Jf[r.pos(q)];
             if (Jq < J) {
               bool fq = true;
               for (int u = 0; u < q && fq; ++u)
-                if (agg[ci[r.pos(u)]] == Jq) fq = false;
+                if (Jf[r.pos(u)] == Jq) fq = false;
               if (fq) ++rank;
             } else if (Jq == J && q > k) {
               sum = __dadd_rn(sum, val[r.pos(q)]);
@@ -1395,8 +1417,15 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   out.n = nc;
   AMG_TRY(pool_alloc((void **)&out.rp, sizeof(int32_t) * (nc + 1 + AMG_PAD), st));
   const int gwarps_blocks = grid_for((long long)nc * 32, T, 152 * 16);
-  k_galerkin<false><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, S.count,
-                                                  nullptr, nullptr, nullptr); count_launch();
+  // operands of the product (the matching's weight array and neighbour table
+  // are free again): member row bounds and coarse columns of the fine entries
+  int4 *meta = reinterpret_cast<int4 *>(S.nb);
+  int32_t *Jf = reinterpret_cast<int32_t *>(S.w);
+  k_pair_meta<<<cdiv(std::max(nc, 1), T), T, 0, st>>>(nc, S.first, S.mate, in.rp, meta); count_launch();
+  k_coarse_cols<<<grid_for(std::max(in.nnz, 1ll), T, 152 * 16), T, 0, st>>>(in.nnz, in.ci, pass_agg, Jf);
+  count_launch();
+  k_galerkin<false><<<gwarps_blocks, T, 0, st>>>(nc, meta, in.val, Jf, S.count, nullptr, nullptr, nullptr);
+  count_launch();
   scan_excl(S.count, out.rp, nc, S.cnt + 35, S.tiles, st);
   cudaMemcpyAsync(out.rp + nc, S.cnt + 35, sizeof(int), cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(S.host + 35, S.cnt + 35, sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -1406,8 +1435,8 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   AMG_TRY(pool_alloc((void **)&out.val, sizeof(double) * (out.nnz + AMG_PAD), st));
   cudaMemsetAsync(out.ci + out.nnz, 0, sizeof(int32_t) * AMG_PAD, st);
   cudaMemsetAsync(out.val + out.nnz, 0, sizeof(double) * AMG_PAD, st);
-  k_galerkin<true><<<gwarps_blocks, T, 0, st>>>(nc, S.first, S.mate, in.rp, in.ci, in.val, pass_agg, nullptr,
-                                                 out.rp, out.ci, out.val); count_launch();
+  k_galerkin<true><<<gwarps_blocks, T, 0, st>>>(nc, meta, in.val, Jf, nullptr, out.rp, out.ci, out.val);
+  count_launch();
   AMG_CUDA(cudaGetLastError());
   return AMG_OK;
 }
