@@ -333,6 +333,15 @@ def run_serving(reqs, systems, plain_sample=256):
     res_cap, wall_cap = S.serve_stream(srv, reqs, systems, time_scale=0.0)
     srv.close()
     ok = sum(r.status == amg.AMG_OK and r.rel_res_true <= 1e-8 for r in res)
+    # the same stream with the paper's edge weight max(|a_ij|, |a_ji|)
+    paper = {}
+    for tag, scale in (("", 1.0), ("capacity_", 0.0)):
+        srv = S.SolveServer(params={"edge_weight": amg.AMG_WEIGHT_ABS})
+        rp_, wp_ = S.serve_stream(srv, reqs, systems, time_scale=scale)
+        srv.close()
+        lp = S.latency_summary(rp_)
+        paper.update({f"{tag}solves_per_s": len(rp_) / wp_, f"{tag}p50_ms": lp["p50_ms"], f"{tag}p99_ms": lp["p99_ms"],
+                      f"{tag}converged_1e-8": int(sum(r.status == amg.AMG_OK and r.rel_res_true <= 1e-8 for r in rp_))})
     # the queue stays bounded when late requests wait no longer than early ones
     q = len(res) // 4
     lat_first = S.latency_summary(res[:q]) if q else None
@@ -377,6 +386,9 @@ def run_serving(reqs, systems, plain_sample=256):
         "plain_fp64_sequential_p99_ms": float(np.percentile(plain_lat, 99)),
         "batched_requests": int(stats.get("batched", 0)), "batches": int(stats.get("batches", 0)),
         "precision": "fp32 V-cycle, fp64 flexible PCG",
+        "edge_weight": "max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|) (option; the server's default)",
+        "workers": srv_defaults["workers"],
+        "paper_edge_weight": paper,
     }
 
 

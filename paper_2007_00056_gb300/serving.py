@@ -35,7 +35,9 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    operations, while one more level costs far less.  A hierarchy whose
    coarsening stalls above that (the P1 systems near 10^6 rows stop at a few
    thousand rows) still gets the dense inverse up to ``big_dense_max`` rows:
-   a coarse CG would run hundreds of grid-wide iterations in every cycle;
+   a coarse CG would run hundreds of grid-wide iterations in every cycle.
+   Every setup uses the scaled edge weight by default (``params``), which
+   keeps the lognormal systems coarsening past the paper's weight's stall;
 4. completion: the solution is copied to host memory; the latency is
    completion time minus arrival time.
 
@@ -109,12 +111,18 @@ class _Entry:
 
 class SolveServer:
     def __init__(self, device: int = 0, memory_budget: int | None = None, precision: int = amg.AMG_FP32,
-                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 12, small_max_n: int = 60000,
+                 rtol: float = 1e-8, max_iter: int = 1000, workers: int = 16, small_max_n: int = 60000,
                  batch_coarse_max: int = 256, big_coarse_max: int = 1024, big_dense_max: int = 8192,
                  max_batch: int = 256,
                  cache_entries: int = 64, batch_classes=(5000, 20000, 60000), batch_window_s: float = 0.001,
-                 batch_min=(1, 3, 8)):
+                 batch_min=(1, 3, 8), params=None):
         self.dev = torch.device("cuda", device)
+        # amg_params fields for every request's setup.  Default: the scaled
+        # edge weight max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|), an option the paper
+        # does not have; with the paper's weight the variable-coefficient
+        # systems stall at a few percent of N and their coarse CG dominates the
+        # stream's GPU time (measured: 141 against 206 solves/s of capacity)
+        self.params = {"edge_weight": amg.AMG_WEIGHT_SCALED} if params is None else dict(params)
         torch.cuda.set_device(self.dev)
         amg.lib()
         if memory_budget is None:
@@ -154,10 +162,12 @@ class SolveServer:
 
     # ------------------------------------------------------------------ admission
     def _params_for(self, n: int):
+        extra = getattr(self, "params", {})
         if n <= self.small_max_n:
-            return amg.amg_default_params(precision=self.precision, coarse_max=self.batch_coarse_max)
-        return amg.amg_default_params(precision=self.precision, coarse_max=self.big_coarse_max,
-                                      dense_max=self.big_dense_max)
+            return amg.amg_default_params(**{"precision": self.precision, "coarse_max": self.batch_coarse_max,
+                                             **extra})
+        return amg.amg_default_params(**{"precision": self.precision, "coarse_max": self.big_coarse_max,
+                                         "dense_max": self.big_dense_max, **extra})
 
     def _evict_for(self, need: int) -> bool:
         """Evicts idle cached hierarchies (least recent first) until `need` fits."""

@@ -49,6 +49,7 @@ def _bare_server(budget):
     srv.batch_coarse_max = 256
     srv.big_coarse_max = 1024
     srv.big_dense_max = 8192
+    srv.params = {"edge_weight": amg.AMG_WEIGHT_SCALED}
     srv._lock = threading.Condition()
     srv._in_use = 0
     srv._cache = collections.OrderedDict()
@@ -97,3 +98,7 @@ def test_small_and_large_requests_get_their_coarse_limits():
     assert small.dense_max == 0 and large.dense_max == 8192
     assert small.precision == large.precision == amg.AMG_FP32
     assert small.cycle == amg.AMG_CYCLE_V  # the batched kernel runs V-cycles
+    assert small.edge_weight == large.edge_weight == amg.AMG_WEIGHT_SCALED
+    srv.params = {"edge_weight": amg.AMG_WEIGHT_ABS, "operator_form": 0}
+    p = srv._params_for(6000)
+    assert p.edge_weight == amg.AMG_WEIGHT_ABS and p.operator_form == 0 and p.dense_max == 8192
