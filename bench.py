@@ -44,6 +44,10 @@ DRAM_BYTES_PER_LAUNCH = {
     # (profiles/level_kernels_anisotropic3d_128.md), times 8.0217, the ratio of the
     # launch's algorithmic bytes at 256^3 and at 128^3
     ("op_residual", 0): 213434624 * 8.0217,
+    # k_pcg_spmv<1> (the outer q = A p) at level 0 of anisotropic3d_128: 212,622,208 bytes, the
+    # mean of two launches (profiles/krylov_spmv_anisotropic3d_128.md), times 8.0202, the ratio
+    # of the launch's algorithmic bytes at 256^3 and at 128^3
+    ("krylov_spmv", 0): 212622208 * 8.0202,
 }
 # DRAM bytes per launch of the coarse CG on the 128^3 lognormal coarsest
 # level (profiles/coarse_cg_lognormal3d_128.md): its matrix and vectors live

@@ -393,6 +393,7 @@ __device__ __forceinline__ int ld_state(const int *p) { return L2ONLY ? __ldcg(p
 // padded: a pick is then the first free entry of one 32-byte row, with no
 // weights and no row pointers on the round's dependent-load chain.
 #define HEM_ELL 8
+#define HEM_ELL_MIN_N 65536  // graphs up to this size skip the table
 struct HemGraph {
   const int32_t *rp, *ci;
   const double *w;
@@ -1325,18 +1326,24 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   int batch = 4;                     // rounds per host check: 4, 8, then 16
   bool finished = false, frontier_rounds = true;
   const int coop_blocks = hem_coop_blocks(h, n);
+  bool coop_deferred = false;
   if (coop_blocks > 0) {
     // every round in one cooperative launch; the sorted neighbour table when
     // every node has at most HEM_ELL neighbours
     int *ctr = S.coop;
     AMG_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int) * HEM_COOP_INTS, st));
-    unsigned *too_wide = (unsigned *)(S.cnt + 60);
-    AMG_CUDA(cudaMemsetAsync(too_wide, 0, sizeof(unsigned), st));
-    k_hem_ell<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, S.w, tie_larger, S.nb, too_wide);
-    count_launch();
-    AMG_CUDA(cudaMemcpyAsync(S.host + 60, too_wide, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    AMG_CUDA(cudaStreamSynchronize(st));
-    const bool ell = S.host[60] == 0;
+    // the table pays on large graphs; a small one goes without it (and
+    // without the host synchronisation that reads whether it fits)
+    bool ell = false;
+    if (n > HEM_ELL_MIN_N) {
+      unsigned *too_wide = (unsigned *)(S.cnt + 60);
+      AMG_CUDA(cudaMemsetAsync(too_wide, 0, sizeof(unsigned), st));
+      k_hem_ell<<<cdiv(n, T), T, 0, st>>>(n, in.rp, in.ci, S.w, tie_larger, S.nb, too_wide);
+      count_launch();
+      AMG_CUDA(cudaMemcpyAsync(S.host + 60, too_wide, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+      AMG_CUDA(cudaStreamSynchronize(st));
+      ell = S.host[60] == 0;
+    }
     int a_n = n, a_tie = tie_larger, a_max = round_cap;
     const int32_t *a_rp = in.rp, *a_ci = in.ci;
     const double *a_w = S.w;
@@ -1350,14 +1357,12 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
     AMG_CUDA(cudaLaunchCooperativeKernel(ell ? (void *)k_hem_coop<true> : (void *)k_hem_coop<false>, coop_blocks,
                                          HEM_COOP_THREADS, args, 0, st));
     count_launch();
-    AMG_CUDA(cudaMemcpyAsync(S.host, ctr + HEM_COOP_OUT, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
-    AMG_CUDA(cudaStreamSynchronize(st));
-    r = S.host[0];
+    // the round count and the completion flag are read with the aggregate
+    // count below (one synchronisation); the numbering kernels in between
+    // only index by mate[], which holds node indices or -1 at any time
+    AMG_CUDA(cudaMemcpyAsync(S.host + 44, ctr + HEM_COOP_OUT, sizeof(int) * 2, cudaMemcpyDeviceToHost, st));
     finished = true;
-    if (!S.host[1]) {
-      AMG_TRY(check_flags(h, st));
-      return AMG_ERR_TIMEOUT;
-    }
+    coop_deferred = true;
   }
   const int grid = std::min(cdiv(std::max(n, 1), T), 8 * h->num_sms);
   while (!finished) {
@@ -1414,6 +1419,13 @@ amg_status coarsen_pass(amg_hierarchy *h, Scratch &S, const Csr &in, int32_t *pa
   k_agg_assign<<<cdiv(n, T), T, 0, st>>>(n, S.mate, S.id, pass_agg, S.first); count_launch();
   cudaMemcpyAsync(S.host + 34, S.cnt + 34, sizeof(int), cudaMemcpyDeviceToHost, st);
   AMG_CUDA(cudaStreamSynchronize(st));
+  if (coop_deferred) {
+    *rounds = S.host[44];
+    if (!S.host[45]) {
+      AMG_TRY(check_flags(h, st));
+      return AMG_ERR_TIMEOUT;
+    }
+  }
   const int nc = S.host[34];
   // Galerkin: count, scan, fill
   out.n = nc;

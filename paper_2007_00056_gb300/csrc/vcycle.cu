@@ -530,6 +530,38 @@ __global__ void k_cast_scale(int n, const A *__restrict__ a, const float *__rest
   }
 }
 
+// Level 0 of the FP32 cycle in the residual-operator form, reading the FP64
+// right-hand side and writing the FP64 result itself: f is rounded to FP32 as
+// it is read and y widened as it is written, with the conversions the cast
+// kernels use, which saves two passes over the level-0 vectors.
+template <int TPR>
+__global__ void k_op_residual_in64(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp,
+                                   const int32_t *__restrict__ ci, const float *__restrict__ cval,
+                                   const double *__restrict__ f, float *__restrict__ t, const KState *st) {
+  if (is_done(st)) return;
+  ROW_LOOP_BEGIN(TPR, n)
+  int b = 0, e = 0;
+  if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
+  float cf = row_sum<TPR, float, float>(ci, cval, b, e, _sub, [&](int j) { return to_f32(__ldg(&f[j])); });
+  if (valid && _sub == 0) t[row] = cf;
+  ROW_LOOP_END
+}
+
+template <int TPR>
+__global__ void k_op_post_io64(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ qrp,
+                               const int32_t *__restrict__ qci, const float *__restrict__ qval,
+                               const float *__restrict__ xc, const float *__restrict__ wd,
+                               const double *__restrict__ f, const float *__restrict__ t, double *__restrict__ y,
+                               const KState *st) {
+  if (is_done(st)) return;
+  ROW_LOOP_BEGIN(TPR, n)
+  int b = 0, e = 0;
+  if (valid) { b = __ldg(&qrp[row]); e = __ldg(&qrp[row + 1]); }
+  float qx = row_sum<TPR, float, float>(qci, qval, b, e, _sub, [&](int J) { return __ldg(&xc[J]); });
+  if (valid && _sub == 0) y[row] = to_f64(qx + wd[row] * (to_f32(f[row]) + t[row]));
+  ROW_LOOP_END
+}
+
 template <typename A, typename B>
 __global__ void k_cast(int n, const A *__restrict__ a, B *__restrict__ b, const KState *st) {
   if (is_done(st)) return;
@@ -1464,11 +1496,71 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
   cycle_level<T, V>(h, 0, f0, nullptr, out0, h->prm.cycle, s, st);
 }
 
+#define DISPATCH_TPR_PLAIN(tpr_, g_, KERNEL, ...)                                     \
+  do {                                                                              \
+    switch (tpr_) {                                                                 \
+      case 2: KERNEL<2><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
+      case 4: KERNEL<4><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
+      case 8: KERNEL<8><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
+      case 16: KERNEL<16><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      case 32: KERNEL<32><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
+      default: KERNEL<1><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;              \
+    }                                                                               \
+  } while (0)
+
+// The level-0 visit of the FP32 cycle in the residual-operator form, from the
+// FP64 residual r to the FP64 result z (the casts folded into its first and
+// last kernels); the coarser levels run the FP32 cycle as usual.
+bool level0_fp32_op(const amg_hierarchy *h) {
+  const Level &l = h->lev[0];
+  return h->prm.precision == AMG_FP32 && h->L > 0 && l.op_on && l.cval32 && l.qval32 && h->prm.nu_pre == 1 &&
+         h->prm.nu_post == 1;
+}
+
+void cycle_level0_fp32_io64(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st) {
+  using S = Sel<float, float>;
+  const int L = h->L, kind = h->prm.cycle;
+  const bool staged = stage_on(h, 0);
+  Level l = h->lev[0];
+  Level &c = h->lev[1];
+  float *b = S::t(l);
+  // lanes per row of the level (0, the TMA-staged form, has no operator-form kernel: one lane)
+  Level lr = l;
+  lr.tpr = l.tpr == 0 ? 1 : l.tpr;
+  const int tpr = lr.tpr, g = row_blocks(lr);
+  if (staged) l = stage_acquire(h, 0, SET_C, s);
+  {
+    LaunchScope ls(h, s, PK_OP_RESIDUAL, 0, bytes_A(l, 4) + 12.0 * l.n);
+    DISPATCH_TPR_PLAIN(tpr, g, k_op_residual_in64, l.n, l.perm, l.rp, l.ci, (const float *)l.cval32, r, b, st);
+  }
+  if (staged) stage_release(h, 0, true, s);
+  {
+    LaunchScope ls(h, s, PK_RESTRICT, 0, 8.0 * l.n + 8.0 * c.n + 4.0);
+    k_restrict<float><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, nullptr, nullptr,
+                                                                          S::f(c), st);
+  }
+  float *xc = S::y(c);
+  const float *fc = S::f(c);
+  cycle_level<float, float>(h, 1, fc, nullptr, xc, kind, s, st);
+  if (1 < L && kind == AMG_CYCLE_W) cycle_level<float, float>(h, 1, fc, xc, xc, AMG_CYCLE_W, s, st);
+  if (1 < L && kind == AMG_CYCLE_F) cycle_level<float, float>(h, 1, fc, xc, xc, AMG_CYCLE_V, s, st);
+  if (staged) l = stage_acquire(h, 0, SET_Q, s);
+  {
+    const double BQ = (double)l.qnnz * 8.0 + 4.0 * (l.n + 1);
+    LaunchScope ls(h, s, PK_OP_POST, 0, BQ + 24.0 * l.n + 4.0 * c.n);
+    DISPATCH_TPR_PLAIN(tpr, g, k_op_post_io64, l.n, l.perm, l.qrp, l.qci, (const float *)l.qval32,
+                       (const float *)xc, (const float *)l.wd32, r, (const float *)b, z, st);
+  }
+  if (staged) stage_release(h, 0, false, s);
+}
+
 }  // namespace
 
 amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st) {
   if (h->prm.precision == AMG_FP64) {
     vcycle_levels<double, double>(h, r, z, s, st);
+  } else if (level0_fp32_op(h)) {
+    cycle_level0_fp32_io64(h, r, z, s, st);
   } else {
     Level &l0 = h->lev[0];
     const bool half = h->prm.precision == AMG_FP16_STORAGE;
