@@ -387,9 +387,7 @@ amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
 template <typename T>
 amg_status dense_refined_solve(amg_hierarchy *h, const T *f, T *x, int steps, cudaStream_t s, const KState *st);
 amg_status precision_setup(amg_hierarchy *h, cudaStream_t s);
-// C, Q and wd of the levels below the coarsest (allocations recorded in h, or
-// in *own when run on a helper thread; see amg_setup).
-amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t s, std::vector<std::pair<void *, size_t>> *own);
+amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t s);
 void reset_graphs(amg_hierarchy *h);
 amg_status cluster_cg_config(int n, ClusterCG *cc);
 template <typename T>

