@@ -1,19 +1,27 @@
 // batch.cu -- many AMG-PCG solves in one persistent launch.
 //
-// Each thread block owns one system of the batch and runs its whole flexible
-// PCG (Algorithm 4) with the V-cycle of Algorithm 1 as preconditioner: every
-// level of the hierarchy, smoothing, residual, restriction, dense coarsest
-// solve and prolongation, separated by block barriers only.  All reductions
-// are block reductions in a fixed order, so a system's iterates do not depend
-// on which other systems share the launch: a solve in a batch is bitwise the
-// solve alone.  Systems are read through per-hierarchy device descriptors
-// (the levels' CSR arrays and work vectors already owned by each hierarchy),
-// i.e. the batch is the block-diagonal concatenation of its systems without
-// copying any of them.
+// Each system of the batch is owned by a team -- one thread block, or a
+// thread-block cluster of 2, 4 or 8 blocks for larger systems -- that runs its
+// whole flexible PCG (Algorithm 4) with the V-cycle of Algorithm 1 as
+// preconditioner: every level of the hierarchy, smoothing, residual,
+// restriction, dense coarsest solve and prolongation, separated by team
+// barriers only (__syncthreads, or the cluster barrier).  The team size is a
+// function of the system's row count alone, and every reduction is a fixed-
+// order block reduction followed, in a cluster, by the sum of the blocks'
+// totals in rank order read through distributed shared memory, so a system's
+// iterates do not depend on which other systems share the launch: a solve in
+// a batch is bitwise the solve alone.  Systems are read through per-hierarchy
+// device descriptors (the levels' CSR arrays and work vectors already owned
+// by each hierarchy), i.e. the batch is the block-diagonal concatenation of
+// its systems without copying any of them.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <vector>
 
 #include "common.cuh"
+
+namespace cgrp = cooperative_groups;
 
 #define BATCH_THREADS 512
 #define BATCH_MAX_COARSE 2048  // largest dense coarsest level a batched system may have
@@ -53,6 +61,10 @@ struct BatchInfo {
   double rel, rel_true;
 };
 
+// Team size (blocks per system) by row count: one block up to 8192 rows,
+// then 2, 4 and 8 blocks, so a mid-size system is not left to one SM.
+static inline int batch_team(int n) { return n <= 8192 ? 1 : n <= 24576 ? 2 : n <= 65536 ? 4 : 8; }
+
 // ---------------------------------------------------------------------------
 // block-scope helpers
 // ---------------------------------------------------------------------------
@@ -67,6 +79,36 @@ __device__ __forceinline__ double bsum(double v, double *sh) {
   return s;  // every warp computes the same total in the same order
 }
 
+// The threads of one system: C blocks of a cluster (C = 1: one block).  tid
+// and nthr index the system's rows; sync() is the team barrier; sum() returns
+// the same total, formed in the same order, to every thread of the team.
+template <int C>
+struct Team {
+  int tid, nthr;
+  __device__ Team() {
+    const int rank = C > 1 ? (int)cgrp::this_cluster().block_rank() : 0;
+    tid = rank * blockDim.x + threadIdx.x;
+    nthr = C * blockDim.x;
+  }
+  __device__ __forceinline__ void sync() const {
+    if (C > 1) cgrp::this_cluster().sync();
+    else __syncthreads();
+  }
+  // sh: 33 doubles of the block's shared memory (sh[32] holds its total)
+  __device__ double sum(double v, double *sh) const {
+    const double blk = bsum(v, sh);
+    if (C == 1) return blk;
+    cgrp::cluster_group cl = cgrp::this_cluster();
+    if (threadIdx.x == 0) sh[32] = blk;
+    cl.sync();
+    double tot = 0.0;
+#pragma unroll
+    for (int r = 0; r < C; ++r) tot += *cl.map_shared_rank(&sh[32], r);
+    cl.sync();  // every block has read the totals before a later sum overwrites them
+    return tot;
+  }
+};
+
 template <typename T, typename V>
 __device__ __forceinline__ T brow(const int32_t *rp, const int32_t *ci, const V *val, const T *x, int i) {
   T s = T(0);
@@ -78,8 +120,8 @@ __device__ __forceinline__ T brow(const int32_t *rp, const int32_t *ci, const V 
 // A level with the residual-operator form (Level documents C and Q) forms its
 // residual as t = C f on the way down and its result as Q x_c + wd (f + t) on
 // the way up; the others run the explicit sweeps.
-template <typename T>
-__device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
+template <typename T, int C>
+__device__ void b_vcycle(const Team<C> &tm, const BatchSys &S, const T *f0, T *out0) {
   const int L = S.L;
   const T omega = (T)S.omega;
   const T *fk[AMG_MAX_LEVELS];
@@ -92,44 +134,44 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
     const T *f = fk[k];
     if (l.cval) {
       const T *cv = (const T *)l.cval;
-      for (int i = threadIdx.x; i < l.n; i += blockDim.x) b[i] = brow<T, T>(l.rp, l.ci, cv, f, i);
-      __syncthreads();
+      for (int i = tm.tid; i < l.n; i += tm.nthr) b[i] = brow<T, T>(l.rp, l.ci, cv, f, i);
+      tm.sync();
       cur[k] = nullptr;
       T *fc = (T *)S.lev[k + 1].f;
-      for (int I = threadIdx.x; I < l.nc; I += blockDim.x) {
+      for (int I = tm.tid; I < l.nc; I += tm.nthr) {
         int e0 = l.mrp[I], e1 = l.mrp[I + 1];
         T s = b[l.mem[e0]];
         for (int m = e0 + 1; m < e1; ++m) s += b[l.mem[m]];
         fc[I] = s;
       }
-      __syncthreads();
+      tm.sync();
       continue;
     }
-    for (int i = threadIdx.x; i < l.n; i += blockDim.x) a[i] = omega * (dinv[i] * f[i]);
-    __syncthreads();
+    for (int i = tm.tid; i < l.n; i += tm.nthr) a[i] = omega * (dinv[i] * f[i]);
+    tm.sync();
     for (int sw = 1; sw < S.nu_pre; ++sw) {
-      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+      for (int i = tm.tid; i < l.n; i += tm.nthr)
         b[i] = a[i] + omega * (dinv[i] * (f[i] - brow<T, T>(l.rp, l.ci, val, a, i)));
-      __syncthreads();
+      tm.sync();
       T *tmp = a; a = b; b = tmp;
     }
     cur[k] = a;
-    for (int i = threadIdx.x; i < l.n; i += blockDim.x) b[i] = f[i] - brow<T, T>(l.rp, l.ci, val, a, i);
-    __syncthreads();
+    for (int i = tm.tid; i < l.n; i += tm.nthr) b[i] = f[i] - brow<T, T>(l.rp, l.ci, val, a, i);
+    tm.sync();
     T *fc = (T *)S.lev[k + 1].f;
-    for (int I = threadIdx.x; I < l.nc; I += blockDim.x) {
+    for (int I = tm.tid; I < l.nc; I += tm.nthr) {
       int e0 = l.mrp[I], e1 = l.mrp[I + 1];
       T s = b[l.mem[e0]];
       for (int m = e0 + 1; m < e1; ++m) s += b[l.mem[m]];
       fc[I] = s;
     }
-    __syncthreads();
+    tm.sync();
   }
   // coarsest level: x_L = A_L^{-1} f_L (FP64 accumulation), warp per row
   T *xL = (L == 0) ? out0 : (T *)S.lev[L].y;
   {
     const T *fL = fk[L];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = tm.tid >> 5, nw = tm.nthr >> 5;
     for (int i = wid; i < S.nL; i += nw) {
       const double *row = S.ainv + (size_t)i * S.nL;
       double s = 0.0;
@@ -137,7 +179,7 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
       s = warp_sum(s);
       if (lane == 0) xL[i] = (T)s;
     }
-    __syncthreads();
+    tm.sync();
   }
   T *xc = xL;
   for (int k = L - 1; k >= 0; --k) {
@@ -147,9 +189,9 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
     T *fin = (k == 0) ? out0 : (T *)l.y;
     if (l.cval) {
       const T *qv = (const T *)l.qval, *wd = (const T *)l.wd, *t = (const T *)l.t;
-      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+      for (int i = tm.tid; i < l.n; i += tm.nthr)
         fin[i] = brow<T, T>(l.qrp, l.qci, qv, xc, i) + wd[i] * (f[i] + t[i]);
-      __syncthreads();
+      tm.sync();
       xc = fin;
       continue;
     }
@@ -157,14 +199,14 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
     T *other = (in == (T *)l.x) ? (T *)l.t : (T *)l.x;
     // prolongation into `other`, then the post-smoothing sweeps, the last into fin
     T *dst0 = S.nu_post == 0 ? fin : other;
-    for (int i = threadIdx.x; i < l.n; i += blockDim.x) dst0[i] = in[i] + xc[l.agg[i]];
-    __syncthreads();
+    for (int i = tm.tid; i < l.n; i += tm.nthr) dst0[i] = in[i] + xc[l.agg[i]];
+    tm.sync();
     T *c = dst0, *spare = in;
     for (int sw = 0; sw < S.nu_post; ++sw) {
       T *dst = (sw == S.nu_post - 1) ? fin : spare;
-      for (int i = threadIdx.x; i < l.n; i += blockDim.x)
+      for (int i = tm.tid; i < l.n; i += tm.nthr)
         dst[i] = c[i] + omega * (dinv[i] * (f[i] - brow<T, T>(l.rp, l.ci, val, c, i)));
-      __syncthreads();
+      tm.sync();
       spare = c;
       c = dst;
     }
@@ -173,22 +215,18 @@ __device__ void b_vcycle(const BatchSys &S, const T *f0, T *out0) {
 }
 
 // z = M^{-1} r in FP64 at the interface; T is the V-cycle's arithmetic type.
-template <typename T>
-__device__ void b_precond(const BatchSys &S, const double *r, double *z);
-
-template <>
-__device__ void b_precond<double>(const BatchSys &S, const double *r, double *z) {
-  b_vcycle<double>(S, r, z);
-}
-
-template <>
-__device__ void b_precond<float>(const BatchSys &S, const double *r, double *z) {
-  float *f0 = (float *)S.lev[0].f, *y0 = (float *)S.lev[0].y;
-  for (int i = threadIdx.x; i < S.n; i += blockDim.x) f0[i] = (float)r[i];
-  __syncthreads();
-  b_vcycle<float>(S, f0, y0);
-  for (int i = threadIdx.x; i < S.n; i += blockDim.x) z[i] = (double)y0[i];
-  __syncthreads();
+template <typename T, int C>
+__device__ void b_precond(const Team<C> &tm, const BatchSys &S, const double *r, double *z) {
+  if constexpr (sizeof(T) == sizeof(double)) {
+    b_vcycle<double, C>(tm, S, r, z);
+  } else {
+    float *f0 = (float *)S.lev[0].f, *y0 = (float *)S.lev[0].y;
+    for (int i = tm.tid; i < S.n; i += tm.nthr) f0[i] = (float)r[i];
+    tm.sync();
+    b_vcycle<float, C>(tm, S, f0, y0);
+    for (int i = tm.tid; i < S.n; i += tm.nthr) z[i] = (double)y0[i];
+    tm.sync();
+  }
 }
 
 // Flexible (or not) AMG-PCG of Algorithm 4 for the block's system, with the
@@ -198,13 +236,14 @@ __device__ void b_precond<float>(const BatchSys &S, const double *r, double *z) 
 // ||b - A x|| <= rtol ||b||.  The flexible beta is (z_{j+1}, r_{j+1} - r_j) /
 // (z_j, r_j), formed as -alpha (z_{j+1}, q_j) / (z_j, r_j).
 #define BATCH_RESTARTS 4
-template <typename T>
-__global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const BatchJob *__restrict__ jobs,
+template <typename T, int C>
+__global__ void __launch_bounds__(BATCH_THREADS, 1) k_batch_pcg(int nsys, const BatchJob *__restrict__ jobs,
                                                               double rtol, int max_iter, int flexible,
                                                               BatchInfo *__restrict__ info) {
-  __shared__ double sh[32];
-  const int sidx = blockIdx.x;
+  __shared__ double sh[33];
+  const int sidx = blockIdx.x / C;  // the whole team leaves together
   if (sidx >= nsys) return;
+  const Team<C> tm;
   const BatchSys &S = *jobs[sidx].sys;
   const double *b = jobs[sidx].b;
   double *x = jobs[sidx].x;
@@ -213,14 +252,14 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const Bat
   // ||b||, and r = b - A x with its norm
   auto residual = [&](double *bb_out) {
     double bb = 0.0, rr = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = tm.tid; i < n; i += tm.nthr) {
       const double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
       r[i] = ri;
       bb += b[i] * b[i];
       rr += ri * ri;
     }
-    bb = bsum(bb, sh);
-    rr = bsum(rr, sh);
+    bb = tm.sum(bb, sh);
+    rr = tm.sum(rr, sh);
     if (bb_out) *bb_out = bb;
     return rr;
   };
@@ -232,60 +271,60 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const Bat
   if (!isfinite(bb) || !isfinite(rr)) {
     status = AMG_ERR_INVALID_ARG;
   } else if (bnorm == 0.0) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = 0.0;
+    for (int i = tm.tid; i < n; i += tm.nthr) x[i] = 0.0;
     status = AMG_OK;
   } else if (rel <= rtol) {
     status = AMG_OK;
   } else if (max_iter > 0) {
     for (int restart = 0;; ++restart) {
-      __syncthreads();
-      b_precond<T>(S, r, z);
+      tm.sync();
+      b_precond<T, C>(tm, S, r, z);
       double rz = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) { p[i] = z[i]; rz += r[i] * z[i]; }
-      rz = bsum(rz, sh);
+      for (int i = tm.tid; i < n; i += tm.nthr) { p[i] = z[i]; rz += r[i] * z[i]; }
+      rz = tm.sum(rz, sh);
       status = AMG_ERR_NOT_CONVERGED;
       while (it < max_iter) {
-        __syncthreads();
+        tm.sync();
         double pq = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tm.tid; i < n; i += tm.nthr) {
           const double qi = brow<double, double>(S.rp0, S.ci0, S.val0, p, i);
           q[i] = qi;
           pq += p[i] * qi;
         }
-        pq = bsum(pq, sh);
+        pq = tm.sum(pq, sh);
         if (pq == 0.0 || !isfinite(pq) || !isfinite(rz)) { status = AMG_ERR_BREAKDOWN; break; }
         const double alpha = rz / pq;
         double r2 = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tm.tid; i < n; i += tm.nthr) {
           x[i] = x[i] + alpha * p[i];
           const double ri = r[i] - alpha * q[i];
           r[i] = ri;
           r2 += ri * ri;
         }
-        r2 = bsum(r2, sh);
+        r2 = tm.sum(r2, sh);
         ++it;
         rel = sqrt(r2) / bnorm;
         if (rel <= rtol) { status = AMG_OK; break; }
         if (!isfinite(rel)) { status = AMG_ERR_BREAKDOWN; break; }
         if (it == max_iter) break;
-        __syncthreads();
-        b_precond<T>(S, r, z);
+        tm.sync();
+        b_precond<T, C>(tm, S, r, z);
         double rzn = 0.0, zq = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tm.tid; i < n; i += tm.nthr) {
           rzn += r[i] * z[i];
           if (flexible) zq += z[i] * q[i];
         }
-        rzn = bsum(rzn, sh);
-        if (flexible) zq = bsum(zq, sh);
+        rzn = tm.sum(rzn, sh);
+        if (flexible) zq = tm.sum(zq, sh);
         const double beta = (flexible ? -alpha * zq : rzn) / rz;
         if (!isfinite(beta)) { status = AMG_ERR_BREAKDOWN; break; }
         rz = rzn;
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+        tm.sync();
+        for (int i = tm.tid; i < n; i += tm.nthr) p[i] = z[i] + beta * p[i];
       }
       if (status != AMG_OK || restart >= BATCH_RESTARTS || it >= max_iter) break;
       // true residual: accept, or restart from x with r = b - A x
-      __syncthreads();
+      tm.sync();
       rr = residual(nullptr);
       rel = sqrt(rr) / bnorm;
       if (rel <= rtol) break;
@@ -293,15 +332,15 @@ __global__ void __launch_bounds__(BATCH_THREADS) k_batch_pcg(int nsys, const Bat
       status = AMG_ERR_NOT_CONVERGED;
     }
   }
-  __syncthreads();
+  tm.sync();
   // true relative residual from x
   double tr = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = tm.tid; i < n; i += tm.nthr) {
     double ri = b[i] - brow<double, double>(S.rp0, S.ci0, S.val0, x, i);
     tr += ri * ri;
   }
-  tr = bsum(tr, sh);
-  if (threadIdx.x == 0) {
+  tr = tm.sum(tr, sh);
+  if (tm.tid == 0) {
     info[sidx].iterations = it;
     info[sidx].status = status;
     info[sidx].rel = rel;
@@ -370,6 +409,29 @@ amg_status batch_descriptor(amg_hierarchy *h, cudaStream_t s, const BatchSys **o
   return AMG_OK;
 }
 
+// nsys systems of one team size: nsys * team blocks, clusters of `team`.
+template <typename T>
+cudaError_t launch_batch(int team, int nsys, const BatchJob *jobs, double rtol, int max_iter, int flexible,
+                         BatchInfo *info, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nsys * team));
+  cfg.blockDim = dim3(BATCH_THREADS);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)team;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = team > 1 ? 1 : 0;
+  switch (team) {
+    case 1: return cudaLaunchKernelEx(&cfg, k_batch_pcg<T, 1>, nsys, jobs, rtol, max_iter, flexible, info);
+    case 2: return cudaLaunchKernelEx(&cfg, k_batch_pcg<T, 2>, nsys, jobs, rtol, max_iter, flexible, info);
+    case 4: return cudaLaunchKernelEx(&cfg, k_batch_pcg<T, 4>, nsys, jobs, rtol, max_iter, flexible, info);
+    default: return cudaLaunchKernelEx(&cfg, k_batch_pcg<T, 8>, nsys, jobs, rtol, max_iter, flexible, info);
+  }
+}
+
 }  // namespace
 
 extern "C" amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const double *const *d_b,
@@ -399,20 +461,30 @@ extern "C" amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const do
     return AMG_ERR_OOM;
   }
   std::vector<BatchInfo> hinfo(nsys);
-  cudaError_t e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(BatchJob) * nsys, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) {
-    if (prec == AMG_FP32)
-      k_batch_pcg<float><<<nsys, BATCH_THREADS, 0, s>>>(nsys, d_jobs, rtol, max_iter, flexible, d_info);
-    else
-      k_batch_pcg<double><<<nsys, BATCH_THREADS, 0, s>>>(nsys, d_jobs, rtol, max_iter, flexible, d_info);
+  // one launch per team size, the systems of each size contiguous
+  std::vector<int> order(nsys);
+  for (int i = 0; i < nsys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return batch_team(hs[a]->lev[0].n) < batch_team(hs[b]->lev[0].n); });
+  std::vector<BatchJob> sorted(nsys);
+  for (int i = 0; i < nsys; ++i) sorted[i] = jobs[order[i]];
+  cudaError_t e = cudaMemcpyAsync(d_jobs, sorted.data(), sizeof(BatchJob) * nsys, cudaMemcpyHostToDevice, s);
+  for (int g0 = 0; g0 < nsys && e == cudaSuccess;) {
+    const int team = batch_team(hs[order[g0]]->lev[0].n);
+    int g1 = g0;
+    while (g1 < nsys && batch_team(hs[order[g1]]->lev[0].n) == team) ++g1;
+    e = prec == AMG_FP32 ? launch_batch<float>(team, g1 - g0, d_jobs + g0, rtol, max_iter, flexible, d_info + g0, s)
+                         : launch_batch<double>(team, g1 - g0, d_jobs + g0, rtol, max_iter, flexible, d_info + g0, s);
     count_launch();
-    e = cudaGetLastError();
+    g0 = g1;
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hinfo.data(), d_info, sizeof(BatchInfo) * nsys, cudaMemcpyDeviceToHost, s);
+  std::vector<BatchInfo> sinfo(nsys);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sinfo.data(), d_info, sizeof(BatchInfo) * nsys, cudaMemcpyDeviceToHost, s);
   pool_free(d_jobs, s);
   pool_free(d_info, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return amg_cuda_status(e);
+  for (int i = 0; i < nsys; ++i) hinfo[order[i]] = sinfo[i];
   amg_status worst = AMG_OK;
   for (int i = 0; i < nsys; ++i) {
     if (infos) {

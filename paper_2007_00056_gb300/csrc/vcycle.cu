@@ -530,35 +530,23 @@ __global__ void k_cast_scale(int n, const A *__restrict__ a, const float *__rest
   }
 }
 
-// Level 0 of the FP32 cycle in the residual-operator form, reading the FP64
-// right-hand side and writing the FP64 result itself: f is rounded to FP32 as
-// it is read and y widened as it is written, with the conversions the cast
-// kernels use, which saves two passes over the level-0 vectors.
+// Level 0 of the FP32 cycle in the residual-operator form writes the FP64
+// result itself: y is widened as it is written, with the conversion the cast
+// kernel uses, which saves a pass over the level-0 vectors.  (Reading the FP64
+// right-hand side in the first kernel as well was measured slower on the
+// 7-point systems: its neighbour gathers then move twice the bytes.)
 template <int TPR>
-__global__ void k_op_residual_in64(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ rp,
-                                   const int32_t *__restrict__ ci, const float *__restrict__ cval,
-                                   const double *__restrict__ f, float *__restrict__ t, const KState *st) {
-  if (is_done(st)) return;
-  ROW_LOOP_BEGIN(TPR, n)
-  int b = 0, e = 0;
-  if (valid) { b = __ldg(&rp[row]); e = __ldg(&rp[row + 1]); }
-  float cf = row_sum<TPR, float, float>(ci, cval, b, e, _sub, [&](int j) { return to_f32(__ldg(&f[j])); });
-  if (valid && _sub == 0) t[row] = cf;
-  ROW_LOOP_END
-}
-
-template <int TPR>
-__global__ void k_op_post_io64(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ qrp,
-                               const int32_t *__restrict__ qci, const float *__restrict__ qval,
-                               const float *__restrict__ xc, const float *__restrict__ wd,
-                               const double *__restrict__ f, const float *__restrict__ t, double *__restrict__ y,
-                               const KState *st) {
+__global__ void k_op_post_out64(int n, const int32_t *__restrict__ perm, const int32_t *__restrict__ qrp,
+                                const int32_t *__restrict__ qci, const float *__restrict__ qval,
+                                const float *__restrict__ xc, const float *__restrict__ wd,
+                                const float *__restrict__ f, const float *__restrict__ t, double *__restrict__ y,
+                                const KState *st) {
   if (is_done(st)) return;
   ROW_LOOP_BEGIN(TPR, n)
   int b = 0, e = 0;
   if (valid) { b = __ldg(&qrp[row]); e = __ldg(&qrp[row + 1]); }
   float qx = row_sum<TPR, float, float>(qci, qval, b, e, _sub, [&](int J) { return __ldg(&xc[J]); });
-  if (valid && _sub == 0) y[row] = to_f64(qx + wd[row] * (to_f32(f[row]) + t[row]));
+  if (valid && _sub == 0) y[row] = to_f64(qx + wd[row] * (f[row] + t[row]));
   ROW_LOOP_END
 }
 
@@ -1496,21 +1484,22 @@ void vcycle_levels(amg_hierarchy *h, const T *f0, T *out0, cudaStream_t s, const
   cycle_level<T, V>(h, 0, f0, nullptr, out0, h->prm.cycle, s, st);
 }
 
+// KERNEL names the lanes-per-row parameter TPR_.
 #define DISPATCH_TPR_PLAIN(tpr_, g_, KERNEL, ...)                                     \
   do {                                                                              \
     switch (tpr_) {                                                                 \
-      case 2: KERNEL<2><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
-      case 4: KERNEL<4><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
-      case 8: KERNEL<8><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;               \
-      case 16: KERNEL<16><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      case 32: KERNEL<32><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;             \
-      default: KERNEL<1><<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break;              \
+      case 2: { constexpr int TPR_ = 2; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; }   \
+      case 4: { constexpr int TPR_ = 4; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; }   \
+      case 8: { constexpr int TPR_ = 8; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; }   \
+      case 16: { constexpr int TPR_ = 16; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; } \
+      case 32: { constexpr int TPR_ = 32; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; } \
+      default: { constexpr int TPR_ = 1; KERNEL<<<g_, AMG_THREADS, 0, s>>>(__VA_ARGS__); break; } \
     }                                                                               \
   } while (0)
 
 // The level-0 visit of the FP32 cycle in the residual-operator form, from the
-// FP64 residual r to the FP64 result z (the casts folded into its first and
-// last kernels); the coarser levels run the FP32 cycle as usual.
+// FP64 residual r to the FP64 result z (the output cast folded into its last
+// kernel); the coarser levels run the FP32 cycle as usual.
 bool level0_fp32_op(const amg_hierarchy *h) {
   const Level &l = h->lev[0];
   return h->prm.precision == AMG_FP32 && h->L > 0 && l.op_on && l.cval32 && l.qval32 && h->prm.nu_pre == 1 &&
@@ -1528,10 +1517,16 @@ void cycle_level0_fp32_io64(amg_hierarchy *h, const double *r, double *z, cudaSt
   Level lr = l;
   lr.tpr = l.tpr == 0 ? 1 : l.tpr;
   const int tpr = lr.tpr, g = row_blocks(lr);
+  float *f0 = S::f(l);
+  {
+    LaunchScope ls(h, s, PK_CAST, 0, 12.0 * l.n);
+    k_cast_scale<double, float><<<grid_for(l.n, AMG_THREADS), AMG_THREADS, 0, s>>>(l.n, r, nullptr, f0, st);
+  }
   if (staged) l = stage_acquire(h, 0, SET_C, s);
   {
-    LaunchScope ls(h, s, PK_OP_RESIDUAL, 0, bytes_A(l, 4) + 12.0 * l.n);
-    DISPATCH_TPR_PLAIN(tpr, g, k_op_residual_in64, l.n, l.perm, l.rp, l.ci, (const float *)l.cval32, r, b, st);
+    LaunchScope ls(h, s, PK_OP_RESIDUAL, 0, bytes_A(l, 4) + 8.0 * l.n);
+    DISPATCH_TPR_PLAIN(tpr, g, (k_op_residual<TPR_, float, float>), l.n, l.perm, l.rp, l.ci,
+                       (const float *)l.cval32, (const float *)f0, b, st);
   }
   if (staged) stage_release(h, 0, true, s);
   {
@@ -1547,9 +1542,9 @@ void cycle_level0_fp32_io64(amg_hierarchy *h, const double *r, double *z, cudaSt
   if (staged) l = stage_acquire(h, 0, SET_Q, s);
   {
     const double BQ = (double)l.qnnz * 8.0 + 4.0 * (l.n + 1);
-    LaunchScope ls(h, s, PK_OP_POST, 0, BQ + 24.0 * l.n + 4.0 * c.n);
-    DISPATCH_TPR_PLAIN(tpr, g, k_op_post_io64, l.n, l.perm, l.qrp, l.qci, (const float *)l.qval32,
-                       (const float *)xc, (const float *)l.wd32, r, (const float *)b, z, st);
+    LaunchScope ls(h, s, PK_OP_POST, 0, BQ + 20.0 * l.n + 4.0 * c.n);
+    DISPATCH_TPR_PLAIN(tpr, g, k_op_post_out64<TPR_>, l.n, l.perm, l.qrp, l.qci, (const float *)l.qval32,
+                       (const float *)xc, (const float *)l.wd32, (const float *)f0, (const float *)b, z, st);
   }
   if (staged) stage_release(h, 0, false, s);
 }

@@ -1,5 +1,7 @@
-"""Batched PCG (one thread block per system): each system's result is bitwise
-the same alone and in any batch, and agrees with the oracle like pcg_solve."""
+"""Batched PCG (one thread block per system, or a cluster of 2, 4 or 8 blocks
+for systems above 8192, 24576 and 65536 rows): each system's result is
+bitwise the same alone and in any batch, and agrees with the oracle like
+pcg_solve."""
 import numpy as np
 import pytest
 
@@ -19,11 +21,12 @@ def _systems():
             W.fem_p1_jittered(23, seed=8)]
 
 
-def _setup(systems, precision, coarse_max=200):
+def _setup(systems, precision, coarse_max=200, **kw):
     hs, bs = [], []
     for s in systems:
         rp, ci, val, b = to_cuda(s)
-        hs.append(amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=coarse_max, precision=precision)))
+        hs.append(amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=coarse_max, precision=precision,
+                                                                    **kw)))
         bs.append(b)
     return hs, bs
 
@@ -106,3 +109,40 @@ def test_batch_rejections():
     xz = [torch.ones_like(bs[0]), torch.zeros_like(bs[1])]
     infos = amg.amg_batch_pcg(hs, [torch.zeros_like(bs[0]), bs[1]], xz, rtol=1e-8)
     assert infos[0].iterations == 0 and torch.all(xz[0] == 0) and infos[1].status == amg.AMG_OK
+
+
+def _large_systems():
+    # one, two, four and eight blocks per system
+    return [W.poisson2d(60, seed=3), W.poisson2d(100, seed=4), W.fem_p1_jittered(170, seed=5),
+            W.anisotropic3d(42, seed=6)]
+
+
+@pytest.mark.parametrize("precision", [amg.AMG_FP64, amg.AMG_FP32])
+def test_cluster_teams_alone_equal_in_mix_and_match_oracle(precision):
+    systems = _large_systems()
+    assert [s.n for s in systems] == [3600, 10000, 28900, 74088]
+    # a stalled coarsest level keeps the dense solve the batched kernel needs
+    hs, bs = _setup(systems, precision, coarse_max=256, dense_max=2048)
+    xs = [torch.zeros_like(b) for b in bs]
+    infos = amg.amg_batch_pcg(hs, bs, xs, rtol=1e-8, flexible=True)
+    assert all(i.status == amg.AMG_OK and i.rel_res_true <= 1e-8 for i in infos), infos
+    for k in range(len(systems)):
+        x1 = torch.zeros_like(bs[k])
+        i1 = amg.amg_batch_pcg([hs[k]], [bs[k]], [x1], rtol=1e-8, flexible=True)[0]
+        assert i1.iterations == infos[k].iterations
+        assert torch.equal(x1, xs[k]), f"system {k} differs alone vs in the batch"
+    # the same system twice in one launch of its team size (two hierarchies)
+    h2, b2 = _setup([systems[2]], precision, coarse_max=256, dense_max=2048)
+    xa, xb = torch.zeros_like(bs[2]), torch.zeros_like(b2[0])
+    amg.amg_batch_pcg([hs[2], h2[0]], [bs[2], b2[0]], [xa, xb], rtol=1e-8, flexible=True)
+    assert torch.equal(xa, xb) and torch.equal(xa, xs[2])
+    for s, h, info, x in zip(systems, hs, infos, xs):
+        oh = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=256)
+        assert oh.sizes() == h.sizes()
+        x_o, info_o = oh.pcg(s.b, rtol=1e-12, flexible=True)
+        # both stop at a relative residual of 1e-8 or below: the error is at
+        # most cond(A) 1e-8, a few 1e-5 for these systems
+        assert rel_err(x.cpu().numpy(), x_o) < 1e-5
+        if precision == amg.AMG_FP64:
+            _, io = oh.pcg(s.b, rtol=1e-8, flexible=True)
+            assert abs(info.iterations - io.iterations) <= 1
