@@ -18,14 +18,14 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    that become ready while a batch runs join the next one, and batches of
    different classes overlap with each other and with the large solves on
    the worker streams.  Classes keep a batch's systems of similar size: a
-   batch returns when its slowest system converges.  One thread block per
-   system outruns the whole-GPU solve in throughput once enough systems of a
-   class are ready together (measured: 32 systems of 60,000 rows 715
-   solves/s batched against 254/s one at a time; 64 of 8,100 rows 12,950/s
-   against 424/s), but a lone mid-size system is several times slower on one
-   block than on the whole GPU; so a class launches the batched kernel only
-   with at least ``batch_min`` systems and otherwise hands them back to
-   their workers.  Under a backlog the batches fill; at a light load the
+   batch returns when its slowest system converges.  A team of one to eight
+   thread blocks per system outruns the whole-GPU solve in throughput once a
+   few systems of a class are ready together (measured: 32 systems of 60,000
+   rows 2,142 solves/s batched against 259/s one at a time, 4 of them 490/s
+   against 278/s; 64 of 8,100 rows 12,057/s against 440/s), but a lone
+   mid-size system is 2-3x slower on its team than on the whole GPU; so a
+   class launches the batched kernel only with at least ``batch_min``
+   systems and otherwise hands them back to their workers.  Under a backlog the batches fill; at a light load the
    requests take the whole-GPU path.  Requests whose matrix is already
    cached share its hierarchy and take turns on it (its work vectors serve
    one solve at a time).  Larger requests run ``pcg_solve`` on their worker's
@@ -115,7 +115,7 @@ class SolveServer:
                  batch_coarse_max: int = 256, big_coarse_max: int = 1024, big_dense_max: int = 8192,
                  max_batch: int = 256,
                  cache_entries: int = 64, batch_classes=(5000, 20000, 60000), batch_window_s: float = 0.001,
-                 batch_min=(1, 3, 8), params=None):
+                 batch_min=(1, 2, 3), params=None):
         self.dev = torch.device("cuda", device)
         # amg_params fields for every request's setup.  Default: the scaled
         # edge weight max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|), an option the paper
