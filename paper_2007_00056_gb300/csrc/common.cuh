@@ -382,11 +382,6 @@ __device__ __forceinline__ bool is_done(const KState *st) {
 // the hierarchy's precision); `st` may be a Krylov state whose done flag
 // turns every kernel into a no-op.
 amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st);
-// The FP64 cycle whose level-0 visit also forms the PCG step's inner products
-// and beta (vcycle.cu); available when vcycle_fuses_pcg_beta(h).
-bool vcycle_fuses_pcg_beta(const amg_hierarchy *h);
-amg_status vcycle_run_pcg(amg_hierarchy *h, const double *r, double *z, const double *q, double *part,
-                          unsigned *counter, cudaStream_t s, KState *st);
 amg_status coarse_setup(amg_hierarchy *h, cudaStream_t s);
 amg_status dense_inverse(amg_hierarchy *h, cudaStream_t s);
 template <typename T>

@@ -442,11 +442,8 @@ amg_status pcg_iteration(amg_hierarchy *h, cudaStream_t s) {
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
     k_pcg_update<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->part, h->counter + KSLOT_B, h->st);
   }
-  if (vcycle_fuses_pcg_beta(h)) {
-    // the V-cycle's last kernel also forms (r, z), (z, q) and beta
-    AMG_TRY(vcycle_run_pcg(h, h->kr, h->kz, h->kq, h->part, h->counter + KSLOT_C, s, h->st));
-  } else {
-    AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
+  AMG_TRY(vcycle_run(h, h->kr, h->kz, s, h->st));
+  {
     LaunchScope _ls(h, s, PK_KRYLOV_VEC, 0, 3.0 * 8.0 * n);
     k_pcg_beta<<<vec_blocks(n), AMG_THREADS, 0, s>>>(n, h->kr, h->kq, h->kz, h->part, h->counter + KSLOT_C, h->st);
   }

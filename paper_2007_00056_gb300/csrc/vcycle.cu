@@ -550,42 +550,6 @@ __global__ void k_op_post_out64(int n, const int32_t *__restrict__ perm, const i
   ROW_LOOP_END
 }
 
-// Level 0 of the FP64 cycle inside PCG: y = Q x_c + wd (f + t) as k_op_post,
-// with f the PCG residual r and y the preconditioned z, fused with the inner
-// products of the PCG step that follows (Algorithm 4): (r, z), and (z, q) for
-// the flexible beta = -alpha (z, q) / (r_old, z_old).  The last block forms
-// beta and the new (r, z), as a separate pass over r, z and q would.
-template <int TPR>
-__global__ void k_op_post_pcg(int n, const int32_t *__restrict__ qrp, const int32_t *__restrict__ qci,
-                              const double *__restrict__ qval, const double *__restrict__ xc,
-                              const double *__restrict__ wd, const double *__restrict__ f,
-                              const double *__restrict__ t, const double *__restrict__ q, double *__restrict__ y,
-                              double *part, unsigned *counter, KState *st) {
-  if (is_done(st)) return;
-  const bool flex = st->flexible != 0;
-  double v[2] = {0.0, 0.0};
-  const int32_t *perm = nullptr;
-  ROW_LOOP_BEGIN(TPR, n)
-  int b = 0, e = 0;
-  if (valid) { b = __ldg(&qrp[row]); e = __ldg(&qrp[row + 1]); }
-  double qx = row_sum<TPR, double, double>(qci, qval, b, e, _sub, [&](int J) { return __ldg(&xc[J]); });
-  if (valid && _sub == 0) {
-    const double fi = f[row];
-    const double zi = qx + wd[row] * (fi + t[row]);
-    y[row] = zi;
-    v[0] += fi * zi;
-    if (flex) v[1] += zi * q[row];
-  }
-  ROW_LOOP_END
-  double tot[2];
-  if (grid_sum_last<2>(v, part, counter, tot) && threadIdx.x == 0) {
-    const double beta = (flex ? -st->alpha * tot[1] : tot[0]) / st->rz;
-    if (!isfinite(beta)) { st->done = 1; st->status = AMG_ERR_BREAKDOWN; }
-    st->beta = beta;
-    st->rz = tot[0];
-  }
-}
-
 template <typename A, typename B>
 __global__ void k_cast(int n, const A *__restrict__ a, B *__restrict__ b, const KState *st) {
   if (is_done(st)) return;
@@ -1586,55 +1550,6 @@ void cycle_level0_fp32_io64(amg_hierarchy *h, const double *r, double *z, cudaSt
 }
 
 }  // namespace
-
-bool vcycle_fuses_pcg_beta(const amg_hierarchy *h) {
-  const Level &l = h->lev[0];
-  return h->prm.precision == AMG_FP64 && h->L > 0 && l.op_on && l.cval && l.qval && h->prm.nu_pre == 1 &&
-         h->prm.nu_post == 1;
-}
-
-// z = V-cycle(r) in FP64 with the level-0 visit's last kernel forming the PCG
-// step's (r, z), (z, q) and beta (see k_op_post_pcg); vcycle_fuses_pcg_beta(h)
-// must hold.
-amg_status vcycle_run_pcg(amg_hierarchy *h, const double *r, double *z, const double *q, double *part,
-                          unsigned *counter, cudaStream_t s, KState *st) {
-  using S = Sel<double, double>;
-  const int L = h->L, kind = h->prm.cycle;
-  const bool staged = stage_on(h, 0);
-  Level l = h->lev[0];
-  Level &c = h->lev[1];
-  double *b = S::t(l);
-  Level lr = l;
-  lr.tpr = l.tpr == 0 ? 1 : l.tpr;
-  const int tpr = lr.tpr, g = row_blocks(lr);
-  if (staged) l = stage_acquire(h, 0, SET_C, s);
-  {
-    using T = double;
-    using V = double;
-    LaunchScope ls(h, s, PK_OP_RESIDUAL, 0, bytes_A(l, 8) + 16.0 * l.n);
-    DISPATCH_ROWS(l, k_op_residual, l.n, l.perm, l.rp, l.ci, S::cval(l), r, b, st);
-  }
-  if (staged) stage_release(h, 0, true, s);
-  {
-    LaunchScope ls(h, s, PK_RESTRICT, 0, 16.0 * l.n + 8.0 * c.n + 4.0);
-    k_restrict<double><<<grid_for(c.n, AMG_THREADS), AMG_THREADS, 0, s>>>(c.n, l.mrp, l.mem, b, nullptr, nullptr,
-                                                                           S::f(c), st);
-  }
-  double *xc = S::y(c);
-  const double *fc = S::f(c);
-  cycle_level<double, double>(h, 1, fc, nullptr, xc, kind, s, st);
-  if (1 < L && kind == AMG_CYCLE_W) cycle_level<double, double>(h, 1, fc, xc, xc, AMG_CYCLE_W, s, st);
-  if (1 < L && kind == AMG_CYCLE_F) cycle_level<double, double>(h, 1, fc, xc, xc, AMG_CYCLE_V, s, st);
-  if (staged) l = stage_acquire(h, 0, SET_Q, s);
-  {
-    const double BQ = (double)l.qnnz * 12.0 + 4.0 * (l.n + 1);
-    LaunchScope ls(h, s, PK_OP_POST, 0, BQ + 40.0 * l.n + 8.0 * c.n);
-    DISPATCH_TPR_PLAIN(tpr, g, k_op_post_pcg<TPR_>, l.n, l.qrp, l.qci, (const double *)l.qval, (const double *)xc,
-                       (const double *)l.wd, r, (const double *)b, q, z, part, counter, st);
-  }
-  if (staged) stage_release(h, 0, false, s);
-  return amg_cuda_status(cudaGetLastError());
-}
 
 amg_status vcycle_run(amg_hierarchy *h, const double *r, double *z, cudaStream_t s, const KState *st) {
   if (h->prm.precision == AMG_FP64) {
