@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--grid", type=int, default=128, help="cells per side of the lognormal system")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=2048,
                     help="requests of the serving stream added to the line (2048: the whole stream; 0: none)")
@@ -935,19 +935,29 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     e2e_steps = max(1, args.e2e_steps)
+    phases = []  # per step: events after the input copies, after the solve, after the result copy
     for _ in range(e2e_steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
         for d, hsrc in ((d_rp, h_rp), (d_ci, h_ci), (d_val, h_val), (d_b, h_b)):
             d.copy_(hsrc, non_blocking=True)
+        ev[1].record(stream)
         he = amg.amg_setup(d_rp, d_ci, d_val, params)
         xe = torch.zeros_like(d_b)
         amg.pcg_solve(he, d_b, xe, rtol=RTOL, max_iter=1000, flexible=True)
+        ev[2].record(stream)
         h_x.copy_(xe, non_blocking=True)
+        ev[3].record(stream)
         torch.cuda.current_stream().synchronize()
         he.close()
+        phases.append(ev)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = allreduce_max(e0.elapsed_time(e1), world)
     e2e_value = job_throughput(e2e_steps, world, e2e_ms)
+    e2e_phase_ms = {k: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in phases)
+                    for i, k in enumerate(("h2d_ms", "setup_solve_ms", "d2h_ms"))}
+    e2e_step_ms = [ev[0].elapsed_time(ev[3]) for ev in phases]
     del d_rp, d_ci, d_val, d_b, h_rp, h_ci, h_val
 
     # the oracle's full solve runs in a spawned child process on one host core
@@ -993,7 +1003,9 @@ def main():
                                "passes, nine vector passes and the aggregate map per level, 8 N_L^2 for the dense "
                                "coarsest inverse) over the time of twenty V-cycles run with the profiler off"},
             "roofline": roofline, "hbm_level0": hbm_level0, "kernels": kernels,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "mean_phase_ms": e2e_phase_ms, "step_ms": e2e_step_ms,
+                    "h2d_gbs": h2d / (e2e_phase_ms["h2d_ms"] * 1e-3) / 1e9 if e2e_phase_ms["h2d_ms"] > 0 else None},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
             "configs_measured": configs, "cycles": cycles, "complexity": complexity,
             "option_scaled_weight": scaled, "host_resident_levels": residency, "serving": serving,
