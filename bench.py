@@ -242,7 +242,7 @@ def finish_cpu_baseline(proc, conn, timeout_s=900.0):
             "sample": (f"one complete solve of the full 256^3 system by the serial FP64 oracle on one host core: "
                        f"setup {r['setup_s']:.1f} s + flexible PCG {r['solve_s']:.1f} s ({r['iterations']} "
                        f"iterations to 1e-8), timed whole, nothing extrapolated; it ran in a child process while "
-                       f"the GPU lines after the headline and end-to-end timings were measured"),
+                       f"the GPU lines between the end-to-end timing and the serving stream were measured"),
             "time_to_solution_s": t, "iterations": r["iterations"], "rel_res_true": r["rel_res_true"],
             "levels": r["levels"]}
 
@@ -978,12 +978,14 @@ def main():
         scaled = run_scaled_weight(dev, s2)
         del s2
 
+    # the oracle's child is joined before the serving stream: the server's host
+    # threads and copies must not share the host with it either
+    cpu = finish_cpu_baseline(cpu_proc, cpu_conn) if rank == 0 else None
+
     serving = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
         reqs, systems = generate_requests(args.serving_requests)
         serving = run_serving(reqs, systems)
-
-    cpu = finish_cpu_baseline(cpu_proc, cpu_conn) if rank == 0 else None
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
