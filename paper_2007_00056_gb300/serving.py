@@ -80,7 +80,10 @@ class ServeResult:
 
 
 def fingerprint(rp: np.ndarray, ci: np.ndarray, val: np.ndarray) -> str:
-    h = hashlib.blake2b(digest_size=16)
+    """Cache key of a matrix: its sizes and the SHA-256 of its CSR bytes.  SHA-256
+    runs on the CPUs' hash instructions, about twice as fast as BLAKE2 here, and
+    a request hashes its whole matrix (up to about 80 MB) on its worker."""
+    h = hashlib.sha256()
     for a in (rp, ci, val):
         h.update(np.ascontiguousarray(a).view(np.uint8))
     return f"{len(rp) - 1}:{len(ci)}:{h.hexdigest()}"
