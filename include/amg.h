@@ -50,7 +50,7 @@ typedef enum {
   AMG_ERR_NOT_CONVERGED = 6, /* max_iter reached before the tolerance (x still holds the last iterate) */
   AMG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up */
   AMG_ERR_CUDA = 8,          /* a CUDA runtime call failed */
-  AMG_ERR_UNSUPPORTED = 9    /* valid input outside what this build implements */
+  AMG_ERR_UNSUPPORTED = 9    /* valid input outside what this library implements */
 } amg_status;
 
 typedef enum {
