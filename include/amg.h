@@ -121,7 +121,13 @@ typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
  *                dense inverse (0, the default: coarse_max).  A value above
  *                coarse_max keeps the stop size small while a hierarchy whose
  *                coarsening stalled a little above it still gets the direct
- *                coarsest solve instead of the CG. */
+ *                coarsest solve instead of the CG.
+ *   graphs       when the Krylov and stationary solvers replay one captured CUDA graph
+ *                per iteration instead of launching its kernels one by one: 0 (the
+ *                default) from the second solve on a hierarchy, since for a single
+ *                solve the capture costs about what it saves; 1 from the first solve,
+ *                for many concurrent solves whose kernel launches compete on the host;
+ *                -1 never.  Results are the same either way. */
 typedef struct {
   int passes;
   int max_levels;
@@ -137,6 +143,7 @@ typedef struct {
   int edge_weight;
   int operator_form;
   int dense_max;
+  int graphs;
 } amg_params;
 
 /* Result of a Krylov solve.  iterations counts completed iterations (a

@@ -73,6 +73,7 @@ class amg_params(C.Structure):
         ("edge_weight", C.c_int),
         ("operator_form", C.c_int),
         ("dense_max", C.c_int),
+        ("graphs", C.c_int),
     ]
 
 

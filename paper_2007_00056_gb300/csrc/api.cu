@@ -181,6 +181,7 @@ extern "C" amg_status amg_default_params(amg_params *p) {
   p->edge_weight = AMG_WEIGHT_ABS;
   p->operator_form = 1;
   p->dense_max = 0;
+  p->graphs = 0;
   return AMG_OK;
 }
 

@@ -527,11 +527,13 @@ amg_status get_graph(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long l
 }
 
 amg_status run_iterations(amg_hierarchy *h, iter_fn fn, cudaGraphExec_t *exec, long long *nodes, cudaStream_t s) {
-  // a graph is captured once the hierarchy is reused: for a single solve the
-  // capture and instantiation cost more than the launches they save
+  // by default a graph is captured once the hierarchy is reused: for a single
+  // solve the capture and instantiation cost about what the launches they
+  // replace cost; params.graphs = 1 captures on the first solve, -1 never
   // (not while host-resident levels are staged: each visit's copies are
   // issued from the host with the prediction of the next one)
-  const bool use_graph = !h->prof.on && h->stg == nullptr && (*exec != nullptr || h->solves >= 1);
+  const bool use_graph = !h->prof.on && h->stg == nullptr && h->prm.graphs >= 0 &&
+                         (*exec != nullptr || h->solves >= 1 || h->prm.graphs == 1);
   h->solves += 1;
   if (use_graph) AMG_TRY(get_graph(h, fn, exec, nodes));
   // enqueue a few iterations between host checks; kernels after convergence are no-ops

@@ -1467,6 +1467,7 @@ amg_status validate_params(const amg_params *p) {
   if (p->edge_weight != AMG_WEIGHT_ABS && p->edge_weight != AMG_WEIGHT_SCALED) return AMG_ERR_INVALID_ARG;
   if (p->operator_form != 0 && p->operator_form != 1) return AMG_ERR_INVALID_ARG;
   if (p->dense_max < 0) return AMG_ERR_INVALID_ARG;
+  if (p->graphs < -1 || p->graphs > 1) return AMG_ERR_INVALID_ARG;
   return AMG_OK;
 }
 

@@ -248,3 +248,26 @@ def test_staged_rows_on_large_level_match_oracle():
     amg.amg_vcycle(h, b, z)
     tol = VCYCLE_TOL_DENSE if oh.dense_coarse else VCYCLE_TOL_CG
     assert rel_err(z.cpu().numpy(), oh.vcycle(s.b)) < tol
+
+
+@pytest.mark.parametrize("graphs", [-1, 1])
+def test_graph_policy_gives_the_same_solve(graphs):
+    """A solve replayed from a captured graph from its first iteration, or never
+    captured, is the same solve as the default policy's, bit for bit."""
+    s = W.lognormal3d(20, seed=6)
+    ref = None
+    for g in (0, graphs):
+        rp, ci, val, b = to_cuda(s)
+        h = amg.amg_setup(rp, ci, val, amg.amg_default_params(coarse_max=100, graphs=g))
+        outs = []
+        for _ in range(2):  # the default captures on the second solve
+            x = torch.zeros_like(b)
+            info = amg.pcg_solve(h, b, x, rtol=1e-10, flexible=True, check=True)
+            outs.append((info.iterations, x.cpu().numpy().view(np.int64)))
+        h.close()
+        if ref is None:
+            ref = outs
+        else:
+            for (i0, x0), (i1, x1) in zip(ref, outs):
+                assert i0 == i1
+                np.testing.assert_array_equal(x0, x1)
