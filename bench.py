@@ -316,6 +316,34 @@ def generate_requests(count: int):
     return reqs, [systems[r.rid] for r in reqs]
 
 
+def oracle_serving_sample(reqs, systems, count=16):
+    """The oracle (serial FP64, one host core) serving the first `count` requests
+    one at a time at their arrival times: its own solves/s and p50/p99, for
+    context beside the GPU server.  Each request is its setup (the server's
+    stop sizes and edge weight) plus flexible PCG to 1e-8."""
+    import numpy as np
+
+    import oracle as O
+
+    times = []
+    for req, s in list(zip(reqs, systems))[:count]:
+        t0 = time.perf_counter()
+        cm = 256 if s.n <= 60000 else 1024
+        oh = O.Hierarchy(s.rp, s.ci, s.val, params=O.Params(coarse_max=cm, edge_weight=1))
+        oh.pcg(s.b, rtol=RTOL, flexible=True)
+        times.append(time.perf_counter() - t0)
+    done, lat = 0.0, []
+    for (rq, _), t in zip(list(zip(reqs, systems))[:count], times):
+        done = max(done, rq.arrival_s) + t
+        lat.append((done - rq.arrival_s) * 1e3)
+    return {"requests": len(times), "cores": 1, "kind": "oracle",
+            "solves_per_s": len(times) / sum(times),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "sample": f"the first {len(times)} requests of the stream, one at a time at their arrival times, "
+                      f"by the serial FP64 oracle on one host core (setup with the server's stop sizes and "
+                      f"scaled edge weight, flexible PCG to 1e-8)"}
+
+
 def run_serving(reqs, systems, plain_sample=256):
     """Serves the stream at its arrival times (latency), then all at once
     (capacity), then the plain FP64 method one request at a time on the first
@@ -394,6 +422,7 @@ def run_serving(reqs, systems, plain_sample=256):
         "edge_weight": "max(|a_ij|,|a_ji|)/sqrt(|a_ii a_jj|) (option; the server's default)",
         "workers": srv_defaults["workers"],
         "paper_edge_weight": paper,
+        "oracle_one_at_a_time": oracle_serving_sample(reqs, systems),
     }
 
 
