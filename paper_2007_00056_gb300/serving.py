@@ -25,12 +25,13 @@ Requests (a CSR system and a right-hand side, arriving over time) go through:
    against 278/s; 64 of 8,100 rows 12,057/s against 440/s), but a lone
    mid-size system is 2-3x slower on its team than on the whole GPU; so a
    class launches the batched kernel only with at least ``batch_min``
-   systems and otherwise hands them back to their workers.  Under a backlog the batches fill; at a light load the
-   requests take the whole-GPU path.  Requests whose matrix is already
-   cached share its hierarchy and take turns on it (its work vectors serve
-   one solve at a time).  Larger requests run ``pcg_solve`` on their worker's
-   stream, with the whole GPU.  Their
-   hierarchies stop at 1024 rows (``big_coarse_max``) rather than the
+   systems and otherwise hands them back to their workers.  Under a backlog
+   the batches fill; at a light load the requests take the whole-GPU path.
+   Requests whose matrix is already cached share its hierarchy and take
+   turns on it (its work vectors serve one solve at a time).  Larger
+   requests run ``pcg_solve`` on their worker's stream (16 workers by
+   default), with the whole GPU.  Their hierarchies stop at 1024 rows
+   (``big_coarse_max``) rather than the
    library's 4096: the dense inverse of the coarsest level costs 2 N_L^3
    operations, while one more level costs far less.  A hierarchy whose
    coarsening stalls above that (the P1 systems near 10^6 rows stop at a few
