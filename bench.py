@@ -915,14 +915,20 @@ def main():
         level_nnz = [amg.amg_level_info(h, k) for k in range(h.num_levels)]
         for r in amg.amg_profile_table(h):
             key = (r["kind"], r["level"])
-            acc = table_acc.setdefault(key, dict(kind=r["kind"], level=r["level"], ms=0.0, bytes=0.0, launches=0))
+            acc = table_acc.setdefault(key, dict(kind=r["kind"], level=r["level"], ms=0.0, bytes=0.0, launches=0,
+                                                 step_ms=[]))
             acc["ms"] += r["ms"]
             acc["bytes"] += r["bytes"]
             acc["launches"] += r["launches"]
+            acc["step_ms"].append(r["ms"])
         if ps == args.profile_steps - 1:
             bv = b_v_bytes(h, 8, 8)
             vc = vcycle_rate(h, b, bv)
         h.close()
+    # each kernel's time is its median over the profiled steps, times their
+    # number (one step's timings can be disturbed by the node's other work)
+    for acc in table_acc.values():
+        acc["ms"] = statistics.median(acc["step_ms"]) * len(acc["step_ms"])
     table = sorted(table_acc.values(), key=lambda r: -r["ms"])
     # dominant single kernel of the step among the solve-phase kernels
     top = next((r for r in table if r["kind"] in HBM_KERNEL_KINDS), None)
