@@ -1298,10 +1298,12 @@ int hem_coop_blocks(amg_hierarchy *h, int n) {
     cudaGetLastError();
     return 0;
   }
-  // one block per 4096 nodes up to one per SM: a small graph's rounds take a
+  // one block per 1024 nodes up to one per SM: a small graph's rounds take a
   // few blocks (a cheaper grid barrier) and leave the other SMs to the work
-  // of other streams
-  return (int)std::min<long long>(h->num_sms, std::max<long long>(1, cdiv(n, 4096)));
+  // of other streams (measured: one block per 4096 nodes slowed the 128^3
+  // lognormal setup from 14.1 to 17.2 ms, its coarse levels' wide rounds
+  // wanting more blocks)
+  return (int)std::min<long long>(h->num_sms, std::max<long long>(1, cdiv(n, 1024)));
 }
 
 // One pairwise pass on `in`: matching rounds, numbering, Galerkin product.
