@@ -398,9 +398,14 @@ __global__ void __launch_bounds__(BGJ_W * 16) k_bgj_diag(int m, int k0, int w, c
 }
 
 // Step 2: R = P^-1 M_K* for the columns outside K, stored in R (w x m) and in
-// the K rows of M.  Block: 64 columns; thread: one column, 16 of the rows.
+// the K rows of M.  Block: BGJ_RC columns (all w rows; a block writes only the
+// columns it read, so the update in place is safe); thread: one column, every
+// 16th row.
 // Shared memory of k_bgj_rows / k_bgj_cols: two BGJ_W x (BGJ_W + 1) tiles.
 #define BGJ_TILE_SMEM(T) (2 * sizeof(T) * BGJ_W * (BGJ_W + 1))
+// columns (rows) of M per block of k_bgj_rows (k_bgj_cols): 16 gives 4 x m / 64
+// blocks, enough to cover the GPU at m = 4096 (64 blocks did not)
+#define BGJ_RC 16
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_bgj_rows(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv,
@@ -408,16 +413,16 @@ __global__ void __launch_bounds__(256) k_bgj_rows(int m, int k0, int w, T *__res
   extern __shared__ __align__(16) unsigned char bgj_rs[];
   T(*Ps)[BGJ_W + 1] = (T(*)[BGJ_W + 1])bgj_rs;
   T(*Ms)[BGJ_W + 1] = Ps + BGJ_W;
-  const int tid = threadIdx.x, j0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, j0 = blockIdx.x * BGJ_RC;
   for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
-  for (int idx = tid; idx < w * 64; idx += blockDim.x) {
-    const int r = idx >> 6, jj = idx & 63, j = j0 + jj;
+  for (int idx = tid; idx < w * BGJ_RC; idx += blockDim.x) {
+    const int r = idx / BGJ_RC, jj = idx % BGJ_RC, j = j0 + jj;
     Ms[r][jj] = j < m ? M[(size_t)(k0 + r) * m + j] : (T)0;
   }
   __syncthreads();
-  const int jj = tid & 63, j = j0 + jj, rg = tid >> 6;
+  const int jj = tid % BGJ_RC, j = j0 + jj, rg = tid / BGJ_RC;
   if (j >= m || (j >= k0 && j < k0 + w)) return;
-  for (int r = rg; r < w; r += 4) {
+  for (int r = rg; r < w; r += 256 / BGJ_RC) {
     T acc = (T)0;
     for (int c = 0; c < w; ++c) acc += Ps[r][c] * Ms[c][jj];
     R[(size_t)r * m + j] = acc;
@@ -549,24 +554,25 @@ __global__ void __launch_bounds__(256) k_bgj_update4(int m, int k0, int w, float
   }
 }
 
-// Step 4: M_IK <- -M_IK P^-1 for I outside K, M_KK <- P^-1.  Block: 64 rows;
-// thread: one row, 16 of the columns.
+// Step 4: M_IK <- -M_IK P^-1 for I outside K, M_KK <- P^-1.  Block: BGJ_RC
+// rows (all w columns, again only what it read); thread: one row, every 16th
+// column.
 template <typename T>
 __global__ void __launch_bounds__(256) k_bgj_cols(int m, int k0, int w, T *__restrict__ M, const T *__restrict__ Pinv) {
   extern __shared__ __align__(16) unsigned char bgj_cs[];
   T(*Ps)[BGJ_W + 1] = (T(*)[BGJ_W + 1])bgj_cs;
   T(*Cs)[BGJ_W + 1] = Ps + BGJ_W;
-  const int tid = threadIdx.x, i0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, i0 = blockIdx.x * BGJ_RC;
   for (int idx = tid; idx < w * w; idx += blockDim.x) Ps[idx / w][idx % w] = Pinv[idx];
-  for (int idx = tid; idx < 64 * w; idx += blockDim.x) {
+  for (int idx = tid; idx < BGJ_RC * w; idx += blockDim.x) {
     const int r = idx / w, c = idx - r * w, i = i0 + r;
     Cs[r][c] = i < m ? M[(size_t)i * m + k0 + c] : (T)0;
   }
   __syncthreads();
-  const int r = tid & 63, cg = tid >> 6, i = i0 + r;
+  const int r = tid % BGJ_RC, cg = tid / BGJ_RC, i = i0 + r;
   if (i >= m) return;
   const bool in_k = i >= k0 && i < k0 + w;
-  for (int c = cg; c < w; c += 4) {
+  for (int c = cg; c < w; c += 256 / BGJ_RC) {
     T v;
     if (in_k) {
       v = Ps[i - k0][c];
@@ -623,12 +629,12 @@ amg_status bgj_inverse(amg_hierarchy *h, T *out, cudaStream_t st) {
   for (int k0 = 0; k0 < m; k0 += BGJ_W) {
     const int w = std::min(BGJ_W, m - k0);
     k_bgj_diag<T><<<1, BGJ_W * 16, 0, st>>>(m, k0, w, out, Pinv, h->eflags);
-    k_bgj_rows<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv, R);
+    k_bgj_rows<T><<<cdiv(m, BGJ_RC), 256, tsmem, st>>>(m, k0, w, out, Pinv, R);
     if (vec4)
       k_bgj_update4<<<ug, 256, BGJ4_SMEM, st>>>(m, k0, w, (float *)out, (const float *)R);
     else
       k_bgj_update<T, TL::BM, TL::BN, TL::TM, TL::TN><<<ug, 256, smem, st>>>(m, k0, w, out, R);
-    k_bgj_cols<T><<<cdiv(m, 64), 256, tsmem, st>>>(m, k0, w, out, Pinv);
+    k_bgj_cols<T><<<cdiv(m, BGJ_RC), 256, tsmem, st>>>(m, k0, w, out, Pinv);
     count_launch(4);
   }
   if (m != n) {
