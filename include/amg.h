@@ -216,18 +216,20 @@ amg_status bicgstab_solve(const amg_hierarchy *h, const double *d_b, double *d_x
                           int max_iter, amg_stream_t stream, amg_solve_info *info);
 
 /* Batched AMG-PCG (Algorithm 4 per system, V-cycle of Algorithm 1): solves
- * nsys independent systems in one persistent launch, one thread block per
- * system, each running its whole solve (same arguments and stopping rule as
- * pcg_solve, applied per system).  hs[i] is the hierarchy of system i (each
+ * nsys independent systems in one persistent launch per team size, each
+ * system on its own team -- one thread block up to 8192 rows, a thread-block
+ * cluster of 2 / 4 / 8 blocks above 8192 / 24576 / 65536 rows -- running its
+ * whole solve (same arguments and stopping rule as pcg_solve, applied per
+ * system).  hs[i] is the hierarchy of system i (each
  * hierarchy at most once per call; every hierarchy must have a dense
  * coarsest level of at most 2048 rows (an FP64 inverse), the V-cycle and the
  * same precision, FP64 or FP32;
  * AMG_ERR_UNSUPPORTED otherwise); d_b[i], d_x[i] are its device right-hand
- * side and initial guess / solution.  Block reductions only: the result of a
- * system does not depend on the rest of the batch.  infos (host, length nsys,
+ * side and initial guess / solution.  Team reductions in a fixed order only:
+ * the result of a system does not depend on the rest of the batch.  infos (host, length nsys,
  * may be NULL) receives every system's result; the return value is AMG_OK
  * when every system converged, else the first non-OK status.  Synchronises
- * the stream.  Meant for many small systems; a large system is faster alone
+ * the stream.  Meant for several systems at once; a lone system is faster
  * with pcg_solve, which spreads it over the whole GPU. */
 amg_status amg_batch_pcg(int nsys, amg_hierarchy *const *hs, const double *const *d_b, double *const *d_x,
                          double rtol, int max_iter, int flexible, amg_stream_t stream, amg_solve_info *infos);
