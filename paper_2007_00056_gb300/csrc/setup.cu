@@ -915,8 +915,58 @@ __global__ void __launch_bounds__(AMG_THREADS)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int warps = (gridDim.x * blockDim.x) >> 5;
-  for (int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; I < nc; I += warps) {
-    const int4 mt = meta[I];
+  // coarse rows in pairs: two rows of at most 16 contributions each take one
+  // half-warp each (the same per-row steps and sum order as the full-warp
+  // path below); any other row takes the whole warp
+  for (int I2 = 2 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); I2 < nc; I2 += 2 * warps) {
+    const bool two = I2 + 1 < nc;
+    const int4 mt0 = meta[I2];
+    const int4 mt1 = two ? meta[I2 + 1] : make_int4(0, 0, 0, 0);
+    if (two && mt0.y + mt0.w <= 16 && mt1.y + mt1.w <= 16) {
+      const int h = lane >> 4, hl = lane & 15;
+      const int4 mt = h ? mt1 : mt0;
+      PairRow r;
+      r.b0 = mt.x;
+      r.n0 = mt.y;
+      r.b1 = mt.z;
+      r.n1 = mt.w;
+      const int m = r.m();
+      const int I = I2 + h;
+      const int out0 = FILL ? rpc[I] : 0;
+      const bool in = hl < m;
+      const int J = in ? Jf[r.pos(hl)] : 0;
+      const double v = in ? val[r.pos(hl)] : 0.0;
+      // keys of the two halves never meet (bit 31 marks the second half,
+      // coarse columns are below 2^31); unused lanes get distinct negatives
+      const int key = in ? (int)((unsigned)J | ((unsigned)h << 31)) : -1 - lane;
+      sV[wib][lane] = v;
+      const unsigned grp = __match_any_sync(0xffffffffu, key);
+      const bool firstJ = in && (grp & ((1u << lane) - 1u)) == 0u;
+      __syncwarp();
+      double sum = v;
+      if (firstJ) {
+        unsigned rest = grp & ~((2u << lane) - 1u);
+        while (rest) {
+          const int q = __ffs(rest) - 1;
+          sum = __dadd_rn(sum, sV[wib][q]);
+          rest &= rest - 1u;
+        }
+      }
+      const unsigned fm = __ballot_sync(0xffffffffu, firstJ);
+      int rank = 0;
+      for (int k = 0; k < 16; ++k) {
+        const int src = (h << 4) + k;
+        const int Jk = __shfl_sync(0xffffffffu, J, src);
+        if (k < m && ((fm >> src) & 1u) && Jk < J) ++rank;
+      }
+      if (FILL && firstJ) { cic[out0 + rank] = J; valc[out0 + rank] = sum; }
+      if (!FILL && hl == 0) count[I] = __popc(fm & (h ? 0xffff0000u : 0x0000ffffu));
+      __syncwarp();
+      continue;
+    }
+    for (int u = 0; u < (two ? 2 : 1); ++u) {
+    const int I = I2 + u;
+    const int4 mt = u ? mt1 : mt0;
     PairRow r;
     r.b0 = mt.x;
     r.n0 = mt.y;
@@ -1019,6 +1069,7 @@ __global__ void __launch_bounds__(AMG_THREADS)
       for (int o = 16; o > 0; o >>= 1) distinct += __shfl_xor_sync(0xffffffffu, distinct, o);
     }
     if (!FILL && lane == 0) count[I] = distinct;
+    }
   }
 }
 
