@@ -70,8 +70,9 @@ def parse_args():
                     help="requests of the serving stream added to the line (2048: the whole stream; 0: none)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the other workloads (256^3 mixed precision, 2048^2 BiCGStab, 64^2 Poisson)")
-    ap.add_argument("--workload", choices=["solve", "serving"], default="solve",
-                    help="serving: run the full 2048-request stream and print only its line")
+    ap.add_argument("--workload", choices=["solve", "serving", "batched"], default="solve",
+                    help="serving: run the full 2048-request stream and print only its line; batched: the "
+                         "batched kernel against single solves, alone")
     ap.add_argument("--profile-case", default=None,
                     help="one setup + FP64 flexible PCG solve of a named system for profiler captures, e.g. "
                          "anisotropic3d_128, anisotropic3d_256, lognormal3d_128 (prints one line, no timing)")
@@ -424,6 +425,95 @@ def run_serving(reqs, systems, plain_sample=256):
         "paper_edge_weight": paper,
         "oracle_one_at_a_time": oracle_serving_sample(reqs, systems),
     }
+
+
+def run_batched(dev, groups=((2000, 48), (16000, 48), (30000, 24), (60000, 24))):
+    """The batched kernel against the same systems solved one at a time.
+
+    Each group holds `k` systems of about `n` rows, the three families of the
+    serving stream in turn (seed 5000 + j), set up as the server sets up a
+    batchable request (FP32 V-cycle, coarsest at most 256 rows, dense, scaled
+    edge weight). Timed with CUDA events, solve phase only (hierarchies
+    already built): one `amg_batch_pcg` call over the group; `pcg_solve` on each
+    system in turn with the same hierarchies; and the plain FP64 method (FP64
+    hierarchies, PCG with the fixed preconditioner) in turn."""
+    import torch
+
+    from paper_2007_00056_gb300 import amg
+    from paper_2007_00056_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    def dense_coarse(h):
+        return amg.amg_coarse_cg_cluster_size(h) < 0
+
+    lines = []
+    for n_target, k in groups:
+        systems = [W.Request(j, 0.0, W.FAMILIES[j % 3], n_target, 5000 + j).system() for j in range(k)]
+        p32 = amg.amg_default_params(precision=amg.AMG_FP32, coarse_max=256, edge_weight=amg.AMG_WEIGHT_SCALED)
+        p64 = amg.amg_default_params(coarse_max=256, edge_weight=amg.AMG_WEIGHT_SCALED)
+        h32, h64, bs = [], [], []
+        for s in systems:
+            rp, ci, val, b = (torch.from_numpy(a).to(dev) for a in (s.rp, s.ci, s.val, s.b))
+            h = amg.amg_setup(rp, ci, val, p32)
+            if h.sizes()[-1] > 256 or not dense_coarse(h):
+                h.close()
+                continue
+            h32.append(h)
+            h64.append(amg.amg_setup(rp, ci, val, p64))
+            bs.append(b)
+        m = len(h32)
+        if m == 0:
+            lines.append({"n_target": n_target, "systems": 0, "status": "no batchable hierarchy"})
+            continue
+
+        def batch():
+            xs = [torch.zeros_like(b) for b in bs]
+            return xs, amg.amg_batch_pcg(h32, bs, xs, rtol=RTOL, flexible=True)
+
+        def single(hs, flexible):
+            xs, infos = [], []
+            for h, b in zip(hs, bs):
+                x = torch.zeros_like(b)
+                infos.append(amg.pcg_solve(h, b, x, rtol=RTOL, flexible=flexible))
+                xs.append(x)
+            return xs, infos
+
+        batch()  # warm-up: first launches of each team size
+        single(h32[:1], True)
+        single(h64[:1], False)
+        ms_b, (xb, ib) = timed(batch)
+        ms_s, (_, is_) = timed(lambda: single(h32, True))
+        ms_p, (xp, ip) = timed(lambda: single(h64, False))
+        err = max(float(torch.linalg.norm(x - y) / torch.linalg.norm(y)) for x, y in zip(xb, xp))
+        lines.append({
+            "n_target": n_target, "systems": m, "rows_total": int(sum(b.numel() for b in bs)),
+            "team_blocks": sorted({1 if b.numel() <= 8192 else 2 if b.numel() <= 24576 else 4 if b.numel() <= 65536
+                                   else 8 for b in bs}),
+            "batched_solves_per_s": m / (ms_b * 1e-3),
+            "single_fp32_solves_per_s": m / (ms_s * 1e-3),
+            "plain_fp64_single_solves_per_s": m / (ms_p * 1e-3),
+            "batched_over_single": ms_s / ms_b, "batched_over_plain_fp64": ms_p / ms_b,
+            "iterations_batched": [min(i.iterations for i in ib), max(i.iterations for i in ib)],
+            "iterations_plain_fp64": [min(i.iterations for i in ip), max(i.iterations for i in ip)],
+            "converged_1e-8": int(sum(i.status == amg.AMG_OK and i.rel_res_true <= RTOL for i in ib)),
+            "rel_res_true_max": max(i.rel_res_true for i in ib),
+            "max_rel_err_vs_plain_fp64": err,
+        })
+        for h in h32 + h64:
+            h.close()
+    return {"note": "solve phase only, hierarchies built beforehand; FP32 V-cycle in FP64 flexible PCG for the "
+                    "batched and single lines, the FP64 V-cycle in PCG for the plain method; CUDA events",
+            "lines": lines}
 
 
 VCYCLE_KINDS = {"jacobi0", "jacobi", "residual", "restrict", "prolong_jacobi", "prolong", "coarse_dense",
@@ -825,6 +915,16 @@ def main():
                     "config": {"workload": "serving stream, 2048 requests, Poisson arrivals 200/s"}})
         print(json.dumps(out), flush=True)
         return
+    if args.workload == "batched":
+        import torch
+
+        from paper_2007_00056_gb300 import amg
+
+        amg.lib(build_if_missing=True)
+        out = run_batched(torch.device("cuda", 0))
+        print(json.dumps({"metric": "batched AMG-PCG solves/s against single solves", "unit": "solves/s",
+                          "n_gpus": 1, "data": "synthetic", "batched": out}), flush=True)
+        return
 
     rank, world, local = dist_setup(args)
     import torch
@@ -1003,9 +1103,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_proc, cpu_conn = start_cpu_baseline()
 
-    configs = cycles = complexity = scaled = residency = None
+    configs = cycles = complexity = scaled = residency = batched = None
     if rank == 0 and world == 1 and not args.no_configs:
         configs = run_configs(dev, peak, x_main)
+        try:
+            batched = run_batched(dev)
+        except Exception as e:  # recorded in the line; the other workloads still run
+            batched = {"error": f"{type(e).__name__}: {e}"}
         residency = run_residency(dev)
         s2 = W.config_lognormal3d_128()
         cycles = run_cycles(dev, s2)
@@ -1045,7 +1149,8 @@ def main():
                     "h2d_gbs": h2d / (e2e_phase_ms["h2d_ms"] * 1e-3) / 1e9 if e2e_phase_ms["h2d_ms"] > 0 else None},
             "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
             "configs_measured": configs, "cycles": cycles, "complexity": complexity,
-            "option_scaled_weight": scaled, "host_resident_levels": residency, "serving": serving,
+            "option_scaled_weight": scaled, "host_resident_levels": residency, "batched": batched,
+            "serving": serving,
         }
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -426,7 +426,8 @@ def amg_memory_info(h: Hierarchy) -> dict:
 
 
 def amg_batch_pcg(hs, bs, xs, rtol: float = 1e-8, max_iter: int = 1000, flexible: bool = False, stream=None):
-    """Solves len(hs) systems in one launch (one thread block per system).
+    """Solves len(hs) systems in one persistent launch per team size (a thread
+    block, or a cluster of 2, 4 or 8 blocks, per system by its row count).
     Returns the list of per-system solve infos; raises AmgError only for
     errors other than non-convergence or breakdown."""
     k = len(hs)
