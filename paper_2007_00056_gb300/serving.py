@@ -150,8 +150,9 @@ class SolveServer:
         self._pending: "collections.deque" = collections.deque()  # admitted, waiting for a worker
         self.batch_classes = tuple(sorted(c for c in batch_classes if c < small_max_n)) + (small_max_n,)
         # fewest systems a batch of each class needs to beat solving them one
-        # by one on the worker streams (the batched kernel gives a system one
-        # thread block, so a lone mid-size system is faster on the whole GPU)
+        # by one on the worker streams (the batched kernel gives a system a
+        # team of one to four thread blocks here, so a lone mid-size system
+        # is faster on the whole GPU)
         bm = tuple(batch_min) + (batch_min[-1],) * len(self.batch_classes)
         self.batch_min = bm[:len(self.batch_classes)]
         self._batchqs = [queue.Queue() for _ in self.batch_classes]
@@ -255,29 +256,35 @@ class SolveServer:
                 self.stats["setup"] += 1
             else:
                 self.stats["cache_hit"] += 1
-            x = torch.zeros_like(d_b)
-            h = entry.h
-            stream.synchronize()
-            setup_done = time.perf_counter()
-            batchable = (n <= self.small_max_n and h.sizes()[-1] <= self.batch_coarse_max
-                         and self._dense_coarse(h))
-            with entry.lock:
-                info = None
-                path = "single"
-                if batchable:
-                    done = threading.Event()
-                    slot = {}
-                    cls = next(k for k, c in enumerate(self.batch_classes) if n <= c)
-                    self._batchqs[cls].put((h, d_b, x, done, slot))
-                    done.wait()
-                    info = slot["info"]  # None: too few systems of the class were ready to batch
-                    if info is not None:
-                        path = "batch"
-                if info is None:
-                    info = amg.pcg_solve(h, d_b, x, rtol=self.rtol, max_iter=self.max_iter, flexible=True,
-                                         stream=stream)
-                hx = x.to("cpu", non_blocking=True)
+            try:
+                x = torch.zeros_like(d_b)
+                h = entry.h
                 stream.synchronize()
+                setup_done = time.perf_counter()
+                batchable = (n <= self.small_max_n and h.sizes()[-1] <= self.batch_coarse_max
+                             and self._dense_coarse(h))
+                with entry.lock:
+                    info = None
+                    path = "single"
+                    if batchable:
+                        done = threading.Event()
+                        slot = {}
+                        cls = next(k for k, c in enumerate(self.batch_classes) if n <= c)
+                        self._batchqs[cls].put((h, d_b, x, done, slot))
+                        done.wait()
+                        info = slot["info"]  # None: the batcher handed the system back
+                        if info is not None:
+                            path = "batch"
+                    if info is None:
+                        info = amg.pcg_solve(h, d_b, x, rtol=self.rtol, max_iter=self.max_iter, flexible=True,
+                                             stream=stream)
+                    hx = x.to("cpu", non_blocking=True)
+                    stream.synchronize()
+            except BaseException:
+                # the worker reports the error; the cached hierarchy becomes evictable again
+                with self._lock:
+                    entry.users -= 1
+                raise
         fin = time.perf_counter()
         with self._lock:
             entry.users -= 1
@@ -331,8 +338,14 @@ class SolveServer:
             try:
                 infos = amg.amg_batch_pcg([g[0] for g in group], [g[1] for g in group], [g[2] for g in group],
                                           rtol=self.rtol, max_iter=self.max_iter, flexible=True, stream=stream)
-            except amg.AmgError as exc:
-                infos = [amg.amg_solve_info(0, float("nan"), float("nan"), exc.status) for _ in group]
+            except Exception:
+                # the batch failed as a whole: hand its systems back, each worker
+                # then solves (or reports) its own system alone
+                for g in group:
+                    g[4]["info"] = None
+                    g[3].set()
+                self.stats["batch_errors"] += 1
+                continue
             self.stats["batches"] += 1
             self.stats["batched"] += len(group)
             for g, info in zip(group, infos):

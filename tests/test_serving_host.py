@@ -102,3 +102,37 @@ def test_small_and_large_requests_get_their_coarse_limits():
     srv.params = {"edge_weight": amg.AMG_WEIGHT_ABS, "operator_form": 0}
     p = srv._params_for(6000)
     assert p.edge_weight == amg.AMG_WEIGHT_ABS and p.operator_form == 0 and p.dense_max == 8192
+
+
+def test_batcher_hands_a_failed_batch_back_to_the_workers(monkeypatch):
+    """A batch that fails as a whole returns every system to its worker (info
+    None: the worker then solves it alone) instead of leaving it waiting."""
+    import queue
+
+    srv = _bare_server(budget=100)
+    srv.dev = None
+    srv.max_batch = 8
+    srv.batch_window_s = 0.001
+    srv._stop = False
+    monkeypatch.setattr(S.torch.cuda, "set_device", lambda d: None)
+    monkeypatch.setattr(S.torch.cuda, "Stream", lambda device=None: None)
+
+    def failing_batch(*args, **kwargs):
+        raise RuntimeError("batch failed")
+
+    monkeypatch.setattr(S.amg, "amg_batch_pcg", failing_batch)
+    bq = queue.Queue()
+    items = [(object(), None, None, threading.Event(), {}) for _ in range(3)]
+    for it in items:
+        bq.put(it)
+    t = threading.Thread(target=srv._batch_loop, args=(bq, 1), daemon=True)
+    t.start()
+    try:
+        for it in items:
+            assert it[3].wait(5.0)
+    finally:
+        srv._stop = True
+        t.join(5.0)
+    assert not t.is_alive()
+    assert all(it[4]["info"] is None for it in items)
+    assert srv.stats["batch_errors"] >= 1 and srv.stats["batches"] == 0
