@@ -550,25 +550,6 @@ __global__ void k_op_post_out64(int n, const int32_t *__restrict__ perm, const i
   ROW_LOOP_END
 }
 
-template <typename A, typename B>
-__global__ void k_cast(int n, const A *__restrict__ a, B *__restrict__ b, const KState *st) {
-  if (is_done(st)) return;
-  const long long S = (long long)gridDim.x * blockDim.x;
-  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += STREAM_U * S) {
-    A av[STREAM_U];
-#pragma unroll
-    for (int u = 0; u < STREAM_U; ++u) {
-      const long long i = i0 + u * S;
-      if (i < n) av[u] = a[i];
-    }
-#pragma unroll
-    for (int u = 0; u < STREAM_U; ++u) {
-      const long long i = i0 + u * S;
-      if (i < n) b[i] = (B)av[u];
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // Coarsest solve: dense inverse (one warp per row, FP64 accumulation)
 // ---------------------------------------------------------------------------
