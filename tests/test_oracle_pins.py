@@ -509,6 +509,38 @@ def test_bicgstab_spd_and_exact_preconditioner():
     np.testing.assert_allclose(x, np.linalg.solve(s.dense(), s.b), rtol=1e-11)
 
 
+def _bicgstab_breakdown_system():
+    """Two copies of [[1, 3], [3, 1]] (eigenvalues 4 and -2), omega = 1 and a
+    coarsest level of 2 rows: pairs {0,1} and {2,3}, A_c = diag(8, 8).  Every
+    step of the V-cycle is exact in binary.  Worked by hand from Algorithm 1:
+    A M^-1 = I on the pair-constant vectors and -8 I on the pair-alternating
+    ones.  For b = 2 (1,1,0,0) + (1,-1,0,0) + 2 (0,0,1,1) = (3, 1, 2, 2),
+    (A M^-1 b, b) = 2 (4 - 8 + 4) = 0 exactly."""
+    a = np.kron(np.eye(2), np.array([[1.0, 3.0], [3.0, 1.0]]))
+    return a, np.array([3.0, 1.0, 2.0, 2.0])
+
+
+def test_bicgstab_breakdown_when_the_first_direction_meets_the_shadow_residual_at_zero():
+    """R11's breakdown rule: with r_0 = rbar_0 = b and p~ = M^-1 b, the first
+    step divides by (A p~, rbar_0); when that is 0 the solve stops with
+    ERR_BREAKDOWN and leaves x at the initial guess.  A b whose product is not
+    0 (the last entry changed) converges instead."""
+    a, b = _bicgstab_breakdown_system()
+    s = W.from_dense(a, b)
+    h = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=2, omega=1.0)
+    assert h.sizes() == [4, 2] and h.dense_coarse
+    z = h.vcycle(b)
+    np.testing.assert_array_equal(z, [4.5, -3.5, 0.5, 0.5])  # Algorithm 1 by hand
+    assert (a @ z) @ b == 0.0
+    x, info = h.bicgstab(b, rtol=1e-10)
+    assert info.status == O.ERR_BREAKDOWN and not np.any(x)
+    b2 = np.array([3.0, 1.0, 2.0, 1.0])
+    assert (a @ h.vcycle(b2)) @ b2 != 0.0
+    x2, info2 = h.bicgstab(b2, rtol=1e-12)
+    assert info2.status == O.OK
+    np.testing.assert_allclose(x2, np.linalg.solve(a, b2), rtol=0, atol=1e-12)
+
+
 def test_check_csr_rejects_bad_input():
     s = W.poisson2d(4)
     assert O.check_csr(s.rp, s.ci) == O.OK
