@@ -427,6 +427,41 @@ def test_vcycle_operator_symmetric_and_contracting():
     assert np.max(np.abs(np.linalg.eigvals(E))) < 1.0
 
 
+def test_residual_operator_form_equals_algorithm_1():
+    """The device evaluates a zero-guess visit of level k (one pre- and one
+    post-sweep) as t = C f and y = Q x_c + omega D^-1 (f + t), with
+    C = I - omega A D^-1 and Q = P - omega D^-1 A P formed at setup.  Expanding
+    Algorithm 1: x1 = omega D^-1 f, t = f - A x1 = C f, f_c = P^T t,
+    x2 = x1 + P x_c and y = x2 + omega D^-1 (f - A x2) = Q x_c + omega D^-1 (f + t).
+    The rewritten recursion, built from the oracle's own levels, gives the
+    oracle's V-cycle on symmetric and nonsymmetric hierarchies of three or
+    more levels."""
+    omega = 2.0 / 3.0
+    for s, cm in ((W.poisson2d(12), 16), (W.lognormal3d(6, seed=3), 16), (W.convdiff2d(12, peclet=50.0), 10)):
+        oh = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=cm)
+        L = oh.num_levels
+        assert L >= 3 and oh.dense_coarse
+        lev = [oh.level(k) for k in range(L)]
+        A = [_dense(rp, ci, val, len(rp) - 1) for rp, ci, val, _ in lev]
+        P = [_P(lev[k][3], A[k + 1].shape[0]) for k in range(L - 1)]
+
+        def op_cycle(k, f, q_sign=-1.0):
+            if k == L - 1:
+                return np.linalg.solve(A[k], f)
+            dinv = 1.0 / np.diag(A[k])
+            C = np.eye(len(f)) - omega * A[k] * dinv[None, :]
+            Q = P[k] + q_sign * (omega * dinv)[:, None] * (A[k] @ P[k])
+            t = C @ f
+            x_c = op_cycle(k + 1, P[k].T @ t, q_sign)
+            return Q @ x_c + omega * dinv * (f + t)
+
+        f = np.random.default_rng(5).uniform(-1.0, 1.0, s.n)
+        z = oh.vcycle(f)
+        assert np.linalg.norm(op_cycle(0, f) - z) <= 1e-12 * np.linalg.norm(z)
+        # the check sees a planted mistake (Q with its second term's sign flipped)
+        assert np.linalg.norm(op_cycle(0, f, q_sign=1.0) - z) > 1e-3 * np.linalg.norm(z)
+
+
 def test_coarse_cg_solver_agrees_with_dense():
     s = W.lognormal3d(8, seed=2)
     hd = O.Hierarchy(s.rp, s.ci, s.val, coarse_max=60, coarse_solver=1)
