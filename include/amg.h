@@ -15,7 +15,9 @@
  * Conventions shared by every entry point
  *   - All array arguments are DEVICE pointers on the current CUDA device
  *     (for example torch tensors' data_ptr()).  No entry point reads host
- *     arrays except where stated (amg_params, amg_solve_info are host structs).
+ *     arrays except where stated (amg_params, amg_solve_info are host structs;
+ *     amg_batch_pcg takes host arrays of hierarchy handles and of device
+ *     vector pointers).
  *   - CSR: 0-based, int32 row pointers (n+1) and column indices (nnz), columns
  *     strictly ascending within each row, square n x n, values FP64.
  *   - Work is ordered on the caller's stream; functions that return results
@@ -95,7 +97,9 @@ typedef enum { AMG_WEIGHT_ABS = 0, AMG_WEIGHT_SCALED = 1 } amg_edge_weight;
  *                rows, else Jacobi-PCG to a relative residual of 1e-12 (Sec. 4.2),
  *                on one thread block cluster up to 2048 rows, else on the whole GPU.
  *                The dense solve applies the inverse formed at setup by blocked
- *                Gauss-Jordan elimination with partial pivoting: in FP64 up to
+ *                Gauss-Jordan elimination (without row interchanges when every
+ *                pivot block is invertible and the inverse passes its accuracy
+ *                check, else with partial pivoting): in FP64 up to
  *                2048 rows; above that in FP32 with a fixed number of FP64
  *                refinement steps per solve (x += X (f - A x)), chosen at setup
  *                so the result has FP64 accuracy (FP64 inverse if refinement
@@ -220,7 +224,8 @@ amg_status bicgstab_solve(const amg_hierarchy *h, const double *d_b, double *d_x
  * system on its own team -- one thread block up to 8192 rows, a thread-block
  * cluster of 2 / 4 / 8 blocks above 8192 / 24576 / 65536 rows -- running its
  * whole solve (same arguments and stopping rule as pcg_solve, applied per
- * system).  hs[i] is the hierarchy of system i (each
+ * system).  hs, d_b and d_x are host arrays of nsys entries.  hs[i] is the
+ * hierarchy of system i (each
  * hierarchy at most once per call; every hierarchy must have a dense
  * coarsest level of at most 2048 rows (an FP64 inverse), the V-cycle and the
  * same precision, FP64 or FP32;
