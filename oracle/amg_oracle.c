@@ -45,7 +45,11 @@
  *    coarsest level is solved once per coarse correction;
  *  - AMG as a solver (Sec. 3.1, Sec. 4.4) is the stationary iteration
  *    x_{j+1} = x_j + M^{-1}(b - A x_j) with M^{-1} one cycle from a zero
- *    guess, stopping once ||b - A x_j|| <= rtol ||b||.
+ *    guess, stopping once ||b - A x_j|| <= rtol ||b||;
+ *  - the node-based matching's scan "alternately from the first and the last
+ *    index" (Sec. 2.1.1) alternates per pairwise pass over the whole
+ *    hierarchy (upward in passes 0, 2, 4, ..., downward in 1, 3, 5, ...),
+ *    numbering aggregates in visit order as Algorithm 2's counter does.
  */
 #include <math.h>
 #include <stdint.h>
